@@ -1,0 +1,605 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: a library
+routine (numpy Gauss nodes), a closed form (polynomial reproduction, analytic
+maps, the Stokes relaxation, the analytic high-order time-integration case of
+Sec. 5.1, bounce counts between planar walls), an invariant (order conditions
+of the RK table, partition of unity, speed under reflection, particle count)
+or brute force (point location over every element).
+
+Readings pinned here (arXiv 2211.05458):
+  * Sec. 5.1 prints x_1,ex with t^3 where integrating its own v_1,ex gives t^3/3;
+    the integrated form is used.
+  * Sec. 5.1 starts the particle on the domain boundary y = 2; the domain is
+    shifted to y in [0.5, 4.5] (flow u = y/2 unchanged) so the start is interior.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import optimize
+
+import oracle
+from paper_2211_05458_gb300 import workloads as W
+
+
+def _np(t):
+    return t.detach().cpu().numpy() if hasattr(t, "detach") else np.asarray(t)
+
+
+# ---------------------------------------------------------------------------
+# nodes and Lagrange basis
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", range(1, 10))
+def test_gauss_nodes_match_numpy(n):
+    assert np.allclose(oracle.nodes(0, n), np.polynomial.legendre.leggauss(n)[0], atol=1e-15)
+
+
+@pytest.mark.parametrize("n", range(2, 10))
+def test_gll_nodes_are_legendre_derivative_roots(n):
+    c = np.zeros(n)
+    c[-1] = 1.0
+    roots = np.sort(np.polynomial.legendre.Legendre(c).deriv().roots().real)
+    ref = np.concatenate([[-1.0], roots, [1.0]])
+    assert np.allclose(oracle.nodes(1, n), ref, atol=1e-14)
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+@pytest.mark.parametrize("n", [2, 4, 6, 8])
+def test_lagrange_reproduces_polynomials(kind, n):
+    xn = oracle.nodes(kind, n)
+    rng = np.random.default_rng(n + 10 * kind)
+    for x in rng.uniform(-1, 1, 5):
+        for j in range(n):
+            assert abs(oracle.lagrange(xn, j, xn[j]) - 1.0) < 1e-14
+            for m in range(n):
+                if m != j:
+                    assert abs(oracle.lagrange(xn, j, xn[m])) < 1e-14
+        for k in range(n):
+            val = sum(xn[i] ** k * oracle.lagrange(xn, i, x) for i in range(n))
+            der = sum(xn[i] ** k * oracle.lagrange_deriv(xn, i, x) for i in range(n))
+            assert abs(val - x ** k) < 1e-12
+            assert abs(der - (k * x ** (k - 1) if k else 0.0)) < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# element map and Newton inverse
+# ---------------------------------------------------------------------------
+
+def _poly_warp(x, y, z, amp):
+    return x, y + amp * x * x * (1.0 + z), z + 0.5 * amp * x * y
+
+
+def _poly_warp_jac(x, y, z, amp):
+    return np.array([[1.0, 0.0, 0.0],
+                     [2 * amp * x * (1 + z), 1.0, amp * x * x],
+                     [0.5 * amp * y, 0.5 * amp * x, 1.0]])
+
+
+def _straight(mesh, e, xi):
+    nx, ny, nz = mesh.dims
+    i, j, k = e % nx, (e // nx) % ny, e // (nx * ny)
+    h = [(mesh.hi[d] - mesh.lo[d]) / mesh.dims[d] for d in range(3)]
+    ijk = (i, j, k)
+    return np.array([mesh.lo[d] + (ijk[d] + 0.5 * (xi[d] + 1)) * h[d] for d in range(3)]), h
+
+
+@pytest.mark.parametrize("ngeo", [2, 3])
+def test_elem_map_matches_polynomial_warp(ngeo):
+    amp = 0.3
+    mesh = W.box_mesh((2, 3, 2), (0.0, -1.0, 0.5), (1.0, 1.0, 1.5), ngeo,
+                      periodic=(False, False, False), warp="poly", amp=amp)
+    orc = oracle.Oracle(mesh.as_dict())
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        e = int(rng.integers(mesh.nelem))
+        xi = rng.uniform(-1, 1, 3)
+        xs, h = _straight(mesh, e, xi)
+        ref = np.array(_poly_warp(*xs, amp))
+        Jref = _poly_warp_jac(*xs, amp) @ np.diag([0.5 * hd for hd in h])
+        x, J = orc.elem_map(e, xi)
+        assert np.allclose(x, ref, atol=1e-13)
+        assert np.allclose(J, Jref, atol=1e-12)
+        ok, xin, it = orc.newton(e, ref)
+        assert ok and np.allclose(xin, xi, atol=1e-12)
+
+
+def test_newton_affine_closed_form():
+    mesh = W.box_mesh((3, 2, 4), (0.0, 0.0, 0.0), (1.5, 1.0, 2.0), 1)
+    orc = oracle.Oracle(mesh.as_dict())
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        e = int(rng.integers(mesh.nelem))
+        xi = rng.uniform(-1, 1, 3)
+        x, _ = _straight(mesh, e, xi)
+        ok, xin, it = orc.newton(e, x)
+        assert ok and it <= 2
+        assert np.allclose(xin, xi, atol=1e-14)
+
+
+@pytest.mark.parametrize("ngeo", [2, 3])
+def test_newton_curved_roundtrip_and_residual(ngeo):
+    mesh = W.channel_mesh((4, 4, 3), ngeo, amp=0.2)
+    orc = oracle.Oracle(mesh.as_dict())
+    rng = np.random.default_rng(3)
+    for _ in range(30):
+        e = int(rng.integers(mesh.nelem))
+        xi = rng.uniform(-1, 1, 3)
+        x, _ = orc.elem_map(e, xi)
+        ok, xin, it = orc.newton(e, x)
+        assert ok
+        assert np.max(np.abs(xin - xi)) < 1e-12
+        xr, _ = orc.elem_map(e, xin)
+        assert np.max(np.abs(xr - x)) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# interpolation
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("node_type", [0, 1])
+@pytest.mark.parametrize("N", [1, 3, 5, 7])
+def test_interp_exact_for_tensor_polynomials(N, node_type):
+    mesh = W.box_mesh((2, 2, 2), (0.0, 0.0, 0.0), (1.0, 2.0, 0.5), 1)
+    rng = np.random.default_rng(N)
+    coeffs = rng.normal(size=(5, N + 1, N + 1, N + 1))
+    U = W.fluid_polynomial(mesh, N, coeffs, node_type)
+    orc = oracle.Oracle(mesh.as_dict())
+    orc.set_fluid(N, node_type, _np(U))
+    for _ in range(10):
+        e = int(rng.integers(mesh.nelem))
+        xi = rng.uniform(-1, 1, 3)
+        x, _ = _straight(mesh, e, xi)
+        ref = np.zeros(5)
+        for a in range(N + 1):
+            for b in range(N + 1):
+                for c in range(N + 1):
+                    ref += coeffs[:, a, b, c] * x[0] ** a * x[1] ** b * x[2] ** c
+        got = orc.interp(e, xi)
+        assert np.allclose(got, ref, rtol=1e-11, atol=1e-11)
+
+
+# ---------------------------------------------------------------------------
+# LSERK coefficients
+# ---------------------------------------------------------------------------
+
+def butcher_from_2n(A, B):
+    """Butcher tableau (a, b, c) of the 2N-storage scheme du <- A_i du + dt F,
+    u <- u + B_i du, stage i evaluated at the state after stage i-1."""
+    s = len(A)
+
+    def w(j, l):  # prod_{m=j+1}^{l} A_m
+        p = 1.0
+        for m in range(j + 1, l + 1):
+            p *= A[m]
+        return p
+    a = np.zeros((s, s))
+    for k in range(s):
+        for j in range(k):
+            a[k, j] = sum(B[l] * w(j, l) for l in range(j, k))
+    b = np.array([sum(B[l] * w(j, l) for l in range(j, s)) for j in range(s)])
+    return a, b, a.sum(axis=1)
+
+
+def test_lserk_order_conditions():
+    A, B, C = oracle.lserk_coeffs()
+    a, b, c = butcher_from_2n(A, B)
+    assert np.allclose(c, C, atol=1e-14)
+    conds = [
+        (b.sum(), 1.0), (b @ c, 1 / 2), (b @ c ** 2, 1 / 3), (b @ (a @ c), 1 / 6),
+        (b @ c ** 3, 1 / 4), (b @ (c * (a @ c)), 1 / 8), (b @ (a @ c ** 2), 1 / 12),
+        (b @ (a @ (a @ c)), 1 / 24),
+    ]
+    for got, want in conds:
+        assert abs(got - want) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# drag + LSERK against closed forms
+# ---------------------------------------------------------------------------
+
+def _uniform_setup(u0, N=2, dims=(4, 4, 4)):
+    mesh = W.box_mesh(dims, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), 1)
+    U = W.fluid_uniform(mesh, N, u0)
+    orc = oracle.Oracle(mesh.as_dict())
+    orc.set_fluid(N, 0, _np(U))
+    return mesh, orc
+
+
+def test_stokes_relaxation_discrete_and_analytic():
+    u0 = np.array([0.7, -0.2, 0.4])
+    mesh, orc = _uniform_setup(u0)
+    mu, rho_p, d = 1e-5, 1000.0, 1e-4
+    tau = rho_p * d * d / (18 * mu)
+    dt, nsteps = 5e-3, 40
+    p = oracle.make_params(mu=mu, rho_p=rho_p, drag_law=0)
+    x0 = np.array([[0.43, 0.51, 0.47]])
+    out = orc.push(p, x0, np.zeros((1, 3)), [d], orc.locate_bruteforce(x0[0])[:1],
+                   nsteps=nsteps, dt=dt)
+    A, B, _ = oracle.lserk_coeffs()
+    a, b, _ = butcher_from_2n(A, B)
+    z = -dt / tau
+    R = 1.0 + sum(z ** k * (b @ np.linalg.matrix_power(a, k - 1) @ np.ones(5)) for k in range(1, 6))
+    want = u0 + R ** nsteps * (0.0 - u0)
+    assert np.allclose(out["v"][0], want, rtol=0, atol=1e-13)
+    t = dt * nsteps
+    exact = u0 * (1 - math.exp(-t / tau))
+    assert np.allclose(out["v"][0], exact, atol=1e-6)
+    xex = x0[0] + u0 * t - tau * u0 * (1 - math.exp(-t / tau))
+    shift = np.round(out["x"][0] - xex)  # periodic wraps of the unit cube
+    assert np.allclose(out["x"][0] - shift, xex, atol=1e-6)
+
+
+@pytest.mark.parametrize("St", [0.1, 1.0, 10.0])
+def test_high_order_time_integration_case(St):
+    """Sec. 5.1: linear shear u = (y/y0, 0, 0), gravity in y, drag on x only."""
+    y0, g = 2.0, -9.81
+    mesh = W.box_mesh((2, 4, 2), (0.0, 0.5, 0.0), (2.0, 4.5, 2.0), 1,
+                      periodic=(False, False, False))
+    N = 3
+    U = W.fluid_linear_shear(mesh, N, y0)
+    orc = oracle.Oracle(mesh.as_dict())
+    orc.set_fluid(N, 0, _np(U))
+    tau = St * 2.0 / 1.0
+    mu, rho_p = 1e-5, 1000.0
+    d = math.sqrt(18 * mu * tau / rho_p)
+    p = oracle.make_params(mu=mu, rho_p=rho_p, drag_law=0, g=(0, g, 0), mask=(1, 0, 0))
+    x0 = np.array([[0.5, y0, 0.5]])
+    e0 = orc.locate_bruteforce(x0[0])
+    assert len(e0) == 1
+    T = 0.4
+    c = g / (2 * y0)
+    x1 = 0.5 + T - tau * (1 - math.exp(-T / tau)) + c * (
+        T ** 3 / 3 - T ** 2 * tau + 2 * tau ** 2 * T + 2 * tau ** 3 * (math.exp(-T / tau) - 1))
+    v1 = 1 - math.exp(-T / tau) + c * (T ** 2 - 2 * T * tau + 2 * tau ** 2 -
+                                        2 * tau ** 2 * math.exp(-T / tau))
+    errs = []
+    for k in range(4):
+        dt = 0.1 / 2 ** k
+        out = orc.push(p, x0, np.zeros((1, 3)), [d], e0, nsteps=int(round(T / dt)), dt=dt)
+        assert out["status"][0] & oracle.ST_FROZEN == 0
+        assert abs(out["x"][0, 1] - (y0 + 0.5 * g * T ** 2)) < 1e-12
+        assert abs(out["v"][0, 1] - g * T) < 1e-12
+        errs.append(abs(out["x"][0, 0] - x1))
+        if k == 3:
+            assert abs(out["v"][0, 0] - v1) < 1e-6
+    errs = np.array(errs)
+    slopes = np.log2(errs[:-1] / errs[1:])
+    assert errs[-1] < 1e-7
+    # observed order between successive halvings, where rounding (~1e-12) does
+    # not yet dominate the truncation error
+    usable = errs[1:] > 5e-11
+    assert usable.sum() >= 1
+    assert np.all(slopes[usable] > 3.6) and np.all(slopes[usable] < 4.6), (errs, slopes)
+
+
+def test_schiller_naumann_terminal_velocity():
+    """Quiescent fluid, gravity: v_t solves f_D(Re(v_t)) v_t / tau = |g|."""
+    mesh, orc = _uniform_setup(np.zeros(3), N=1, dims=(3, 3, 3))
+    mu, rho_p, d, g = 1e-5, 1000.0, 1e-4, 9.81
+    tau = rho_p * d * d / (18 * mu)
+    p = oracle.make_params(mu=mu, rho_p=rho_p, drag_law=1, g=(0, -g, 0))
+
+    def resid(vt):
+        re = vt * d / mu
+        return (1 + 0.15 * re ** 0.687) * vt / tau - g
+    vt = optimize.brentq(resid, 1e-6, 10.0, xtol=1e-15)
+    x0 = np.array([[0.3, 0.6, 0.7]])
+    out = orc.push(p, x0, np.zeros((1, 3)), [d], orc.locate_bruteforce(x0[0]),
+                   nsteps=1000, dt=1e-3)
+    assert out["status"][0] & oracle.ST_FROZEN == 0
+    assert abs(out["v"][0, 1] + vt) < 1e-6 * vt
+    assert abs(out["v"][0, 0]) < 1e-14 and abs(out["v"][0, 2]) < 1e-14
+
+
+# ---------------------------------------------------------------------------
+# tracking
+# ---------------------------------------------------------------------------
+
+def _fold_periodic(x, lo, hi):
+    L = hi - lo
+    return lo + np.mod(x - lo, L)
+
+
+def test_free_stream_straight_lines_through_curved_faces():
+    mesh = W.channel_mesh((6, 4, 3), 3, amp=0.2)
+    N = 2
+    u0 = np.array([1.0, 0.0, 0.3])
+    U = W.fluid_uniform(mesh, N, u0)
+    orc = oracle.Oracle(mesh.as_dict())
+    orc.set_fluid(N, 0, _np(U))
+    x, el = W.seed_particles(mesh, 40, seed=5, margin=0.05)
+    x = _np(x)
+    v = np.tile(u0, (len(x), 1))
+    d = np.full(len(x), 1e-4)
+    p = oracle.make_params(drag_law=0)
+    dt, nsteps = 0.01, 100
+    out = orc.push(p, x, v, d, _np(el), nsteps=nsteps, dt=dt)
+    T = dt * nsteps
+    want = x + u0 * T
+    want[:, 0] = _fold_periodic(want[:, 0], 0.0, 2 * math.pi)
+    want[:, 2] = _fold_periodic(want[:, 2], 0.0, math.pi)
+    got = out["x"].copy()
+    got[:, 0] = _fold_periodic(got[:, 0], 0.0, 2 * math.pi)
+    got[:, 2] = _fold_periodic(got[:, 2], 0.0, math.pi)
+    assert np.allclose(got, want, atol=1e-10)
+    assert np.all(out["status"] & oracle.ST_FROZEN == 0)
+    assert np.all(out["hits"] == 0)
+    ncheck = 0
+    for i in range(len(x)):
+        if out["status"][i] & oracle.ST_NEAR_FACE:
+            continue
+        owners = orc.locate_bruteforce(out["x"][i], tol=1e-10)
+        assert list(owners) == [out["elem"][i]]
+        ncheck += 1
+    assert ncheck >= 35
+
+
+@pytest.mark.parametrize("ngeo,N", [(2, 3), (3, 4)])
+def test_turbulent_channel_owner_is_bruteforce_owner(ngeo, N):
+    mesh = W.channel_mesh((5, 4, 3), ngeo, amp=0.1)
+    U, scale = W.fluid_channel(mesh, N, 0, seed=3)
+    orc = oracle.Oracle(mesh.as_dict())
+    orc.set_fluid(N, 0, _np(U))
+    P = 60
+    x, el = W.seed_particles(mesh, P, seed=9)
+    x = _np(x)
+    rng = np.random.default_rng(4)
+    vel = rng.normal(size=(P, 3)) * 2.0  # fast, so that walls and faces are crossed
+    d = np.full(P, 4e-3)
+    p = oracle.make_params(drag_law=1)
+    out = orc.push(p, x, vel, d, _np(el), nsteps=30, dt=5e-3)
+    assert np.all(out["status"] & oracle.ST_FROZEN == 0)  # nothing lost: count conserved
+    assert out["hits"].sum() > 0
+    ncheck = 0
+    for i in range(P):
+        if out["status"][i] & oracle.ST_NEAR_FACE:
+            continue
+        owners = orc.locate_bruteforce(out["x"][i], tol=1e-10)
+        assert list(owners) == [out["elem"][i]], (i, owners, out["elem"][i])
+        assert -1.0 <= out["x"][i, 1] <= 1.0
+        ncheck += 1
+    assert ncheck >= P - 3
+
+
+def test_reflection_between_planar_walls_matches_unfolded_ray():
+    mesh = W.channel_mesh((4, 5, 3), 2, amp=0.15)
+    N = 1
+    U = W.fluid_uniform(mesh, N, (0.0, 0.0, 0.0))
+    orc = oracle.Oracle(mesh.as_dict())
+    orc.set_fluid(N, 0, _np(U))
+    P = 30
+    x, el = W.seed_particles(mesh, P, seed=11)
+    x = _np(x)
+    rng = np.random.default_rng(12)
+    vel = rng.normal(size=(P, 3)) * 3.0
+    p = oracle.make_params(mask=(0.0, 0.0, 0.0))
+    dt, nsteps = 0.01, 60
+    out = orc.push(p, x, vel, np.full(P, 1e-4), _np(el), nsteps=nsteps, dt=dt)
+    T = dt * nsteps
+    yu = x[:, 1] + vel[:, 1] * T
+    nb = np.abs(np.floor((yu + 1) / 2) - np.floor((x[:, 1] + 1) / 2)).astype(int)
+    yf = np.mod(yu + 1, 4.0)
+    yf = np.where(yf > 2.0, 4.0 - yf, yf) - 1.0
+    speed0 = np.linalg.norm(vel, axis=1)
+    speed1 = np.linalg.norm(out["v"], axis=1)
+    assert np.allclose(speed1, speed0, rtol=1e-14 * 8)
+    ok = out["status"] & oracle.ST_NEAR_FACE == 0
+    assert ok.sum() >= P - 2
+    assert np.array_equal(out["hits"][ok], nb[ok])
+    assert np.allclose(out["x"][ok, 1], yf[ok], atol=1e-11)
+    assert np.allclose(np.abs(out["v"][ok, 1]), np.abs(vel[ok, 1]), rtol=1e-13)
+
+
+def test_reflection_on_curved_walls_conserves_speed():
+    mesh = W.channel_mesh((4, 3, 3), 3, amp=0.15, curved_walls=True)
+    N = 1
+    U = W.fluid_uniform(mesh, N, (0.0, 0.0, 0.0))
+    orc = oracle.Oracle(mesh.as_dict())
+    orc.set_fluid(N, 0, _np(U))
+    P = 20
+    x, el = W.seed_particles(mesh, P, seed=13)
+    rng = np.random.default_rng(14)
+    vel = rng.normal(size=(P, 3)) * 3.0
+    p = oracle.make_params(mask=(0.0, 0.0, 0.0))
+    out = orc.push(p, _np(x), vel, np.full(P, 1e-4), _np(el), nsteps=60, dt=0.01)
+    assert np.all(out["status"] & oracle.ST_FROZEN == 0)
+    assert out["hits"].sum() >= 10
+    assert np.allclose(np.linalg.norm(out["v"], axis=1), np.linalg.norm(vel, axis=1),
+                       rtol=1e-13)
+    for i in range(P):
+        if out["status"][i] & oracle.ST_NEAR_FACE:
+            continue
+        assert list(orc.locate_bruteforce(out["x"][i])) == [out["elem"][i]]
+
+
+def test_planar_face_hit_matches_plane_formula():
+    """Sec. 3.2.4: alpha = (x_m.n - x.n) / (t.n) for a planar face."""
+    mesh = W.box_mesh((2, 2, 2), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), 1)
+    orc = oracle.Oracle(mesh.as_dict())
+    rng = np.random.default_rng(15)
+    for _ in range(20):
+        x0 = rng.uniform(0.05, 0.45, 3)
+        x1 = x0 + rng.normal(size=3) * 0.6
+        td = (x1 - x0) / np.linalg.norm(x1 - x0)
+        for f in range(6):
+            ctrl = orc.face_ctrl(0, f)
+            xm = ctrl.reshape(-1, 3).mean(axis=0)
+            nrm = np.zeros(3)
+            nrm[f // 2] = 1.0
+            if abs(td @ nrm) < 1e-6:
+                continue
+            alpha = (xm @ nrm - x0 @ nrm) / (td @ nrm)
+            hits = orc.face_hits(0, f, x0, x1)
+            inside = alpha > 0 and alpha <= np.linalg.norm(x1 - x0)
+            xh = x0 + alpha * td
+            others = [k for k in range(3) if k != f // 2]
+            inside = inside and all(0.0 <= xh[k] <= 0.5 for k in others)
+            if inside:
+                assert len(hits) == 1 and abs(hits[0, 0] - alpha) < 1e-13
+            elif alpha > 0.01 and alpha < np.linalg.norm(x1 - x0) - 0.01 and all(
+                    0.01 <= xh[k] <= 0.49 or xh[k] < -0.01 or xh[k] > 0.51 for k in others):
+                assert len(hits) == 0
+
+
+@pytest.mark.parametrize("warp,ngeo", [("none_twist", 1), ("channel", 3)])
+def test_face_hits_lie_on_face_and_ray(warp, ngeo):
+    if warp == "none_twist":
+        mesh = W.box_mesh((1, 1, 1), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), 1,
+                          periodic=(False, False, False))
+        mesh.xgeo[0, 7] += np.array([0.15, 0.2, -0.1])  # twisted: bilinear faces
+    else:
+        mesh = W.channel_mesh((3, 2, 2), ngeo, amp=0.3)
+    orc = oracle.Oracle(mesh.as_dict())
+    rng = np.random.default_rng(16)
+    nh = 0
+    for _ in range(40):
+        e = int(rng.integers(mesh.nelem))
+        x0, _ = orc.elem_map(e, rng.uniform(-0.9, 0.9, 3))
+        x1, _ = orc.elem_map(e, rng.uniform(-1, 1, 3) * 2.5)
+        td = (x1 - x0) / np.linalg.norm(x1 - x0)
+        for f in range(6):
+            for alpha, s, t in orc.face_hits(e, f, x0, x1):
+                xi = [0.0, 0.0, 0.0]
+                fixed = f // 2
+                free = [k for k in range(3) if k != fixed]
+                xi[fixed] = 1.0 if f & 1 else -1.0
+                xi[free[0]], xi[free[1]] = s, t
+                xf, _ = orc.elem_map(e, np.array(xi))
+                assert np.linalg.norm(x0 + alpha * td - xf) < 1e-12
+                nh += 1
+    assert nh >= 30
+
+
+def test_bezier_control_points_reproduce_face():
+    mesh = W.channel_mesh((2, 2, 2), 3, amp=0.3)
+    orc = oracle.Oracle(mesh.as_dict())
+    from math import comb
+    rng = np.random.default_rng(17)
+    for f in range(6):
+        ctrl = orc.face_ctrl(1, f)  # [k][m][xyz]
+        p = ctrl.shape[0] - 1
+        for _ in range(5):
+            s, t = rng.uniform(-1, 1, 2)
+            u, w = 0.5 * (s + 1), 0.5 * (t + 1)
+            bu = [comb(p, m) * u ** m * (1 - u) ** (p - m) for m in range(p + 1)]
+            bw = [comb(p, k) * w ** k * (1 - w) ** (p - k) for k in range(p + 1)]
+            pt = sum(bw[k] * bu[m] * ctrl[k, m] for k in range(p + 1) for m in range(p + 1))
+            xi = [0.0, 0.0, 0.0]
+            free = [k for k in range(3) if k != f // 2]
+            xi[f // 2] = 1.0 if f & 1 else -1.0
+            xi[free[0]], xi[free[1]] = s, t
+            xf, _ = orc.elem_map(1, np.array(xi))
+            assert np.allclose(pt, xf, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# two-way coupling source
+# ---------------------------------------------------------------------------
+
+def test_deposit_partition_of_unity_sign_and_kronecker():
+    mesh = W.box_mesh((2, 2, 2), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), 1)
+    N = 3
+    U = W.fluid_uniform(mesh, N, (0.0, 0.0, 0.0))
+    orc = oracle.Oracle(mesh.as_dict())
+    orc.set_fluid(N, 0, _np(U))
+    mu, rho_p = 1e-5, 1000.0
+    p = oracle.make_params(mu=mu, rho_p=rho_p, drag_law=1)
+    rng = np.random.default_rng(18)
+    P = 50
+    x, el = W.seed_particles(mesh, P, seed=18)
+    vel = rng.normal(size=(P, 3))
+    d = rng.uniform(1e-4, 1e-3, P)
+    S = orc.deposit(p, _np(x), vel, d, _np(el))
+    # force on each particle from the closed forms of Sec. 2.2 (fluid at rest)
+    tau = rho_p * d * d / (18 * mu)
+    re = np.linalg.norm(vel, axis=1) * d / mu
+    fD = 1 + 0.15 * re ** 0.687
+    mp = rho_p * math.pi * d ** 3 / 6
+    F = (mp * fD / tau)[:, None] * (0.0 - vel)
+    assert np.allclose(S[:, :3, :].sum(axis=(0, 2)), -F.sum(axis=0), rtol=1e-12, atol=1e-18)
+    assert np.allclose(S[:, 3, :].sum(), -(F * vel).sum(), rtol=1e-12)
+    # fluid gains momentum along the particle's motion (action = -reaction)
+    assert np.all(np.sign(-F) == np.sign(vel))
+    # a particle sitting on a solution node deposits on that node only
+    xn = W.gauss_nodes(N + 1)
+    xi = np.array([xn[1], xn[2], xn[0]])
+    xs, _ = _straight(mesh, 3, xi)
+    S1 = orc.deposit(p, xs[None], np.array([[0.3, 0.0, 0.0]]), [5e-4], [3])
+    big = np.abs(S1[3]).max()
+    nz = np.flatnonzero(np.abs(S1[3, 0]) > 1e-12 * big)
+    n = N + 1
+    assert list(nz) == [1 + n * (2 + n * 0)]
+    assert np.all(np.flatnonzero(np.abs(S1[3]).max(axis=0) > 1e-12 * big) == nz)
+    assert np.abs(S1[[0, 1, 2, 4, 5, 6, 7]]).max() == 0.0
+
+
+# ---------------------------------------------------------------------------
+# learned-guess network (no counterpart in the paper)
+# ---------------------------------------------------------------------------
+
+def test_mlp_gradient_matches_central_differences():
+    n = oracle.mlp_nparams()
+    assert n == 64 * 51 + 64 + 2 * (64 * 64 + 64) + 3 * 64 + 3
+    rng = np.random.default_rng(19)
+    theta = rng.normal(size=n) * 0.2
+    inp = rng.normal(size=(7, 51))
+    tgt = rng.normal(size=(7, 3))
+    loss, grad = oracle.mlp_loss_grad(theta, inp, tgt)
+    idx = rng.choice(n, 60, replace=False)
+    idx = np.concatenate([idx, [n - 1, n - 4, 64 * 51 + 3]])
+    for i in idx:
+        h = 1e-5
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (oracle.mlp_loss_grad(tp, inp, tgt)[0] - oracle.mlp_loss_grad(tm, inp, tgt)[0]) / (2 * h)
+        assert abs(fd - grad[i]) <= 1e-7 * max(1.0, abs(fd)) + 1e-9, (i, fd, grad[i])
+
+
+def test_mlp_forward_special_cases():
+    n = oracle.mlp_nparams()
+    theta = np.zeros(n)
+    theta[-3:] = [0.5, -1.0, 2.0]
+    out = oracle.mlp_forward(theta, np.ones((2, 51)))
+    assert np.allclose(out, [[0.5, -1.0, 2.0]] * 2, atol=0)
+    # single path: x0 -> unit weights -> GELU(1) = Phi(1) = 0.8413447460685429
+    theta = np.zeros(n)
+    W1, b1 = 0, 64 * 51
+    W2 = b1 + 64
+    W3 = W2 + 64 * 64 + 64
+    W4 = W3 + 64 * 64 + 64
+    theta[W1 + 0] = 1.0
+    theta[W2 + 0] = 1.0
+    theta[W3 + 0] = 1.0
+    theta[W4 + 0] = 1.0
+    gelu = lambda z: 0.5 * z * (1 + math.erf(z / math.sqrt(2)))
+    x = np.zeros((1, 51))
+    x[0, 0] = 1.0
+    out = oracle.mlp_forward(theta, x)
+    assert abs(gelu(1.0) - 0.8413447460685429) < 1e-15
+    assert abs(out[0, 0] - gelu(gelu(gelu(1.0)))) < 1e-15
+
+
+def test_adam_first_step_closed_form():
+    theta = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -4.0, 1e-3])
+    m, v = np.zeros(3), np.zeros(3)
+    oracle.adam(theta, g, m, v, 1, lr=0.01, eps=1e-8)
+    # first step: m_hat = g, v_hat = g^2 => step = lr g / (|g| + eps)
+    want = np.array([1.0, -2.0, 0.5]) - 0.01 * g / (np.abs(g) + 1e-8)
+    assert np.allclose(theta, want, atol=1e-15)
+
+
+def test_mlp_features_affine_element():
+    mesh = W.box_mesh((2, 2, 2), (0.0, 0.0, 0.0), (1.0, 2.0, 1.0), 3)
+    orc = oracle.Oracle(mesh.as_dict())
+    rng = np.random.default_rng(20)
+    for _ in range(5):
+        e = int(rng.integers(mesh.nelem))
+        xi = rng.uniform(-1, 1, 3)
+        x, _ = _straight(mesh, e, xi)
+        f = orc.mlp_features(e, x)
+        assert np.allclose(f[:3], xi, atol=1e-14)
+        assert np.abs(f[3:]).max() < 1e-13
