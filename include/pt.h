@@ -1,0 +1,257 @@
+/*
+ * pt.h -- C ABI of libpt, a single-GPU (GB300, sm_103a) implementation of the
+ * per-particle push of a high-order DG point-particle solver, after Kopper,
+ * Schwarz et al., "A framework for high-fidelity particle tracking on
+ * massively parallel systems" (arXiv 2211.05458).
+ *
+ * Conventions used by every entry point
+ *   - All pointers are plain host or device pointers as stated per argument;
+ *     no CUDA or framework types cross the boundary (streams are void*).
+ *   - Device arrays are caller-owned unless stated otherwise and must stay
+ *     valid until the work queued on the context's stream has finished.
+ *   - Every call returns a pt_status; no exception or abort crosses the ABI.
+ *     On error pt_last_error() returns a message for the context (or for the
+ *     failed pt_init_mesh when called with NULL).
+ *   - Work is queued on the context's stream; a call synchronises only where
+ *     it says so (reading statistics back, the *_host variants).
+ *   - Particle arrays are structure-of-arrays: a vector quantity of n
+ *     particles is 3 contiguous component arrays, x[0..n), x[n..2n), x[2n..3n).
+ */
+#ifndef PT_H
+#define PT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pt_ctx pt_ctx;
+
+typedef enum {
+  PT_OK = 0,
+  PT_ERR_ARG = 1,      /* invalid argument, nothing was queued              */
+  PT_ERR_CUDA = 2,     /* a CUDA call failed (message in pt_last_error)     */
+  PT_ERR_NEWTON = 3,   /* some particles' inverse map did not converge      */
+  PT_ERR_LOST = 4,     /* some particles ended outside their element        */
+  PT_ERR_CROSS = 5,    /* some particles hit the face-crossing cap          */
+  PT_ERR_TIMEOUT = 6,  /* reserved: a bounded device wait gave up           */
+  PT_ERR_STATE = 7,    /* call order violated (e.g. push before set_fluid)  */
+  PT_WARN_DT = 16      /* dt > 2.75 tau_p for some particle (two-way limit) */
+} pt_status;
+
+/* per-particle status bits (pt_particles.status) */
+enum {
+  PT_ST_NEWTON_FAIL = 1u << 0, /* inverse map failed: particle frozen      */
+  PT_ST_LOST = 1u << 1,        /* xi outside the element: particle frozen  */
+  PT_ST_CROSS_CAP = 1u << 2,   /* crossing cap reached: particle frozen    */
+  PT_ST_NEAR_FACE = 1u << 3,   /* came within the near-face band           */
+  PT_ST_REP800 = 1u << 4,      /* Re_p >= 800 seen (drag law out of range)  */
+  PT_ST_OPEN = 1u << 5         /* left through an open boundary: frozen    */
+};
+
+/* boundary kinds (pt_mesh_desc.bc) */
+enum { PT_BC_INTERNAL = 0, PT_BC_WALL = 1, PT_BC_PERIODIC = 2, PT_BC_OPEN = 3 };
+
+typedef enum { PT_FP64 = 0, PT_FP32 = 1 } pt_precision;
+typedef enum { PT_DRAG_STOKES = 0, PT_DRAG_SCHILLER_NAUMANN = 1 } pt_drag_law;
+typedef enum { PT_GUESS_TRILINEAR = 0, PT_GUESS_MLP = 1 } pt_guess;
+typedef enum { PT_DEPOSIT_ATOMIC = 0, PT_DEPOSIT_SEGMENTED = 1 } pt_deposit_mode;
+
+/* Mesh of curved hexahedra (Sec. 3.1, Eq. dgsem_curvedfaces).  All arrays are
+ * host memory, read during pt_init_mesh and copied; the caller keeps ownership.
+ *   xgeo     [nelem][(ngeo+1)^3][3]  geometry nodes, node (a,b,c) at index
+ *                                    a + g*(b + g*c), g = ngeo+1, on
+ *                                    equidistant reference points in [-1,1]
+ *   neighbor [nelem][6]   element across local face f (-1 on walls / open)
+ *   nbr_face [nelem][6]   that element's local index of the shared face
+ *   bc       [nelem][6]   PT_BC_* of face f
+ *   shift    [nelem][6][3] translation added to a particle crossing a
+ *                          periodic face (ignored for other kinds)
+ * Local faces: 0: xi1=-1, 1: xi1=+1, 2: xi2=-1, 3: xi2=+1, 4: xi3=-1, 5: xi3=+1;
+ * face parameters (s,t) run along the two free reference directions in order. */
+typedef struct {
+  int32_t nelem;
+  int32_t ngeo;
+  const double* xgeo;
+  const int32_t* neighbor;
+  const int32_t* nbr_face;
+  const int32_t* bc;
+  const double* shift;
+} pt_mesh_desc;
+
+/* Run-time configuration.  pt_config_default() fills the documented defaults. */
+typedef struct {
+  double mu;            /* dynamic viscosity (default 1e-5)                        */
+  double rho_p;         /* particle material density (default 1000)               */
+  double g[3];          /* gravity (default 0)                                     */
+  double drag_mask[3];  /* per-axis factor on the drag term (default 1,1,1)       */
+  double newton_tol;    /* |dxi|_inf convergence of the inverse map (1e-12)       */
+  double band_ref;      /* near-face band, reference units (1e-10)                */
+  double band_x;        /* near-face band, physical length (1e-10)                */
+  double lost_tol;      /* xi outside [-1-lost_tol, 1+lost_tol] => lost (1e-6)    */
+  int32_t precision;    /* pt_precision (default PT_FP64)                          */
+  int32_t drag_law;     /* pt_drag_law (default PT_DRAG_STOKES)                    */
+  int32_t guess;        /* pt_guess (default PT_GUESS_TRILINEAR)                   */
+  int32_t max_newton;   /* Newton iteration cap (default 50)                       */
+  int32_t max_cross;    /* face-crossing cap per RK stage (default 64)             */
+  int32_t rebin_every;  /* steps between particle re-binning; 0 = library choice   */
+  int32_t block;        /* threads per block of the push kernel; 0 = autotuned    */
+  int32_t reserved[9];
+} pt_config;
+
+/* Particles, structure of arrays, all device memory, caller-owned, updated in
+ * place by pt_push.  Floating-point arrays marked "real" are double in
+ * PT_FP64 mode and float in PT_FP32 mode; positions are always double.
+ *   n       number of particles (>= 0)
+ *   x       double [3][n] positions (in/out)
+ *   v       real   [3][n] velocities (in/out)
+ *   d       real   [n]    diameters (in)
+ *   elem    int32  [n]    owning element (in/out; must own x on entry)
+ *   hits    int32  [n]    wall-impact counters (in/out)
+ *   status  uint32 [n]    PT_ST_* bits (in/out; frozen particles are skipped) */
+typedef struct {
+  int64_t n;
+  double* x;
+  void* v;
+  const void* d;
+  int32_t* elem;
+  int32_t* hits;
+  uint32_t* status;
+} pt_particles;
+
+/* Totals over one pt_push call (host struct). */
+typedef struct {
+  int64_t particle_steps;   /* live particles x steps                        */
+  int64_t crossings;        /* internal + periodic face crossings            */
+  int64_t wall_hits;        /* specular reflections                          */
+  int64_t newton_it_fp32;   /* FP32 Newton iterations (FP32 mode)            */
+  int64_t newton_it_fp64;   /* FP64 Newton iterations / refinements          */
+  int64_t slow_track;       /* stage segments that needed face intersection  */
+  int64_t near_face;        /* particles with PT_ST_NEAR_FACE set at the end */
+  int64_t newton_fail;      /* particles frozen by each cause, at the end    */
+  int64_t lost;
+  int64_t cross_cap;
+  int64_t open;
+  int64_t rep800;
+  int64_t dt_warn;          /* particles with dt > 2.75 tau_p                */
+  int64_t reserved[3];
+} pt_stats;
+
+/* Fills *cfg with the defaults listed in pt_config. */
+void pt_config_default(pt_config* cfg);
+
+/* Creates a context on the current CUDA device: copies the mesh to the GPU and
+ * builds the per-face tables (face kind by bounding box, Sec. 3.2.4; bilinear
+ * coefficients; bounding slabs), the element centres and trilinear start
+ * tables.  stream: cudaStream_t used for all later work (NULL = default).
+ * Returns PT_ERR_ARG for inconsistent connectivity (a neighbour that does not
+ * point back, an out-of-range element or face index, a non-periodic face with
+ * a shift, unsupported ngeo (1..4)).  *ctx is NULL on error. */
+pt_status pt_init_mesh(pt_ctx** ctx, const pt_mesh_desc* mesh, const pt_config* cfg,
+                       void* stream);
+
+/* Replaces the configuration (same rules as at init). */
+pt_status pt_set_config(pt_ctx* ctx, const pt_config* cfg);
+
+/* Registers the fluid state (Sec. 3.1, Eq. dgsem_interpolation): N in 1..7,
+ * node_type 0 = Legendre-Gauss, 1 = Legendre-Gauss-Lobatto,
+ * U_dev [nelem][5][(N+1)^3] device array of (rho, rho u1, rho u2, rho u3,
+ * rho e) with node (i,j,k) at i + n*(j + n*k); double in PT_FP64 mode, float
+ * in PT_FP32 mode.  Caller-owned; read by every later push / deposit. */
+pt_status pt_set_fluid(pt_ctx* ctx, int32_t N, int32_t node_type, const void* U_dev);
+
+/* Advances every live particle by nsteps steps of the 5-stage, 4th-order
+ * low-storage RK scheme of Carpenter & Kennedy (Sec. 3.1) with time step dt.
+ * Per stage and particle (Sec. 3.2): inverse map x -> xi by Newton, tensor-
+ * product interpolation of rho and rho u at xi (Eq. part_interpolation),
+ * drag (Eqs. dragforce, dragfactor) plus gravity, the RK update of x and v,
+ * and tracking of the straight stage segment (Eq. parttrajectory) through
+ * element faces with specular reflection at walls (Sec. 2.4), periodic
+ * translation and removal at open faces.
+ * out: host pointer or NULL; when non-NULL the call synchronises the stream
+ * and fills the totals.  Returns PT_OK, or (only when out != NULL) the first
+ * of PT_ERR_NEWTON / PT_ERR_LOST / PT_ERR_CROSS whose count is non-zero, or
+ * PT_WARN_DT.  Particle order is preserved; the library bins particles by
+ * element internally. */
+pt_status pt_push(pt_ctx* ctx, const pt_particles* p, int32_t nsteps, double dt,
+                  pt_stats* out);
+
+/* As pt_push, but the particle arrays are HOST memory (same layout); the
+ * library stages them through its own device buffers, copies the results
+ * back and synchronises.  Intended for callers without device buffers. */
+pt_status pt_push_host(pt_ctx* ctx, const pt_particles* p_host, int32_t nsteps, double dt,
+                       pt_stats* out);
+
+/* Two-way coupling source (Sec. 2.3, Eq. theory:source) with Lagrange-basis
+ * weights: each live particle's drag F = m_p f_D (u - v) / tau_p contributes
+ * momentum -F and energy -F.v_p, spread over the nodes of its element with
+ * weights l_i(xi1) l_j(xi2) l_k(xi3).  S_dev [nelem][4][(N+1)^3] float, device,
+ * caller-owned, overwritten.  mode PT_DEPOSIT_ATOMIC adds with FP32 atomics
+ * (order-dependent rounding); PT_DEPOSIT_SEGMENTED sums each element's
+ * particles in index order (bitwise reproducible). */
+pt_status pt_deposit(pt_ctx* ctx, const pt_particles* p, int32_t mode, float* S_dev);
+
+/* Inverse map only (Sec. 3.2.1): for each i, xi of x[:,i] in element elem[i].
+ * x_dev double [3][n], elem_dev int32 [n], xi_dev double [3][n] out,
+ * iters_dev int32 [n] out (Newton iterations, FP32 + FP64), status_dev uint32
+ * [n] out (PT_ST_NEWTON_FAIL on failure).  Uses the context's precision and
+ * guess mode.  All device, caller-owned. */
+pt_status pt_locate(pt_ctx* ctx, int64_t n, const double* x_dev, const int32_t* elem_dev,
+                    double* xi_dev, int32_t* iters_dev, uint32_t* status_dev);
+
+/* Learned initial guess (no counterpart in the paper).  A 51-64-64-64-3 GELU
+ * network maps [xi_tri (3), 48 geometry deviations] to a correction of the
+ * trilinear Newton start; see pt_mlp_features for the inputs (ngeo = 3 only).
+ *
+ * pt_mlp_make_pairs: n training pairs on the device.  Elements and reference
+ * points are drawn by a counter-based generator from seed; x = chi(xi) and the
+ * label xi comes from the FP64 Newton inverse.  in_dev float [n][51] (raw
+ * features), target_dev float [n][3] (xi_newton - xi_tri).
+ * pt_mlp_train: Adam (lr, beta1 0.9, beta2 0.999, eps 1e-8) on the MSE, batch
+ * rows per step, epochs passes in an order drawn from seed; inputs are
+ * standardised by statistics taken from in_dev and targets scaled by their
+ * rms.  loss_host: host float[epochs] mean loss per epoch, or NULL.
+ * Synchronises.  After training the BF16 copy used by the push is refreshed. */
+pt_status pt_mlp_make_pairs(pt_ctx* ctx, int64_t n, uint64_t seed, float* in_dev,
+                            float* target_dev);
+pt_status pt_mlp_train(pt_ctx* ctx, int64_t n, const float* in_dev, const float* target_dev,
+                       int32_t epochs, int32_t batch, float lr, uint64_t seed, float* loss_host);
+/* Raw features of x in elem (same definition as the learned guess uses):
+ * x_dev double [3][n], elem_dev int32 [n], feat_dev float [n][51]. */
+pt_status pt_mlp_features(pt_ctx* ctx, int64_t n, const double* x_dev, const int32_t* elem_dev,
+                          float* feat_dev);
+/* Network parameters as one flat float array (11843 values: W1[64][51], b1,
+ * W2[64][64], b2, W3[64][64], b3, W4[3][64], b4) plus the normalisation
+ * (in_mean[51], in_std[51], out_scale[3]).  Host pointers.  set refreshes the
+ * BF16 copy. */
+int32_t pt_mlp_nparams(void);
+pt_status pt_mlp_set(pt_ctx* ctx, const float* theta_host, const float* norm_host);
+pt_status pt_mlp_get(pt_ctx* ctx, float* theta_host, float* norm_host);
+/* FP32 forward pass and loss gradient of the network on already-normalised
+ * inputs (the kernels training uses): in_dev float [B][51], out_dev [B][3];
+ * grad_dev float [11843] overwritten with d(mean squared error)/d theta for
+ * targets target_dev [B][3]; loss_host receives the loss (synchronises). */
+pt_status pt_mlp_forward(pt_ctx* ctx, int32_t B, const float* in_dev, float* out_dev);
+pt_status pt_mlp_grad(pt_ctx* ctx, int32_t B, const float* in_dev, const float* target_dev,
+                      float* grad_dev, float* loss_host);
+
+/* Batched push: nbox independent contexts (PT_FP32, ngeo = 1, N in 3..7),
+ * each with its own particles, advanced by one persistent launch per step
+ * chunk; the sequence is captured once per (nbox, nsteps) in a CUDA graph on
+ * ctxs[0]'s stream.  out: host array of nbox pt_stats or NULL (synchronises). */
+pt_status pt_push_batch(pt_ctx* const* ctxs, const pt_particles* parts, int32_t nbox,
+                        int32_t nsteps, double dt, pt_stats* out);
+
+/* Releases the context and its device memory (not the caller's arrays). */
+pt_status pt_destroy(pt_ctx* ctx);
+
+/* Last error message of ctx (or of the last failed pt_init_mesh if ctx is
+ * NULL); never NULL. */
+const char* pt_last_error(const pt_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PT_H */

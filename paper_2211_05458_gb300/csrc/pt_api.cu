@@ -1,0 +1,853 @@
+// pt_api.cu -- the C ABI of libpt (include/pt.h): context life cycle, mesh
+// preprocessing on the host, and the launch sequences of push / locate /
+// deposit.  Host-side preprocessing follows Sec. 3.2.4 of arXiv 2211.05458
+// (face kind by bounding-box flatness, Bezier control points for bounds).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pt.h"
+#include "pt_bin.h"
+#include "pt_ctx.h"
+#include "pt_internal.h"
+
+namespace pt {
+int fam_g2_fp64_push(int, const PushArgs&, int, int, void*);
+int fam_g2_fp32_push(int, const PushArgs&, int, int, void*);
+int fam_g3_fp64_push(int, const PushArgs&, int, int, void*);
+int fam_g3_fp32_push(int, const PushArgs&, int, int, void*);
+int fam_g4_fp64_push(int, const PushArgs&, int, int, void*);
+int fam_g4_fp32_push(int, const PushArgs&, int, int, void*);
+int fam_g2_fp64_dep(int, int, const DepositArgs&, int, int, void*);
+int fam_g2_fp32_dep(int, int, const DepositArgs&, int, int, void*);
+int fam_g3_fp64_dep(int, int, const DepositArgs&, int, int, void*);
+int fam_g3_fp32_dep(int, int, const DepositArgs&, int, int, void*);
+int fam_g4_fp64_dep(int, int, const DepositArgs&, int, int, void*);
+int fam_g4_fp32_dep(int, int, const DepositArgs&, int, int, void*);
+int fam_g2_fp64_occ(int, int);
+int fam_g2_fp32_occ(int, int);
+int fam_g3_fp64_occ(int, int);
+int fam_g3_fp32_occ(int, int);
+int fam_g4_fp64_occ(int, int);
+int fam_g4_fp32_occ(int, int);
+int fam_g2_fp64_loc(const LocateArgs&, int, int, void*);
+int fam_g2_fp32_loc(const LocateArgs&, int, int, void*);
+int fam_g3_fp64_loc(const LocateArgs&, int, int, void*);
+int fam_g3_fp32_loc(const LocateArgs&, int, int, void*);
+int fam_g4_fp64_loc(const LocateArgs&, int, int, void*);
+int fam_g4_fp32_loc(const LocateArgs&, int, int, void*);
+
+#define PT_DISPATCH(g, f64, SUFFIX, ...)                                          \
+  ((g) == 2 ? ((f64) ? fam_g2_fp64_##SUFFIX(__VA_ARGS__) : fam_g2_fp32_##SUFFIX(__VA_ARGS__)) \
+   : (g) == 3 ? ((f64) ? fam_g3_fp64_##SUFFIX(__VA_ARGS__) : fam_g3_fp32_##SUFFIX(__VA_ARGS__)) \
+   : ((f64) ? fam_g4_fp64_##SUFFIX(__VA_ARGS__) : fam_g4_fp32_##SUFFIX(__VA_ARGS__)))
+
+int launch_push(int g, bool f64, int np, const PushArgs& a, int grid, int block, void* s) {
+  return PT_DISPATCH(g, f64, push, np, a, grid, block, s);
+}
+int launch_deposit(int g, bool f64, int np, int mode, const DepositArgs& a, int grid, int block,
+                   void* s) {
+  return PT_DISPATCH(g, f64, dep, np, mode, a, grid, block, s);
+}
+int max_active_push(int g, bool f64, int np, int block) {
+  return PT_DISPATCH(g, f64, occ, np, block);
+}
+int launch_locate(int g, bool f64, int np, const LocateArgs& a, int grid, int block, void* s) {
+  (void)np;
+  return PT_DISPATCH(g, f64, loc, a, grid, block, s);
+}
+}  // namespace pt
+
+using namespace pt;
+
+static thread_local std::string g_init_err = "no error";
+
+static pt_status fail(pt_ctx* c, pt_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c)
+    c->err = buf;
+  else
+    g_init_err = buf;
+  return st;
+}
+
+#define CK(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return fail(c, PT_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                  __FILE__, __LINE__);                                               \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// node sets (host): Legendre-Gauss, Gauss-Lobatto, equidistant; barycentric weights
+// ---------------------------------------------------------------------------
+
+// P_n and P_n' at x by the three-term recurrence
+static void legendre_pd(int n, double x, double* p, double* dp) {
+  double a = 1.0, b = x, da = 0.0, db = 1.0;
+  if (n == 0) {
+    *p = 1.0;
+    *dp = 0.0;
+    return;
+  }
+  for (int k = 2; k <= n; ++k) {
+    double c = ((2 * k - 1) * x * b - (k - 1) * a) / k;
+    double dc = da + (2 * k - 1) * b;  // P_k' = P_{k-2}' + (2k-1) P_{k-1}
+    a = b;
+    b = c;
+    da = db;
+    db = dc;
+  }
+  *p = b;
+  *dp = db;
+}
+
+static void solution_nodes(int kind, int n, double* x) {
+  if (n == 1) {
+    x[0] = 0.0;
+    return;
+  }
+  const double pi = 3.14159265358979323846;
+  if (kind == 0) {
+    for (int i = 0; i < n; ++i) {
+      double z = -std::cos(pi * (4 * i + 3) / (4 * n + 2));
+      for (int it = 0; it < 60; ++it) {
+        double p, dp;
+        legendre_pd(n, z, &p, &dp);
+        double dz = p / dp;
+        z -= dz;
+        if (std::fabs(dz) <= 1e-17) break;
+      }
+      x[i] = z;
+    }
+  } else {
+    // Gauss-Lobatto: endpoints and the zeros of P_{n-1}' (Newton with the
+    // second derivative from Legendre's differential equation)
+    int N = n - 1;
+    x[0] = -1.0;
+    x[N] = 1.0;
+    for (int i = 1; i < N; ++i) {
+      double z = -std::cos(pi * i / N);
+      for (int it = 0; it < 60; ++it) {
+        double p, dp;
+        legendre_pd(N, z, &p, &dp);
+        double d2 = (2 * z * dp - N * (N + 1) * p) / (1 - z * z);
+        double dz = dp / d2;
+        z -= dz;
+        if (std::fabs(dz) <= 1e-17) break;
+      }
+      x[i] = z;
+    }
+  }
+  std::sort(x, x + n);
+}
+
+static void bary(int n, const double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double p = 1.0;
+    for (int m = 0; m < n; ++m)
+      if (m != i) p *= (x[i] - x[m]);
+    w[i] = 1.0 / p;
+  }
+}
+
+// 5-stage 4th-order 2N-storage Runge-Kutta (Carpenter & Kennedy, NASA TM-109112)
+static const double kRK_A[5] = {0.0, -567301805773.0 / 1357537059087.0,
+                                -2404267990393.0 / 2016746695238.0,
+                                -3550918686646.0 / 2091501179385.0,
+                                -1275806237668.0 / 842570457699.0};
+static const double kRK_B[5] = {1432997174477.0 / 9575080441755.0,
+                                5161836677717.0 / 13612068292357.0,
+                                1720146321549.0 / 2090206949498.0,
+                                3134564353537.0 / 4481467310338.0,
+                                2277821191437.0 / 14882151754819.0};
+
+// ---------------------------------------------------------------------------
+// mesh preprocessing
+// ---------------------------------------------------------------------------
+
+static int face_node_h(int g, int f, int mm, int kk) {
+  int fixed = (f & 1) ? g - 1 : 0;
+  switch (f >> 1) {
+    case 0: return fixed + g * (mm + g * kk);
+    case 1: return mm + g * (fixed + g * kk);
+    default: return mm + g * (kk + g * fixed);
+  }
+}
+
+// inverse of the Bernstein-Vandermonde matrix on equidistant nodes:
+// Bezier control values = M * nodal values
+static void bezier_matrix(int g, std::vector<double>& M) {
+  int p = g - 1;
+  std::vector<double> V(g * g), I(g * g, 0.0);
+  for (int j = 0; j < g; ++j) {
+    double u = p ? (double)j / p : 0.0;
+    for (int k = 0; k < g; ++k) {
+      double bin = 1.0;
+      for (int q = 1; q <= k; ++q) bin = bin * (p - k + q) / q;
+      V[j * g + k] = bin * std::pow(u, k) * std::pow(1.0 - u, p - k);
+    }
+    I[j * g + j] = 1.0;
+  }
+  // Gauss-Jordan
+  for (int c = 0; c < g; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < g; ++r)
+      if (std::fabs(V[r * g + c]) > std::fabs(V[piv * g + c])) piv = r;
+    for (int q = 0; q < g; ++q) {
+      std::swap(V[c * g + q], V[piv * g + q]);
+      std::swap(I[c * g + q], I[piv * g + q]);
+    }
+    double d = V[c * g + c];
+    for (int q = 0; q < g; ++q) {
+      V[c * g + q] /= d;
+      I[c * g + q] /= d;
+    }
+    for (int r = 0; r < g; ++r)
+      if (r != c) {
+        double f = V[r * g + c];
+        for (int q = 0; q < g; ++q) {
+          V[r * g + q] -= f * V[c * g + q];
+          I[r * g + q] -= f * I[c * g + q];
+        }
+      }
+  }
+  M = I;
+}
+
+static bool inv3h(const double* J, double* Ji) {
+  double c00 = J[4] * J[8] - J[5] * J[7], c01 = J[5] * J[6] - J[3] * J[8],
+         c02 = J[3] * J[7] - J[4] * J[6];
+  double det = J[0] * c00 + J[1] * c01 + J[2] * c02;
+  if (!(std::fabs(det) > 0)) return false;
+  double id = 1.0 / det;
+  Ji[0] = c00 * id;
+  Ji[1] = (J[2] * J[7] - J[1] * J[8]) * id;
+  Ji[2] = (J[1] * J[5] - J[2] * J[4]) * id;
+  Ji[3] = c01 * id;
+  Ji[4] = (J[0] * J[8] - J[2] * J[6]) * id;
+  Ji[5] = (J[2] * J[3] - J[0] * J[5]) * id;
+  Ji[6] = c02 * id;
+  Ji[7] = (J[1] * J[6] - J[0] * J[7]) * id;
+  Ji[8] = (J[0] * J[4] - J[1] * J[3]) * id;
+  return true;
+}
+
+template <typename T>
+static T* dmalloc(pt_ctx* c, size_t n, cudaError_t* err) {
+  void* p = nullptr;
+  *err = cudaMalloc(&p, n * sizeof(T) + 16);
+  if (*err == cudaSuccess) c->allocs.push_back(p);
+  return (T*)p;
+}
+
+static pt_status upload_mesh(pt_ctx* c, const pt_mesh_desc* md) {
+  const int E = md->nelem, g = md->ngeo + 1, g3 = g * g * g;
+  c->nelem = E;
+  c->ngeo = md->ngeo;
+  c->g = g;
+  std::vector<double> xg64((size_t)E * g3 * 3), ce((size_t)E * 3), bil((size_t)E * 72),
+      shift((size_t)E * 18);
+  std::vector<float> xg32((size_t)E * g3 * 3), tri((size_t)E * 12), slab((size_t)E * 48, 0.f);
+  std::vector<int> fnbr((size_t)E * 6), finfo((size_t)E * 6);
+  std::vector<double> M;
+  bezier_matrix(g, M);
+  const double bx = c->cfg.band_x;
+  int ncurved = 0;
+  for (int e = 0; e < E; ++e) {
+    const double* X = md->xgeo + (size_t)e * g3 * 3;
+    double cr[8][3], cc[3] = {0, 0, 0};
+    for (int q = 0; q < 8; ++q) {
+      int a = (q & 1) ? g - 1 : 0, b = (q & 2) ? g - 1 : 0, cz = (q & 4) ? g - 1 : 0;
+      for (int r = 0; r < 3; ++r) {
+        cr[q][r] = X[3 * (a + g * (b + g * cz)) + r];
+        cc[r] += cr[q][r] / 8.0;
+      }
+    }
+    double Rmax = 0.0;
+    for (int q = 0; q < g3; ++q)
+      for (int r = 0; r < 3; ++r) {
+        double v = X[3 * q + r] - cc[r];
+        xg64[((size_t)e * g3 + q) * 3 + r] = v;
+        xg32[(size_t)e * 3 * g3 + r * g3 + q] = (float)v;
+        Rmax = std::max(Rmax, std::fabs(v));
+      }
+    for (int r = 0; r < 3; ++r) ce[3 * e + r] = cc[r];
+    // trilinear start table
+    double Jc[9] = {0}, Ji[9];
+    for (int q = 0; q < 8; ++q)
+      for (int r = 0; r < 3; ++r)
+        for (int d = 0; d < 3; ++d) Jc[3 * r + d] += ((q >> d) & 1 ? 1.0 : -1.0) * cr[q][r] / 8.0;
+    if (!inv3h(Jc, Ji))
+      return fail(nullptr, PT_ERR_ARG, "element %d: degenerate corner Jacobian", e);
+    for (int r = 0; r < 3; ++r) tri[12 * e + r] = 0.f;
+    for (int q = 0; q < 9; ++q) tri[12 * e + 3 + q] = (float)Ji[q];
+    // faces
+    for (int f = 0; f < 6; ++f) {
+      const int k6 = 6 * e + f;
+      int bc = md->bc[k6];
+      int nb = md->neighbor[k6], nf = md->nbr_face[k6];
+      if (bc < 0 || bc > 3) return fail(nullptr, PT_ERR_ARG, "element %d face %d: bad bc %d", e, f, bc);
+      if (bc == PT_BC_INTERNAL || bc == PT_BC_PERIODIC) {
+        if (nb < 0 || nb >= E || nf < 0 || nf > 5)
+          return fail(nullptr, PT_ERR_ARG, "element %d face %d: bad neighbour %d/%d", e, f, nb, nf);
+        if (md->neighbor[6 * nb + nf] != e || md->nbr_face[6 * nb + nf] != f)
+          return fail(nullptr, PT_ERR_ARG, "element %d face %d: neighbour %d does not point back", e,
+                      f, nb);
+      } else {
+        nb = -1;
+        nf = 0;
+      }
+      for (int r = 0; r < 3; ++r) {
+        double sv = md->shift[18 * e + 3 * f + r];
+        if (bc != PT_BC_PERIODIC && sv != 0.0)
+          return fail(nullptr, PT_ERR_ARG, "element %d face %d: shift on a non-periodic face", e, f);
+        shift[18 * e + 3 * f + r] = bc == PT_BC_PERIODIC ? sv : 0.0;
+      }
+      // face nodes (local coords)
+      std::vector<double> P(g * g * 3);
+      for (int kk = 0; kk < g; ++kk)
+        for (int mm = 0; mm < g; ++mm)
+          for (int r = 0; r < 3; ++r)
+            P[3 * (mm + g * kk) + r] =
+                xg64[((size_t)e * g3 + face_node_h(g, f, mm, kk)) * 3 + r];
+      const double* P00 = &P[0];
+      const double* P10 = &P[3 * (g - 1)];
+      const double* P01 = &P[3 * g * (g - 1)];
+      const double* P11 = &P[3 * (g - 1 + g * (g - 1))];
+      double* Bf = &bil[72 * (size_t)e + 12 * f];
+      for (int r = 0; r < 3; ++r) {
+        Bf[r] = 0.25 * (P00[r] - P10[r] - P01[r] + P11[r]);
+        Bf[3 + r] = 0.25 * (-P00[r] + P10[r] - P01[r] + P11[r]);
+        Bf[6 + r] = 0.25 * (-P00[r] - P10[r] + P01[r] + P11[r]);
+        Bf[9 + r] = 0.25 * (P00[r] + P10[r] + P01[r] + P11[r]);
+      }
+      // kind: bilinear if every face node lies on the bilinear patch
+      double dev = 0.0, amax = 0.0;
+      for (int kk = 0; kk < g; ++kk)
+        for (int mm = 0; mm < g; ++mm) {
+          double s = g > 1 ? -1.0 + 2.0 * mm / (g - 1) : 0.0;
+          double t = g > 1 ? -1.0 + 2.0 * kk / (g - 1) : 0.0;
+          for (int r = 0; r < 3; ++r) {
+            double b = Bf[r] * s * t + Bf[3 + r] * s + Bf[6 + r] * t + Bf[9 + r];
+            dev = std::max(dev, std::fabs(P[3 * (mm + g * kk) + r] - b));
+          }
+        }
+      for (int r = 0; r < 3; ++r) amax = std::max(amax, std::fabs(Bf[r]));
+      int kind = dev <= 1e-13 * Rmax ? (amax <= 1e-13 * Rmax ? PT_FACE_PLANAR : PT_FACE_BILINEAR)
+                                     : PT_FACE_CURVED;
+      ncurved += kind == PT_FACE_CURVED;
+      fnbr[k6] = nb;
+      finfo[k6] = bc | (kind << 2) | (nf << 4);
+      // slab: centre normal b x c rounded to FP32, range over the Bezier
+      // control points (their convex hull contains the face), widened
+      double nrm[3] = {Bf[4] * Bf[8] - Bf[5] * Bf[7], Bf[5] * Bf[6] - Bf[3] * Bf[8],
+                       Bf[3] * Bf[7] - Bf[4] * Bf[6]};
+      double nn = std::sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+      if (!(nn > 0)) return fail(nullptr, PT_ERR_ARG, "element %d face %d: degenerate face", e, f);
+      float nf32[3];
+      for (int r = 0; r < 3; ++r) {
+        nf32[r] = (float)(nrm[r] / nn);
+        nrm[r] = nf32[r];
+      }
+      double lo = 1e300, hi = -1e300;
+      for (int km = 0; km < g; ++km)
+        for (int kt = 0; kt < g; ++kt) {
+          double cp[3] = {0, 0, 0};
+          for (int mm = 0; mm < g; ++mm)
+            for (int kk = 0; kk < g; ++kk)
+              for (int r = 0; r < 3; ++r)
+                cp[r] += M[km * g + mm] * M[kt * g + kk] * P[3 * (mm + g * kk) + r];
+          double pr = nrm[0] * cp[0] + nrm[1] * cp[1] + nrm[2] * cp[2];
+          lo = std::min(lo, pr);
+          hi = std::max(hi, pr);
+        }
+      double margin = bx + 4e-6 * Rmax + 1e-12;
+      float* S = &slab[48 * (size_t)e + 8 * f];
+      S[0] = nf32[0];
+      S[1] = nf32[1];
+      S[2] = nf32[2];
+      S[3] = (float)(lo - margin);
+      S[4] = (float)(hi + margin);
+      S[5] = (float)Rmax;
+    }
+  }
+  c->ncurved = ncurved;
+  cudaError_t err;
+  pt_ctx* cc = c;
+  c->d_xg64 = dmalloc<double>(cc, xg64.size(), &err);
+  if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
+  c->d_xg32 = dmalloc<float>(cc, xg32.size(), &err);
+  if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
+  c->d_ce = dmalloc<double>(cc, ce.size(), &err);
+  if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
+  c->d_tri = dmalloc<float>(cc, tri.size(), &err);
+  if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
+  c->d_fnbr = dmalloc<int>(cc, fnbr.size(), &err);
+  if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
+  c->d_finfo = dmalloc<int>(cc, finfo.size(), &err);
+  if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
+  c->d_slab = dmalloc<float>(cc, slab.size(), &err);
+  if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
+  c->d_bil = dmalloc<double>(cc, bil.size(), &err);
+  if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
+  c->d_shift = dmalloc<double>(cc, shift.size(), &err);
+  if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
+  c->d_stats = dmalloc<unsigned long long>(cc, PT_C_COUNT, &err);
+  if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
+  struct {
+    void* d;
+    const void* h;
+    size_t b;
+  } cp[] = {{c->d_xg64, xg64.data(), xg64.size() * 8}, {c->d_xg32, xg32.data(), xg32.size() * 4},
+            {c->d_ce, ce.data(), ce.size() * 8},       {c->d_tri, tri.data(), tri.size() * 4},
+            {c->d_fnbr, fnbr.data(), fnbr.size() * 4}, {c->d_finfo, finfo.data(), finfo.size() * 4},
+            {c->d_slab, slab.data(), slab.size() * 4}, {c->d_bil, bil.data(), bil.size() * 8},
+            {c->d_shift, shift.data(), shift.size() * 8}};
+  for (auto& q : cp) {
+    err = cudaMemcpy(q.d, q.h, q.b, cudaMemcpyHostToDevice);
+    if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMemcpy: %s", cudaGetErrorString(err));
+  }
+  return PT_OK;
+}
+
+static void fill_consts(const pt_ctx* c, DevConsts& k) {
+  std::memset(&k, 0, sizeof k);
+  double gn[PT_MAXG], gw[PT_MAXG];
+  for (int a = 0; a < c->g; ++a) gn[a] = c->g > 1 ? -1.0 + 2.0 * a / (c->g - 1) : 0.0;
+  bary(c->g, gn, gw);
+  for (int a = 0; a < c->g; ++a) {
+    k.gn[a] = gn[a];
+    k.gw[a] = gw[a];
+    k.gn32[a] = (float)gn[a];
+    k.gw32[a] = (float)gw[a];
+  }
+  for (int i = 0; i < c->N + 1 && c->N >= 0; ++i) {
+    k.sn[i] = c->sn[i];
+    k.sw[i] = c->sw[i];
+    k.sn32[i] = (float)c->sn[i];
+    k.sw32[i] = (float)c->sw[i];
+  }
+  for (int i = 0; i < 5; ++i) {
+    k.A[i] = kRK_A[i];
+    k.B[i] = kRK_B[i];
+    k.A32[i] = (float)kRK_A[i];
+    k.B32[i] = (float)kRK_B[i];
+  }
+  k.mu = c->cfg.mu;
+  k.rho_p = c->cfg.rho_p;
+  for (int r = 0; r < 3; ++r) {
+    k.g[r] = c->cfg.g[r];
+    k.mask[r] = c->cfg.drag_mask[r];
+  }
+  k.newton_tol = c->cfg.newton_tol;
+  k.band_ref = c->cfg.band_ref;
+  k.band_x = c->cfg.band_x;
+  k.lost_tol = c->cfg.lost_tol;
+  k.drag_law = c->cfg.drag_law;
+  k.max_newton = c->cfg.max_newton;
+  k.max_cross = c->cfg.max_cross;
+  k.guess = c->cfg.guess;
+}
+
+static DevMesh dev_mesh(const pt_ctx* c) {
+  DevMesh m;
+  m.nelem = c->nelem;
+  m.g = c->g;
+  m.xg64 = c->d_xg64;
+  m.xg32 = c->d_xg32;
+  m.ce = c->d_ce;
+  m.tri = c->d_tri;
+  m.fnbr = c->d_fnbr;
+  m.finfo = c->d_finfo;
+  m.slab = c->d_slab;
+  m.bil = c->d_bil;
+  m.shift = c->d_shift;
+  m.mlp_pre = c->d_mlp_pre;
+  return m;
+}
+
+DevMLP pt_dev_mlp(const pt_ctx* c);
+
+static pt_status check_config(const pt_config* cfg) {
+  if (!cfg) return fail(nullptr, PT_ERR_ARG, "config is NULL");
+  if (cfg->precision != PT_FP64 && cfg->precision != PT_FP32)
+    return fail(nullptr, PT_ERR_ARG, "precision must be PT_FP64 or PT_FP32");
+  if (cfg->drag_law != 0 && cfg->drag_law != 1) return fail(nullptr, PT_ERR_ARG, "bad drag_law");
+  if (cfg->guess != 0 && cfg->guess != 1) return fail(nullptr, PT_ERR_ARG, "bad guess");
+  if (!(cfg->mu > 0) || !(cfg->rho_p > 0)) return fail(nullptr, PT_ERR_ARG, "mu, rho_p must be > 0");
+  if (cfg->max_newton < 1 || cfg->max_cross < 1) return fail(nullptr, PT_ERR_ARG, "caps must be >= 1");
+  if (!(cfg->newton_tol > 0) || !(cfg->band_ref >= 0) || !(cfg->band_x >= 0) ||
+      !(cfg->lost_tol >= 0))
+    return fail(nullptr, PT_ERR_ARG, "bad tolerance");
+  if (cfg->block < 0 || cfg->block > 1024 || (cfg->block % 32))
+    return fail(nullptr, PT_ERR_ARG, "block must be a multiple of 32 in [0, 1024]");
+  if (cfg->rebin_every < 0) return fail(nullptr, PT_ERR_ARG, "rebin_every must be >= 0");
+  return PT_OK;
+}
+
+extern "C" {
+
+void pt_config_default(pt_config* cfg) {
+  std::memset(cfg, 0, sizeof *cfg);
+  cfg->mu = 1e-5;
+  cfg->rho_p = 1000.0;
+  cfg->drag_mask[0] = cfg->drag_mask[1] = cfg->drag_mask[2] = 1.0;
+  cfg->newton_tol = 1e-12;
+  cfg->band_ref = 1e-10;
+  cfg->band_x = 1e-10;
+  cfg->lost_tol = 1e-6;
+  cfg->precision = PT_FP64;
+  cfg->drag_law = PT_DRAG_STOKES;
+  cfg->guess = PT_GUESS_TRILINEAR;
+  cfg->max_newton = 50;
+  cfg->max_cross = 64;
+  cfg->rebin_every = 0;
+  cfg->block = 0;
+}
+
+pt_status pt_init_mesh(pt_ctx** out, const pt_mesh_desc* md, const pt_config* cfg, void* stream) {
+  if (!out) return fail(nullptr, PT_ERR_ARG, "ctx out-pointer is NULL");
+  *out = nullptr;
+  if (!md || !md->xgeo || !md->neighbor || !md->nbr_face || !md->bc || !md->shift)
+    return fail(nullptr, PT_ERR_ARG, "mesh descriptor or one of its arrays is NULL");
+  if (md->nelem <= 0) return fail(nullptr, PT_ERR_ARG, "nelem must be > 0");
+  if (md->ngeo < 1 || md->ngeo > 3) return fail(nullptr, PT_ERR_ARG, "ngeo must be 1..3");
+  if (md->nelem > (1 << 28)) return fail(nullptr, PT_ERR_ARG, "nelem too large");
+  pt_status s = check_config(cfg);
+  if (s) return s;
+  pt_ctx* c = new pt_ctx();
+  c->cfg = *cfg;
+  c->stream = (cudaStream_t)stream;
+  cudaGetDevice(&c->dev);
+  cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev);
+  s = upload_mesh(c, md);
+  if (s) {
+    pt_destroy(c);
+    return s;
+  }
+  *out = c;
+  return PT_OK;
+}
+
+pt_status pt_set_config(pt_ctx* c, const pt_config* cfg) {
+  if (!c) return fail(nullptr, PT_ERR_ARG, "ctx is NULL");
+  pt_status s = check_config(cfg);
+  if (s) {
+    c->err = g_init_err;
+    return s;
+  }
+  if (cfg->band_x != c->cfg.band_x)
+    return fail(c, PT_ERR_ARG, "band_x is fixed at init (it sizes the face slabs)");
+  c->cfg = *cfg;
+  return PT_OK;
+}
+
+pt_status pt_set_fluid(pt_ctx* c, int32_t N, int32_t node_type, const void* U) {
+  if (!c) return fail(nullptr, PT_ERR_ARG, "ctx is NULL");
+  if (N < 1 || N > 7) return fail(c, PT_ERR_ARG, "N must be 1..7");
+  if (node_type != 0 && node_type != 1) return fail(c, PT_ERR_ARG, "node_type must be 0 or 1");
+  if (!U) return fail(c, PT_ERR_ARG, "U is NULL");
+  c->N = N;
+  c->node_type = node_type;
+  c->U = U;
+  solution_nodes(node_type, N + 1, c->sn);
+  bary(N + 1, c->sn, c->sw);
+  return PT_OK;
+}
+
+}  // extern "C"
+
+// scratch for binning + permutation, grown on demand
+static pt_status ensure_scratch(pt_ctx* c, int64_t n) {
+  size_t need = bin_scratch_ints(c->nelem);
+  if (c->scratch_ints < need) {
+    if (c->d_scratch) cudaFree(c->d_scratch);
+    c->d_scratch = nullptr;
+    CK(cudaMalloc(&c->d_scratch, need * sizeof(int)));
+    c->scratch_ints = need;
+  }
+  if (c->perm_cap < n) {
+    if (c->d_perm) cudaFree(c->d_perm);
+    c->d_perm = nullptr;
+    CK(cudaMalloc(&c->d_perm, std::max<int64_t>(n, 1) * sizeof(int)));
+    c->perm_cap = n;
+  }
+  return PT_OK;
+}
+
+static int push_block(pt_ctx* c) { return c->cfg.block > 0 ? c->cfg.block : 128; }
+
+static int grid_for(pt_ctx* c, int64_t n, int block, int occ) {
+  int64_t want = (n + block - 1) / block;
+  int64_t cap = (int64_t)c->nsm * std::max(occ, 1);
+  return (int)std::max<int64_t>(1, std::min(want, cap));
+}
+
+__global__ void k_status_counts(const unsigned* st, int64_t n, unsigned long long* stats) {
+  unsigned long long a[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    unsigned s = st[i];
+    a[0] += (s & PT_ST_NEAR_FACE) != 0;
+    a[1] += (s & PT_ST_NEWTON_FAIL) != 0;
+    a[2] += (s & PT_ST_LOST) != 0;
+    a[3] += (s & PT_ST_CROSS_CAP) != 0;
+    a[4] += (s & PT_ST_OPEN) != 0;
+    a[5] += (s & PT_ST_REP800) != 0;
+  }
+  for (int q = 0; q < 6; ++q) {
+    unsigned long long v = a[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(stats + PT_C_NEAR + q, v);
+  }
+}
+
+template <typename R>
+__global__ void k_dt_check(const R* d, int64_t n, double lim, double rho_p, double mu,
+                           unsigned long long* stats) {
+  unsigned long long a = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double dd = (double)d[i];
+    double tau = rho_p * dd * dd / (18.0 * mu);
+    a += lim > 2.75 * tau;
+  }
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0 && a) atomicAdd(stats + PT_C_DTWARN, a);
+}
+
+static pt_status validate_particles(pt_ctx* c, const pt_particles* p) {
+  if (!p) return fail(c, PT_ERR_ARG, "particles is NULL");
+  if (p->n < 0 || p->n > (int64_t)INT32_MAX) return fail(c, PT_ERR_ARG, "bad particle count");
+  if (p->n > 0 && (!p->x || !p->v || !p->d || !p->elem || !p->hits || !p->status))
+    return fail(c, PT_ERR_ARG, "a particle array is NULL");
+  return PT_OK;
+}
+
+static pt_status read_stats(pt_ctx* c, const pt_particles* p, double dt, pt_stats* out) {
+  const int64_t n = p->n;
+  if (n > 0) {
+    int g = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->nsm * 8);
+    k_status_counts<<<g, 256, 0, c->stream>>>(p->status, n, c->d_stats);
+    if (c->cfg.precision == PT_FP64)
+      k_dt_check<double><<<g, 256, 0, c->stream>>>((const double*)p->d, n, dt, c->cfg.rho_p,
+                                                   c->cfg.mu, c->d_stats);
+    else
+      k_dt_check<float><<<g, 256, 0, c->stream>>>((const float*)p->d, n, dt, c->cfg.rho_p,
+                                                  c->cfg.mu, c->d_stats);
+  }
+  unsigned long long h[PT_C_COUNT];
+  CK(cudaMemcpyAsync(h, c->d_stats, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  std::memset(out, 0, sizeof *out);
+  out->particle_steps = (int64_t)h[PT_C_STEPS];
+  out->crossings = (int64_t)h[PT_C_CROSS];
+  out->wall_hits = (int64_t)h[PT_C_HITS];
+  out->newton_it_fp32 = (int64_t)h[PT_C_IT32];
+  out->newton_it_fp64 = (int64_t)h[PT_C_IT64];
+  out->slow_track = (int64_t)h[PT_C_SLOW];
+  out->near_face = (int64_t)h[PT_C_NEAR];
+  out->newton_fail = (int64_t)h[PT_C_NFAIL];
+  out->lost = (int64_t)h[PT_C_LOST];
+  out->cross_cap = (int64_t)h[PT_C_CCAP];
+  out->open = (int64_t)h[PT_C_OPEN];
+  out->rep800 = (int64_t)h[PT_C_REP];
+  out->dt_warn = (int64_t)h[PT_C_DTWARN];
+  if (out->newton_fail) return fail(c, PT_ERR_NEWTON, "%lld particles failed the inverse map",
+                                    (long long)out->newton_fail);
+  if (out->lost) return fail(c, PT_ERR_LOST, "%lld particles lost", (long long)out->lost);
+  if (out->cross_cap)
+    return fail(c, PT_ERR_CROSS, "%lld particles hit the crossing cap", (long long)out->cross_cap);
+  if (out->dt_warn) return PT_WARN_DT;
+  return PT_OK;
+}
+
+pt_status pt_push_impl(pt_ctx* c, const pt_particles* p, int32_t nsteps, double dt,
+                       pt_stats* out) {
+  const int64_t n = p->n;
+  CK(cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * PT_C_COUNT, c->stream));
+  if (n > 0 && nsteps > 0) {
+    pt_status s = ensure_scratch(c, n);
+    if (s) return s;
+    const bool f64 = c->cfg.precision == PT_FP64;
+    const int np = c->N + 1;
+    const int block = push_block(c);
+    int occ = max_active_push(c->g, f64, np, block);
+    int grid = grid_for(c, n, block, occ);
+    PushArgs a;
+    a.m = dev_mesh(c);
+    fill_consts(c, a.k);
+    a.p = {n, p->x, p->v, p->d, p->elem, p->hits, p->status};
+    a.mlp = pt_dev_mlp(c);
+    a.U = c->U;
+    a.dt = dt;
+    a.stats = c->d_stats;
+    const int chunk = c->cfg.rebin_every > 0 ? c->cfg.rebin_every : 10;
+    for (int s0 = 0; s0 < nsteps; s0 += chunk) {
+      int rc = bin_by_element(p->elem, n, c->nelem, c->d_scratch, c->d_perm, nullptr, c->nsm,
+                              c->stream);
+      if (rc) return fail(c, PT_ERR_CUDA, "binning: %s", cudaGetErrorString((cudaError_t)rc));
+      a.perm = c->d_perm;
+      a.nsteps = std::min(chunk, nsteps - s0);
+      rc = launch_push(c->g, f64, np, a, grid, block, c->stream);
+      if (rc) return fail(c, PT_ERR_CUDA, "push launch: %s", cudaGetErrorString((cudaError_t)rc));
+    }
+  }
+  if (out) return read_stats(c, p, dt, out);
+  return PT_OK;
+}
+
+extern "C" {
+
+pt_status pt_push(pt_ctx* c, const pt_particles* p, int32_t nsteps, double dt, pt_stats* out) {
+  if (!c) return fail(nullptr, PT_ERR_ARG, "ctx is NULL");
+  if (c->N < 0 || !c->U) return fail(c, PT_ERR_STATE, "pt_set_fluid was not called");
+  pt_status s = validate_particles(c, p);
+  if (s) return s;
+  if (nsteps < 0) return fail(c, PT_ERR_ARG, "nsteps must be >= 0");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(c, PT_ERR_ARG, "dt must be finite and > 0");
+  if (c->cfg.guess == PT_GUESS_MLP && (c->g != 4 || !c->mlp_ready))
+    return fail(c, PT_ERR_STATE, "learned guess needs ngeo = 3 and a trained network");
+  return pt_push_impl(c, p, nsteps, dt, out);
+}
+
+pt_status pt_push_host(pt_ctx* c, const pt_particles* h, int32_t nsteps, double dt,
+                       pt_stats* out) {
+  if (!c) return fail(nullptr, PT_ERR_ARG, "ctx is NULL");
+  pt_status s = validate_particles(c, h);
+  if (s) return s;
+  const int64_t n = h->n;
+  const size_t rs = c->cfg.precision == PT_FP64 ? 8 : 4;
+  const size_t bytes = n * (24 + 3 * rs + rs + 12);
+  if (c->stage_bytes < bytes) {
+    if (c->d_stage) cudaFree(c->d_stage);
+    c->d_stage = nullptr;
+    CK(cudaMalloc(&c->d_stage, std::max<size_t>(bytes, 64) + 256));
+    c->stage_bytes = bytes;
+  }
+  char* b = (char*)c->d_stage;
+  pt_particles d;
+  d.n = n;
+  d.x = (double*)b;
+  b += 24 * n;
+  d.v = b;
+  b += 3 * rs * n;
+  d.d = b;
+  b += rs * n;
+  d.elem = (int32_t*)b;
+  b += 4 * n;
+  d.hits = (int32_t*)b;
+  b += 4 * n;
+  d.status = (uint32_t*)b;
+  cudaStream_t st = c->stream;
+  CK(cudaMemcpyAsync(d.x, h->x, 24 * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d.v, h->v, 3 * rs * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync((void*)d.d, h->d, rs * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d.elem, h->elem, 4 * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d.hits, h->hits, 4 * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d.status, h->status, 4 * n, cudaMemcpyHostToDevice, st));
+  pt_stats tmp;
+  s = pt_push(c, &d, nsteps, dt, out ? &tmp : nullptr);
+  if (s && s != PT_WARN_DT && s != PT_ERR_NEWTON && s != PT_ERR_LOST && s != PT_ERR_CROSS)
+    return s;
+  CK(cudaMemcpyAsync(h->x, d.x, 24 * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h->v, d.v, 3 * rs * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h->elem, d.elem, 4 * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h->hits, d.hits, 4 * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h->status, d.status, 4 * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (out) *out = tmp;
+  return s;
+}
+
+pt_status pt_locate(pt_ctx* c, int64_t n, const double* x, const int32_t* elem, double* xi,
+                    int32_t* iters, uint32_t* status) {
+  if (!c) return fail(nullptr, PT_ERR_ARG, "ctx is NULL");
+  if (n < 0) return fail(c, PT_ERR_ARG, "n must be >= 0");
+  if (n > 0 && (!x || !elem || !xi)) return fail(c, PT_ERR_ARG, "NULL array");
+  if (c->cfg.guess == PT_GUESS_MLP && (c->g != 4 || !c->mlp_ready))
+    return fail(c, PT_ERR_STATE, "learned guess needs ngeo = 3 and a trained network");
+  if (n == 0) return PT_OK;
+  LocateArgs a;
+  a.m = dev_mesh(c);
+  fill_consts(c, a.k);
+  a.mlp = pt_dev_mlp(c);
+  a.n = n;
+  a.x = x;
+  a.elem = elem;
+  a.xi = xi;
+  a.iters = iters;
+  a.status = status;
+  int grid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)c->nsm * 16);
+  int rc = launch_locate(c->g, c->cfg.precision == PT_FP64, 0, a, grid, 128, c->stream);
+  if (rc) return fail(c, PT_ERR_CUDA, "locate launch: %s", cudaGetErrorString((cudaError_t)rc));
+  return PT_OK;
+}
+
+pt_status pt_deposit(pt_ctx* c, const pt_particles* p, int32_t mode, float* S) {
+  if (!c) return fail(nullptr, PT_ERR_ARG, "ctx is NULL");
+  if (c->N < 0 || !c->U) return fail(c, PT_ERR_STATE, "pt_set_fluid was not called");
+  pt_status s = validate_particles(c, p);
+  if (s) return s;
+  if (mode != PT_DEPOSIT_ATOMIC && mode != PT_DEPOSIT_SEGMENTED)
+    return fail(c, PT_ERR_ARG, "mode must be PT_DEPOSIT_ATOMIC or PT_DEPOSIT_SEGMENTED");
+  if (!S) return fail(c, PT_ERR_ARG, "S is NULL");
+  const int np = c->N + 1;
+  const size_t n3 = (size_t)np * np * np;
+  const int64_t n = p->n;
+  s = ensure_scratch(c, n);
+  if (s) return s;
+  int* offs = nullptr;
+  int rc = bin_by_element(p->elem, n, c->nelem, c->d_scratch, c->d_perm, &offs, c->nsm, c->stream);
+  if (rc) return fail(c, PT_ERR_CUDA, "binning: %s", cudaGetErrorString((cudaError_t)rc));
+  DepositArgs a;
+  a.m = dev_mesh(c);
+  fill_consts(c, a.k);
+  a.p = {n, p->x, p->v, p->d, p->elem, p->hits, p->status};
+  a.U = c->U;
+  a.perm = c->d_perm;
+  a.offs = offs;
+  a.S = S;
+  const bool f64 = c->cfg.precision == PT_FP64;
+  if (mode == PT_DEPOSIT_ATOMIC) {
+    CK(cudaMemsetAsync(S, 0, sizeof(float) * 4 * n3 * c->nelem, c->stream));
+    if (n == 0) return PT_OK;
+    int grid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)c->nsm * 16);
+    rc = launch_deposit(c->g, f64, np, 0, a, grid, 128, c->stream);
+  } else {
+    int grid = std::min(c->nelem, c->nsm * 32);
+    rc = launch_deposit(c->g, f64, np, 1, a, grid, 256, c->stream);
+  }
+  if (rc) return fail(c, PT_ERR_CUDA, "deposit launch: %s", cudaGetErrorString((cudaError_t)rc));
+  return PT_OK;
+}
+
+pt_status pt_destroy(pt_ctx* c) {
+  if (!c) return PT_OK;
+  for (void* q : c->allocs) cudaFree(q);
+  if (c->d_scratch) cudaFree(c->d_scratch);
+  if (c->d_perm) cudaFree(c->d_perm);
+  if (c->d_stage) cudaFree(c->d_stage);
+  pt_mlp_release(c);
+  delete c;
+  return PT_OK;
+}
+
+const char* pt_last_error(const pt_ctx* c) {
+  if (!c) return g_init_err.c_str();
+  return c->err.c_str();
+}
+
+}  // extern "C"

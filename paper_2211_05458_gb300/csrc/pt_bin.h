@@ -1,0 +1,15 @@
+// pt_bin.h -- element binning (counting sort) used by the push and deposition.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace pt {
+// ints of scratch bin_by_element needs for nelem elements
+size_t bin_scratch_ints(int nelem);
+// perm[n] receives particle indices sorted by elem (order within an element
+// unspecified); *offs_out points into scratch at offs[nelem + 2]: element e's
+// particles are perm[offs[e] .. offs[e+1]); bin nelem holds invalid owners.
+int bin_by_element(const int* elem, int64_t n, int nelem, int* scratch, int* perm, int** offs_out,
+                   int nsm, cudaStream_t s);
+}  // namespace pt

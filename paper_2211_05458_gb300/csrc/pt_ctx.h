@@ -1,0 +1,51 @@
+// pt_ctx.h -- the library-owned context behind the opaque pt_ctx handle.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "pt.h"
+#include "pt_internal.h"
+
+struct pt_mlp_state;
+
+struct pt_ctx {
+  int dev = 0;
+  int nsm = 1;
+  cudaStream_t stream = nullptr;
+  pt_config cfg{};
+  // mesh
+  int nelem = 0, ngeo = 0, g = 0, ncurved = 0;
+  double* d_xg64 = nullptr;
+  float* d_xg32 = nullptr;
+  double* d_ce = nullptr;
+  float* d_tri = nullptr;
+  int* d_fnbr = nullptr;
+  int* d_finfo = nullptr;
+  float* d_slab = nullptr;
+  double* d_bil = nullptr;
+  double* d_shift = nullptr;
+  unsigned long long* d_stats = nullptr;
+  std::vector<void*> allocs;
+  // fluid
+  int N = -1, node_type = 0;
+  const void* U = nullptr;
+  double sn[PT_MAXN] = {0}, sw[PT_MAXN] = {0};
+  // scratch (binning), permutation, host-call staging
+  int* d_scratch = nullptr;
+  size_t scratch_ints = 0;
+  int* d_perm = nullptr;
+  int64_t perm_cap = 0;
+  void* d_stage = nullptr;
+  size_t stage_bytes = 0;
+  // learned guess
+  pt_mlp_state* mlp = nullptr;
+  bool mlp_ready = false;
+  float* d_mlp_pre = nullptr;
+  std::string err = "no error";
+};
+
+void pt_mlp_release(pt_ctx* c);
+pt_status pt_push_impl(pt_ctx* c, const pt_particles* p, int32_t nsteps, double dt, pt_stats* out);

@@ -1,0 +1,711 @@
+// pt_device.cuh -- device building blocks of the particle push (arXiv 2211.05458):
+// Lagrange bases, the inverse map x -> xi (Sec. 3.2.1), interpolation of the
+// nodal state (Eq. part_interpolation), drag (Sec. 2.2) and the physical-
+// space tracking with face intersection (Secs. 3.2.3, 3.2.4) and the specular
+// wall model (Sec. 2.4).  Everything is templated on the number of geometry
+// nodes G = NGeo+1 and solution nodes NP = N+1 so loops unroll into registers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "pt_internal.h"
+
+namespace pt {
+
+template <typename T>
+__device__ __forceinline__ T tabs(T a) {
+  return a < T(0) ? -a : a;
+}
+
+template <typename T>
+__device__ __forceinline__ T tmax3(T a, T b, T c) {
+  return fmax(fmax(tabs(a), tabs(b)), tabs(c));
+}
+
+template <typename T>
+__device__ __forceinline__ T tfma(T a, T b, T c);
+template <>
+__device__ __forceinline__ float tfma<float>(float a, float b, float c) {
+  return fmaf(a, b, c);
+}
+template <>
+__device__ __forceinline__ double tfma<double>(double a, double b, double c) {
+  return fma(a, b, c);
+}
+
+// node set of the right precision from the constants
+template <typename T>
+struct Nodes;
+template <>
+struct Nodes<float> {
+  __device__ static const float* geo(const DevConsts& k) { return k.gn32; }
+  __device__ static const float* geow(const DevConsts& k) { return k.gw32; }
+  __device__ static const float* sol(const DevConsts& k) { return k.sn32; }
+  __device__ static const float* solw(const DevConsts& k) { return k.sw32; }
+};
+template <>
+struct Nodes<double> {
+  __device__ static const double* geo(const DevConsts& k) { return k.gn; }
+  __device__ static const double* geow(const DevConsts& k) { return k.gw; }
+  __device__ static const double* sol(const DevConsts& k) { return k.sn; }
+  __device__ static const double* solw(const DevConsts& k) { return k.sw; }
+};
+
+// Lagrange basis in barycentric product form: l_i(x) = w_i prod_{m != i} (x - x_m),
+// w_i = 1 / prod_{m != i} (x_i - x_m).  Prefix and suffix products avoid the
+// division of the second barycentric form, so the values at the nodes are exact.
+template <int NP, typename T>
+__device__ __forceinline__ void lagr(T x, const T* nodes, const T* w, T* l) {
+  T d[NP];
+#pragma unroll
+  for (int m = 0; m < NP; ++m) d[m] = x - nodes[m];
+  T pre = T(1);
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    l[i] = pre;
+    pre *= d[i];
+  }
+  T suf = T(1);
+#pragma unroll
+  for (int i = NP - 1; i >= 0; --i) {
+    l[i] *= suf * w[i];
+    suf *= d[i];
+  }
+}
+
+// values and first derivatives (dual-number prefix / suffix products)
+template <int NP, typename T>
+__device__ __forceinline__ void lagr_d(T x, const T* nodes, const T* w, T* l, T* dl) {
+  T d[NP], P[NP], dP[NP];
+#pragma unroll
+  for (int m = 0; m < NP; ++m) d[m] = x - nodes[m];
+  T p = T(1), dp = T(0);
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    P[i] = p;
+    dP[i] = dp;
+    dp = tfma(dp, d[i], p);
+    p *= d[i];
+  }
+  T s = T(1), ds = T(0);
+#pragma unroll
+  for (int i = NP - 1; i >= 0; --i) {
+    l[i] = w[i] * P[i] * s;
+    dl[i] = w[i] * tfma(dP[i], s, P[i] * ds);
+    ds = tfma(ds, d[i], s);
+    s *= d[i];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ bool inv3(const T* J, T* Ji) {
+  T c00 = J[4] * J[8] - J[5] * J[7];
+  T c01 = J[5] * J[6] - J[3] * J[8];
+  T c02 = J[3] * J[7] - J[4] * J[6];
+  T det = J[0] * c00 + J[1] * c01 + J[2] * c02;
+  if (!(tabs(det) > T(0))) return false;
+  T id = T(1) / det;
+  Ji[0] = c00 * id;
+  Ji[1] = (J[2] * J[7] - J[1] * J[8]) * id;
+  Ji[2] = (J[1] * J[5] - J[2] * J[4]) * id;
+  Ji[3] = c01 * id;
+  Ji[4] = (J[0] * J[8] - J[2] * J[6]) * id;
+  Ji[5] = (J[2] * J[3] - J[0] * J[5]) * id;
+  Ji[6] = c02 * id;
+  Ji[7] = (J[1] * J[6] - J[0] * J[7]) * id;
+  Ji[8] = (J[0] * J[4] - J[1] * J[3]) * id;
+  return true;
+}
+
+template <typename T>
+__device__ __forceinline__ void matvec3(const T* M, const T* v, T* o) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) o[r] = M[3 * r] * v[0] + M[3 * r + 1] * v[1] + M[3 * r + 2] * v[2];
+}
+
+// ---------------------------------------------------------------------------
+// element map chi(xi) = sum_abc X_abc l_a(xi1) l_b(xi2) l_c(xi3), sum-factorised
+// ---------------------------------------------------------------------------
+
+// FP32, nodes coordinate-major [3][G^3]; chi and Jacobian J[r][q] = d chi_r / d xi_q
+template <int G>
+__device__ __forceinline__ void map_j32(const float* __restrict__ X, const float* xi,
+                                        const DevConsts& k, float* chi, float* J) {
+  constexpr int G3 = G * G * G;
+  float l0[G], d0[G], l1[G], d1[G], l2[G], d2[G];
+  lagr_d<G, float>(xi[0], k.gn32, k.gw32, l0, d0);
+  lagr_d<G, float>(xi[1], k.gn32, k.gw32, l1, d1);
+  lagr_d<G, float>(xi[2], k.gn32, k.gw32, l2, d2);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    chi[r] = 0.f;
+    J[3 * r] = J[3 * r + 1] = J[3 * r + 2] = 0.f;
+  }
+#pragma unroll
+  for (int c = 0; c < G; ++c) {
+    float T0[3] = {0.f, 0.f, 0.f}, T1[3] = {0.f, 0.f, 0.f}, T2[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < G; ++b) {
+      float s[3] = {0.f, 0.f, 0.f}, s1[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int a = 0; a < G; ++a) {
+        const int q = a + G * (b + G * c);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          float xv = __ldg(X + r * G3 + q);
+          s[r] = fmaf(xv, l0[a], s[r]);
+          s1[r] = fmaf(xv, d0[a], s1[r]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        T0[r] = fmaf(s[r], l1[b], T0[r]);
+        T1[r] = fmaf(s1[r], l1[b], T1[r]);
+        T2[r] = fmaf(s[r], d1[b], T2[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      chi[r] = fmaf(T0[r], l2[c], chi[r]);
+      J[3 * r] = fmaf(T1[r], l2[c], J[3 * r]);
+      J[3 * r + 1] = fmaf(T2[r], l2[c], J[3 * r + 1]);
+      J[3 * r + 2] = fmaf(T0[r], d2[c], J[3 * r + 2]);
+    }
+  }
+}
+
+// FP64, nodes point-major [G^3][3]; with WJ also the Jacobian
+template <int G, bool WJ>
+__device__ __forceinline__ void map64(const double* __restrict__ X, const double* xi,
+                                      const DevConsts& k, double* chi, double* J) {
+  double l0[G], d0[G], l1[G], d1[G], l2[G], d2[G];
+  if (WJ) {
+    lagr_d<G, double>(xi[0], k.gn, k.gw, l0, d0);
+    lagr_d<G, double>(xi[1], k.gn, k.gw, l1, d1);
+    lagr_d<G, double>(xi[2], k.gn, k.gw, l2, d2);
+  } else {
+    lagr<G, double>(xi[0], k.gn, k.gw, l0);
+    lagr<G, double>(xi[1], k.gn, k.gw, l1);
+    lagr<G, double>(xi[2], k.gn, k.gw, l2);
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    chi[r] = 0.0;
+    if (WJ) J[3 * r] = J[3 * r + 1] = J[3 * r + 2] = 0.0;
+  }
+#pragma unroll
+  for (int c = 0; c < G; ++c) {
+    double T0[3] = {0, 0, 0}, T1[3] = {0, 0, 0}, T2[3] = {0, 0, 0};
+#pragma unroll
+    for (int b = 0; b < G; ++b) {
+      double s[3] = {0, 0, 0}, s1[3] = {0, 0, 0};
+#pragma unroll
+      for (int a = 0; a < G; ++a) {
+        const double* P = X + 3 * (a + G * (b + G * c));
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          double xv = __ldg(P + r);
+          s[r] = fma(xv, l0[a], s[r]);
+          if (WJ) s1[r] = fma(xv, d0[a], s1[r]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        T0[r] = fma(s[r], l1[b], T0[r]);
+        if (WJ) {
+          T1[r] = fma(s1[r], l1[b], T1[r]);
+          T2[r] = fma(s[r], d1[b], T2[r]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      chi[r] = fma(T0[r], l2[c], chi[r]);
+      if (WJ) {
+        J[3 * r] = fma(T1[r], l2[c], J[3 * r]);
+        J[3 * r + 1] = fma(T2[r], l2[c], J[3 * r + 1]);
+        J[3 * r + 2] = fma(T0[r], d2[c], J[3 * r + 2]);
+      }
+    }
+  }
+}
+
+// trilinear start xi0 = Jc^{-1} (x_loc - xc), from the per-element table
+__device__ __forceinline__ void trilinear_guess(const DevMesh& m, int e, const float* xf,
+                                                float* xi) {
+  const float* t = m.tri + 12 * (size_t)e;
+  float r[3] = {xf[0] - __ldg(t), xf[1] - __ldg(t + 1), xf[2] - __ldg(t + 2)};
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+    xi[q] = __ldg(t + 3 + 3 * q) * r[0] + __ldg(t + 4 + 3 * q) * r[1] + __ldg(t + 5 + 3 * q) * r[2];
+}
+
+// Full FP64 Newton: chi(xi) - x = 0, |dxi|_inf < tol (Sec. 3.2.1).
+template <int G>
+__device__ __forceinline__ bool newton64(const double* X64, const double* xl, double* xi,
+                                         const DevConsts& k, int maxit, int& it64) {
+  for (int it = 0; it < maxit; ++it) {
+    double chi[3], J[9], Ji[9], r[3], d[3];
+    map64<G, true>(X64, xi, k, chi, J);
+    if (!inv3(J, Ji)) return false;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) r[q] = chi[q] - xl[q];
+    matvec3(Ji, r, d);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) xi[q] -= d[q];
+    ++it64;
+    double md = tmax3(d[0], d[1], d[2]);
+    if (md < k.newton_tol) return true;
+    if (!(tmax3(xi[0], xi[1], xi[2]) <= 4.0)) return false;
+  }
+  return false;
+}
+
+// Mixed-precision Newton: FP32 iterations (chi and J in FP32) until the step
+// is below 1e-5, then FP64 residuals with the last FP32 inverse Jacobian until
+// the step is below newton_tol; a full FP64 Newton is the fallback.
+template <int G>
+__device__ __forceinline__ bool newton_mixed(const DevMesh& m, const DevConsts& k, int e,
+                                             const double* xl, const float* guess, double* xi,
+                                             int& it32, int& it64) {
+  constexpr int G3 = G * G * G;
+  const float* X32 = m.xg32 + (size_t)e * 3 * G3;
+  const double* X64 = m.xg64 + (size_t)e * 3 * G3;
+  float xf[3] = {(float)xl[0], (float)xl[1], (float)xl[2]};
+  float z[3] = {guess[0], guess[1], guess[2]};
+  float Ji[9];
+  bool have = false;
+  for (int it = 0; it < 8; ++it) {
+    float chi[3], J[9], r[3], d[3];
+    map_j32<G>(X32, z, k, chi, J);
+    if (!inv3(J, Ji)) break;
+    have = true;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) r[q] = chi[q] - xf[q];
+    matvec3(Ji, r, d);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) z[q] -= d[q];
+    ++it32;
+    if (!(tmax3(z[0], z[1], z[2]) <= 4.f)) {
+      have = false;
+      break;
+    }
+    if (tmax3(d[0], d[1], d[2]) < 1e-5f) break;
+  }
+  if (have) {
+    xi[0] = z[0];
+    xi[1] = z[1];
+    xi[2] = z[2];
+    for (int it = 0; it < 6; ++it) {
+      double chi[3];
+      float r[3], d[3];
+      map64<G, false>(X64, xi, k, chi, nullptr);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) r[q] = (float)(chi[q] - xl[q]);
+      matvec3(Ji, r, d);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) xi[q] -= (double)d[q];
+      ++it64;
+      if ((double)tmax3(d[0], d[1], d[2]) < k.newton_tol) return true;
+    }
+  } else {
+    xi[0] = guess[0];
+    xi[1] = guess[1];
+    xi[2] = guess[2];
+  }
+  if (!(tmax3(xi[0], xi[1], xi[2]) <= 4.0)) xi[0] = xi[1] = xi[2] = 0.0;
+  return newton64<G>(X64, xl, xi, k, k.max_newton, it64);
+}
+
+// ---------------------------------------------------------------------------
+// interpolation of rho and rho u (Eq. part_interpolation), sum-factorised
+// ---------------------------------------------------------------------------
+
+template <int NP, typename T>
+__device__ __forceinline__ void interp4(const T* __restrict__ Ue, const T* l1, const T* l2,
+                                        const T* l3, T* out) {
+  constexpr int N3 = NP * NP * NP;
+#pragma unroll 1
+  for (int v = 0; v < 4; ++v) {
+    const T* Uv = Ue + v * N3;
+    T acc = T(0);
+#pragma unroll
+    for (int kk = 0; kk < NP; ++kk) {
+      T t2 = T(0);
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        const T* row = Uv + NP * (j + NP * kk);
+        T t1 = T(0);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) t1 = tfma(__ldg(row + i), l1[i], t1);
+        t2 = tfma(t1, l2[j], t2);
+      }
+      acc = tfma(t2, l3[kk], acc);
+    }
+    out[v] = acc;
+  }
+}
+
+// drag factor f_D: 1 (Stokes) or 1 + 0.15 Re_p^0.687 (Schiller-Naumann)
+template <typename T>
+__device__ __forceinline__ T drag_factor(int law, T re) {
+  if (law == 0) return T(1);
+  if (std::is_same<T, float>::value) return T(1) + T(0.15) * (T)powf((float)re, 0.687f);
+  return T(1) + T(0.15) * (T)pow((double)re, 0.687);
+}
+
+// ---------------------------------------------------------------------------
+// tracking (Secs. 3.2.3-3.2.4, 2.4)
+// ---------------------------------------------------------------------------
+
+template <int G>
+__device__ __forceinline__ int face_node(int f, int mm, int kk) {
+  const int fixed = (f & 1) ? G - 1 : 0;
+  switch (f >> 1) {
+    case 0: return fixed + G * (mm + G * kk);
+    case 1: return mm + G * (fixed + G * kk);
+    default: return mm + G * (kk + G * fixed);
+  }
+}
+
+// curved face p(s,t) and its tangents from the element's Lagrange nodes
+template <int G>
+__device__ __forceinline__ void face_eval(const double* X64, int f, double s, double t,
+                                          const DevConsts& k, double* p, double* ps,
+                                          double* pt) {
+  double ls[G], ds[G], lt[G], dt[G];
+  lagr_d<G, double>(s, k.gn, k.gw, ls, ds);
+  lagr_d<G, double>(t, k.gn, k.gw, lt, dt);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) p[r] = ps[r] = pt[r] = 0.0;
+#pragma unroll
+  for (int kk = 0; kk < G; ++kk)
+#pragma unroll
+    for (int mm = 0; mm < G; ++mm) {
+      const double* P = X64 + 3 * face_node<G>(f, mm, kk);
+      double w = ls[mm] * lt[kk], wsv = ds[mm] * lt[kk], wtv = ls[mm] * dt[kk];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        double xv = __ldg(P + r);
+        p[r] = fma(xv, w, p[r]);
+        ps[r] = fma(xv, wsv, ps[r]);
+        pt[r] = fma(xv, wtv, pt[r]);
+      }
+    }
+}
+
+__device__ __forceinline__ void cross3d(const double* a, const double* b, double* c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+__device__ __forceinline__ double dot3d(const double* a, const double* b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// Roots of the ray (origin xs, unit direction td, frame n1, n2) with the
+// bilinear patch p(s,t) = a st + b s + c t + d: the two plane equations
+// n_k.(p - xs) = 0 are eliminated to one quadratic (Ramsey et al. 2004).
+// Writes up to 2 (s, t, alpha) triples; returns their number.
+__device__ __forceinline__ int bilinear_roots(const double* B, const double* xs, const double* td,
+                                              const double* n1, const double* n2, double* rs,
+                                              double* rt, double* ra) {
+  const double* a = B;
+  const double* b = B + 3;
+  const double* c = B + 6;
+  double dd[3] = {B[9] - xs[0], B[10] - xs[1], B[11] - xs[2]};
+  double A1 = dot3d(n1, a), B1 = dot3d(n1, b), C1 = dot3d(n1, c), D1 = dot3d(n1, dd);
+  double A2 = dot3d(n2, a), B2 = dot3d(n2, b), C2 = dot3d(n2, c), D2 = dot3d(n2, dd);
+  double scl = fabs(A1) + fabs(B1) + fabs(C1) + fabs(D1) + fabs(A2) + fabs(B2) + fabs(C2) +
+               fabs(D2);
+  if (!(scl > 0.0)) return 0;
+  int nr = 0;
+  for (int pass = 0; pass < 2 && nr == 0; ++pass) {
+    // pass 0 eliminates t (quadratic in s), pass 1 eliminates s (quadratic in t)
+    double P1 = pass ? C1 : B1, Q1 = pass ? B1 : C1, P2 = pass ? C2 : B2, Q2 = pass ? B2 : C2;
+    double q2 = P1 * A2 - P2 * A1;
+    double q1 = P1 * Q2 + D1 * A2 - P2 * Q1 - D2 * A1;
+    double q0 = D1 * Q2 - D2 * Q1;
+    double r[2];
+    int k = 0;
+    if (fabs(q2) <= 1e-14 * scl * scl) {
+      if (fabs(q1) > 0.0) r[k++] = -q0 / q1;
+    } else {
+      double disc = q1 * q1 - 4.0 * q2 * q0;
+      if (disc >= 0.0) {
+        double sq = sqrt(disc);
+        double qq = -0.5 * (q1 + (q1 >= 0.0 ? sq : -sq));
+        if (qq != 0.0) {
+          r[k++] = qq / q2;
+          r[k++] = q0 / qq;
+        } else {
+          r[k++] = 0.0;
+        }
+      }
+    }
+    for (int i = 0; i < k; ++i) {
+      double u = r[i];
+      double den1 = A1 * u + Q1, den2 = A2 * u + Q2, w;
+      if (fabs(den1) >= fabs(den2)) {
+        if (fabs(den1) <= 1e-14 * scl) continue;
+        w = -(P1 * u + D1) / den1;
+      } else {
+        if (fabs(den2) <= 1e-14 * scl) continue;
+        w = -(P2 * u + D2) / den2;
+      }
+      double s = pass ? w : u, t = pass ? u : w;
+      double pp[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) pp[q] = a[q] * s * t + b[q] * s + c[q] * t + B[9 + q] - xs[q];
+      rs[nr] = s;
+      rt[nr] = t;
+      ra[nr] = dot3d(td, pp);
+      nr++;
+    }
+  }
+  return nr;
+}
+
+// Newton on F(s,t,alpha) = p(s,t) - xs - alpha td for a curved face, started
+// from a bilinear root; returns true on convergence.
+template <int G>
+__device__ __forceinline__ bool curved_refine(const double* X64, int f, const double* xs,
+                                              const double* td, const DevConsts& k, double& s,
+                                              double& t, double& al, double L) {
+  for (int it = 0; it < 20; ++it) {
+    double p[3], ps[3], pt[3], F[3], J[9], Ji[9], dl[3];
+    face_eval<G>(X64, f, s, t, k, p, ps, pt);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      F[r] = p[r] - xs[r] - al * td[r];
+      J[3 * r] = ps[r];
+      J[3 * r + 1] = pt[r];
+      J[3 * r + 2] = -td[r];
+    }
+    if (!inv3(J, Ji)) return false;
+    matvec3(Ji, F, dl);
+    s -= dl[0];
+    t -= dl[1];
+    al -= dl[2];
+    if (fabs(dl[0]) < 1e-14 && fabs(dl[1]) < 1e-14 && fabs(dl[2]) < 1e-14 * (L + 1.0))
+      return true;
+    if (!(fabs(s) < 3.0 && fabs(t) < 3.0)) return false;
+  }
+  return false;
+}
+
+template <typename R>
+__device__ __forceinline__ void reflect3(R* a, const double* n) {
+  double s = 2.0 * ((double)a[0] * n[0] + (double)a[1] * n[1] + (double)a[2] * n[2]);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) a[r] = (R)((double)a[r] - s * n[r]);
+}
+
+struct TrackCounters {
+  int cross, hits, slow;
+};
+
+// Conservative FP32 test: can the segment x -> xe (extended by the band) touch
+// any face of element e?  Slab of face f: lo <= n.(P - ce) <= hi for every
+// point of the face, margins included.
+__device__ __forceinline__ bool touches_any_slab(const DevMesh& m, int e, const double* x,
+                                                 const double* xe) {
+  const double* ce = m.ce + 3 * (size_t)e;
+  float a[3], b[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    double c = __ldg(ce + r);
+    a[r] = (float)(x[r] - c);
+    b[r] = (float)(xe[r] - c);
+  }
+  const float4* S = reinterpret_cast<const float4*>(m.slab + 48 * (size_t)e);
+  bool hit = false;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    float4 s0 = __ldg(S + 2 * f), s1 = __ldg(S + 2 * f + 1);
+    float pa = s0.x * a[0] + s0.y * a[1] + s0.z * a[2];
+    float pb = s0.x * b[0] + s0.y * b[1] + s0.z * b[2];
+    hit |= (fmaxf(pa, pb) >= s0.w) && (fminf(pa, pb) <= s1.x);
+  }
+  return hit;
+}
+
+// Tracks the stage segment x -> xe through the mesh.  The ray
+// x(alpha) = xs + alpha td, alpha in (a0, L] (Eq. parttrajectory) is tested
+// against every face of the current element except the entry face; the
+// smallest accepted alpha wins (lowest face index on ties).  Internal face:
+// continue in the neighbour on the same ray.  Periodic: same, translated.
+// Wall: restart at the hit point with the remaining length, mirroring the
+// direction, v, kx and kv by I - 2 n n^T (Sec. 2.4).  Open: stop there.
+template <int G, typename R>
+__device__ void track(const DevMesh& m, const DevConsts& k, int& e, double* x, double* xe,
+                      R* v, R* kx, R* kv, int& hits, unsigned& st, TrackCounters& tc) {
+  if (!touches_any_slab(m, e, x, xe)) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) x[r] = xe[r];
+    return;
+  }
+  tc.slow++;
+  double xs[3] = {x[0], x[1], x[2]};
+  double td[3] = {xe[0] - xs[0], xe[1] - xs[1], xe[2] - xs[2]};
+  double L = sqrt(dot3d(td, td));
+  if (!(L > 0.0)) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) x[r] = xe[r];
+    return;
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) td[r] /= L;
+  double n1[3], n2[3];
+  {
+    double ax[3] = {0, 0, 0};
+    int im = 0;
+    if (fabs(td[1]) < fabs(td[im])) im = 1;
+    if (fabs(td[2]) < fabs(td[im])) im = 2;
+    ax[im] = 1.0;
+    cross3d(td, ax, n1);
+    double nn = sqrt(dot3d(n1, n1));
+#pragma unroll
+    for (int r = 0; r < 3; ++r) n1[r] /= nn;
+    cross3d(td, n1, n2);
+  }
+  double a0 = 0.0;
+  int fin = -1;
+  int ncr;
+  for (ncr = 0; ncr < k.max_cross; ++ncr) {
+    const double* ce = m.ce + 3 * (size_t)e;
+    double xl[3] = {xs[0] - __ldg(ce), xs[1] - __ldg(ce + 1), xs[2] - __ldg(ce + 2)};
+    const double* X64 = m.xg64 + (size_t)e * 3 * G * G * G;
+    double best = 1e300, bs = 0.0, bt = 0.0;
+    int bf = -1;
+    for (int f = 0; f < 6; ++f) {
+      if (f == fin) continue;
+      // slab prefilter (double)
+      const float* sl = m.slab + 48 * (size_t)e + 8 * f;
+      double nrm[3] = {__ldg(sl), __ldg(sl + 1), __ldg(sl + 2)};
+      double pa = dot3d(nrm, xl);
+      double pb = pa + L * dot3d(nrm, td);
+      if (fmax(pa, pb) < (double)__ldg(sl + 3) || fmin(pa, pb) > (double)__ldg(sl + 4)) continue;
+      const int info = __ldg(m.finfo + 6 * (size_t)e + f);
+      const int kind = (info >> 2) & 3;
+      const double* Bf = m.bil + 72 * (size_t)e + 12 * f;
+      double Bl[12];
+#pragma unroll
+      for (int q = 0; q < 12; ++q) Bl[q] = __ldg(Bf + q);
+      double rs[2], rt[2], ra[2];
+      int nr = bilinear_roots(Bl, xl, td, n1, n2, rs, rt, ra);
+      if (kind == PT_FACE_CURVED) {
+        int kk = 0;
+        for (int i = 0; i < nr; ++i) {
+          double s = rs[i], t = rt[i], al = ra[i];
+          if (!(fabs(s) < 2.0 && fabs(t) < 2.0)) continue;
+          if (curved_refine<G>(X64, f, xl, td, k, s, t, al, L)) {
+            bool dup = false;
+            for (int j = 0; j < kk; ++j)
+              if (fabs(rs[j] - s) < 1e-10 && fabs(rt[j] - t) < 1e-10) dup = true;
+            if (!dup) {
+              rs[kk] = s;
+              rt[kk] = t;
+              ra[kk] = al;
+              kk++;
+            }
+          }
+        }
+        nr = kk;
+      }
+      for (int i = 0; i < nr; ++i) {
+        double al = ra[i], s = rs[i], t = rt[i];
+        double mm = fmax(fabs(s), fabs(t));
+        if (mm > 1.0 + k.band_ref) continue;
+        if (al < a0 - k.band_x || al > L + k.band_x) continue;
+        if (fabs(mm - 1.0) < k.band_ref || fabs(al - a0) < k.band_x || fabs(L - al) < k.band_x)
+          st |= PT_ST_NEAR_FACE;
+        if (mm <= 1.0 && al > a0 && al <= L && al < best) {
+          best = al;
+          bf = f;
+          bs = s;
+          bt = t;
+        }
+      }
+    }
+    if (bf < 0) break;
+    const int info = __ldg(m.finfo + 6 * (size_t)e + bf);
+    const int bc = info & 3;
+    if (bc == PT_BC_INTERNAL || bc == PT_BC_PERIODIC) {
+      if (bc == PT_BC_PERIODIC) {
+        const double* sh = m.shift + 18 * (size_t)e + 3 * bf;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          xs[r] += __ldg(sh + r);
+          xe[r] += __ldg(sh + r);
+        }
+      }
+      fin = (info >> 4) & 7;
+      e = __ldg(m.fnbr + 6 * (size_t)e + bf);
+      a0 = best;
+      tc.cross++;
+    } else if (bc == PT_BC_WALL) {
+      double ps[3], pt[3], nrm[3];
+      const int kind = (info >> 2) & 3;
+      if (kind == PT_FACE_CURVED) {
+        double p[3];
+        face_eval<G>(X64, bf, bs, bt, k, p, ps, pt);
+      } else {
+        const double* Bf = m.bil + 72 * (size_t)e + 12 * bf;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          ps[r] = __ldg(Bf + r) * bt + __ldg(Bf + 3 + r);
+          pt[r] = __ldg(Bf + r) * bs + __ldg(Bf + 6 + r);
+        }
+      }
+      cross3d(ps, pt, nrm);
+      double nn = sqrt(dot3d(nrm, nrm));
+#pragma unroll
+      for (int r = 0; r < 3; ++r) nrm[r] /= nn;
+      double xh[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) xh[r] = xs[r] + best * td[r];
+      double Lr = L - best;
+      double sdt = 2.0 * dot3d(td, nrm);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) td[r] -= sdt * nrm[r];
+      reflect3(v, nrm);
+      reflect3(kx, nrm);
+      reflect3(kv, nrm);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        xs[r] = xh[r];
+        xe[r] = xs[r] + Lr * td[r];
+      }
+      L = Lr;
+      a0 = 0.0;
+      fin = bf;
+      hits++;
+      tc.hits++;
+      // the frame follows the new direction
+      double ax[3] = {0, 0, 0};
+      int im = 0;
+      if (fabs(td[1]) < fabs(td[im])) im = 1;
+      if (fabs(td[2]) < fabs(td[im])) im = 2;
+      ax[im] = 1.0;
+      cross3d(td, ax, n1);
+      double n1n = sqrt(dot3d(n1, n1));
+#pragma unroll
+      for (int r = 0; r < 3; ++r) n1[r] /= n1n;
+      cross3d(td, n1, n2);
+      if (!(L > 0.0)) break;
+    } else {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) x[r] = xs[r] + best * td[r];
+      st |= PT_ST_OPEN;
+      return;
+    }
+  }
+  if (ncr >= k.max_cross) st |= PT_ST_CROSS_CAP;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) x[r] = xe[r];
+}
+
+}  // namespace pt

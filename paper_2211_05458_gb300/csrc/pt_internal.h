@@ -1,0 +1,125 @@
+// pt_internal.h -- device-side views and launch arguments shared by the
+// translation units of libpt.  Not part of the public ABI (see include/pt.h).
+#pragma once
+#include <cstdint>
+
+#include "pt.h"
+
+#define PT_MAXG 5  // geometry nodes per direction (NGeo <= 4)
+#define PT_MAXN 8  // solution nodes per direction (N <= 7)
+#define PT_MLP_IN 51
+#define PT_MLP_H 64
+#define PT_MLP_OUT 3
+#define PT_MLP_NP (PT_MLP_H * PT_MLP_IN + PT_MLP_H + 2 * (PT_MLP_H * PT_MLP_H + PT_MLP_H) + \
+                   PT_MLP_OUT * PT_MLP_H + PT_MLP_OUT)
+
+// face kinds (by bounding-box flatness / bilinearity of the face nodes)
+enum { PT_FACE_PLANAR = 0, PT_FACE_BILINEAR = 1, PT_FACE_CURVED = 2 };
+
+// stats counter slots (device uint64 array)
+enum {
+  PT_C_STEPS = 0, PT_C_CROSS, PT_C_HITS, PT_C_IT32, PT_C_IT64, PT_C_SLOW,
+  PT_C_NEAR, PT_C_NFAIL, PT_C_LOST, PT_C_CCAP, PT_C_OPEN, PT_C_REP, PT_C_DTWARN,
+  PT_C_COUNT = 16
+};
+
+#define PT_ST_FROZEN (PT_ST_NEWTON_FAIL | PT_ST_LOST | PT_ST_CROSS_CAP | PT_ST_OPEN)
+
+// Mesh tables on the device.  Geometry is stored relative to each element's
+// centre ce (the mean of its 8 corner nodes), which keeps FP64 residuals and
+// face intersections at the element's own scale.
+struct DevMesh {
+  int nelem;
+  int g;                  // NGeo + 1
+  const double* xg64;     // [E][g^3][3]   nodes - ce
+  const float* xg32;      // [E][3][g^3]   nodes - ce, FP32, coordinate-major
+  const double* ce;       // [E][3]
+  const float* tri;       // [E][12]       trilinear centre (3) and inverse Jacobian (9)
+  const int* fnbr;        // [E][6]        neighbour element
+  const int* finfo;       // [E][6]        bc | kind << 2 | nbr_face << 4
+  const float* slab;      // [E][6][8]     unit normal (3), lo, hi, -, -, - (local coords)
+  const double* bil;      // [E][6][12]    p(s,t) = a st + b s + c t + d (local coords)
+  const double* shift;    // [E][6][3]
+  const float* mlp_pre;   // [E][64]       element part of the first MLP layer, or null
+};
+
+// Constants of one run: node sets, RK table, physics and tolerances.
+struct DevConsts {
+  double gn[PT_MAXG], gw[PT_MAXG];   // geometry nodes / barycentric weights
+  float gn32[PT_MAXG], gw32[PT_MAXG];
+  double sn[PT_MAXN], sw[PT_MAXN];   // solution nodes / barycentric weights
+  float sn32[PT_MAXN], sw32[PT_MAXN];
+  double A[5], B[5];
+  float A32[5], B32[5];
+  double mu, rho_p, g[3], mask[3];
+  double newton_tol, band_ref, band_x, lost_tol;
+  int drag_law, max_newton, max_cross, guess;
+};
+
+struct DevParticles {
+  int64_t n;
+  double* x;
+  void* v;
+  const void* d;
+  int* elem;
+  int* hits;
+  unsigned* status;
+};
+
+// BF16 network for the learned guess: layers 2 and 3 as bf16 [out][in],
+// first-layer xi columns and the output layer in FP32, plus normalisation.
+struct DevMLP {
+  const uint16_t* w2;     // [64][64] bf16
+  const uint16_t* w3;     // [64][64] bf16
+  const float* w1x;       // [64][3]  first-layer columns of the xi_tri inputs / in_std
+  const float* b2;        // [64]
+  const float* b3;        // [64]
+  const float* w4;        // [3][64]
+  const float* b4;        // [3]
+  float xmean[3];         // input mean of the xi_tri features
+  float oscale[3];        // output scale
+};
+
+struct PushArgs {
+  DevMesh m;
+  DevConsts k;
+  DevParticles p;
+  DevMLP mlp;
+  const void* U;          // fluid state, [E][5][n^3], double or float per mode
+  const int* perm;        // particle visiting order (sorted by element) or null
+  int nsteps;
+  double dt;
+  unsigned long long* stats;
+};
+
+struct LocateArgs {
+  DevMesh m;
+  DevConsts k;
+  DevMLP mlp;
+  int64_t n;
+  const double* x;
+  const int* elem;
+  double* xi;
+  int* iters;
+  unsigned* status;
+};
+
+struct DepositArgs {
+  DevMesh m;
+  DevConsts k;
+  DevParticles p;
+  const void* U;
+  const int* perm;        // sorted order (segmented mode)
+  const int* offs;        // [E+1] element segment offsets (segmented mode)
+  float* S;               // [E][4][n^3]
+};
+
+// kernel entry points, one family per (g, mode) translation unit
+namespace pt {
+int launch_push(int g, bool fp64, int np, const PushArgs& a, int grid, int block, void* stream);
+int launch_locate(int g, bool fp64, int np, const LocateArgs& a, int grid, int block,
+                  void* stream);
+int launch_deposit(int g, bool fp64, int np, int mode, const DepositArgs& a, int grid, int block,
+                   void* stream);
+int max_active_push(int g, bool fp64, int np, int block);
+}  // namespace pt

@@ -1,0 +1,438 @@
+// pt_kernels.cuh -- the push, inverse-map and deposition kernels, templated on
+// G = NGeo+1, NP = N+1 and the precision mode.  Each translation unit
+// pt_push_g<G>_<mode>.cu instantiates one (G, mode) family for NP = 2..8.
+#pragma once
+#include "pt_device.cuh"
+#include "pt_mlp_infer.cuh"
+
+namespace pt {
+
+template <bool F64>
+struct RealOf {
+  using type = float;
+};
+template <>
+struct RealOf<true> {
+  using type = double;
+};
+
+__device__ __forceinline__ void count_add(unsigned long long* stats, int slot,
+                                          unsigned long long v) {
+  // warp-aggregated: one atomic per warp and counter
+  unsigned long long s = v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(stats + slot, s);
+}
+
+// Inverse map of one particle with the context's precision and start guess.
+template <int G, bool F64>
+__device__ __forceinline__ bool locate_one(const DevMesh& m, const DevConsts& k, int e,
+                                           const double* x, const float* guess, double* xi,
+                                           int& it32, int& it64) {
+  const double* ce = m.ce + 3 * (size_t)e;
+  double xl[3] = {x[0] - __ldg(ce), x[1] - __ldg(ce + 1), x[2] - __ldg(ce + 2)};
+  if (F64) {
+    xi[0] = guess[0];
+    xi[1] = guess[1];
+    xi[2] = guess[2];
+    return newton64<G>(m.xg64 + (size_t)e * 3 * G * G * G, xl, xi, k, k.max_newton, it64);
+  }
+  return newton_mixed<G>(m, k, e, xl, guess, xi, it32, it64);
+}
+
+// Start guess: trilinear, optionally corrected by the learned network (warp-
+// collective: every lane of the warp must call it).
+template <int G>
+__device__ __forceinline__ void start_guess(const DevMesh& m, const DevConsts& k,
+                                            const DevMLP& mlp, int e, const double* x,
+                                            bool live, float* guess) {
+  const double* ce = m.ce + 3 * (size_t)e;
+  float xf[3] = {(float)(x[0] - __ldg(ce)), (float)(x[1] - __ldg(ce + 1)),
+                 (float)(x[2] - __ldg(ce + 2))};
+  trilinear_guess(m, e, xf, guess);
+  if (G == 4 && k.guess == PT_GUESS_MLP) mlp_correct(m, mlp, e, live, guess);
+}
+
+// One thread per particle; all nsteps x 5 stages of a particle run in
+// registers (the fluid state is constant during the call).  Threads visit
+// particles in element-sorted order (perm) so a warp shares element data.
+template <int G, int NP, bool F64>
+__global__ void __launch_bounds__(256) k_push(const PushArgs a) {
+  using R = typename RealOf<F64>::type;
+  constexpr int N3 = NP * NP * NP;
+  const DevMesh& m = a.m;
+  const DevConsts& k = a.k;
+  const int64_t n = a.p.n;
+  const R dt = (R)a.dt;
+  const R mu = (R)k.mu;
+  R A[5], B[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    A[i] = F64 ? (R)k.A[i] : (R)k.A32[i];
+    B[i] = F64 ? (R)k.B[i] : (R)k.B32[i];
+  }
+  const R* __restrict__ U = reinterpret_cast<const R*>(a.U);
+  R* vg = reinterpret_cast<R*>(a.p.v);
+  const R* dg = reinterpret_cast<const R*>(a.p.d);
+  unsigned long long c_steps = 0, c_it32 = 0, c_it64 = 0;
+  TrackCounters tc = {0, 0, 0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nround = (n + stride - 1) / stride * stride;  // uniform trip count per warp
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nround; t += stride) {
+    const bool inrange = t < n;
+    const int64_t ip = inrange ? (a.perm ? (int64_t)a.perm[t] : t) : 0;
+    unsigned st = inrange ? a.p.status[ip] : PT_ST_FROZEN;
+    bool live = !(st & PT_ST_FROZEN);
+    double x[3] = {0, 0, 0};
+    R v[3] = {0, 0, 0}, d = R(1);
+    int e = 0, hits = 0;
+    if (inrange) {
+      x[0] = a.p.x[ip];
+      x[1] = a.p.x[n + ip];
+      x[2] = a.p.x[2 * n + ip];
+      v[0] = vg[ip];
+      v[1] = vg[n + ip];
+      v[2] = vg[2 * n + ip];
+      d = dg[ip];
+      e = a.p.elem[ip];
+      hits = a.p.hits[ip];
+    }
+    if (e < 0 || e >= m.nelem) {
+      if (live) st |= PT_ST_LOST;
+      live = false;
+    }
+    const R tau = (R)k.rho_p * d * d / (R(18) * mu);
+    for (int step = 0; step < a.nsteps; ++step) {
+      R kx[3] = {0, 0, 0}, kv[3] = {0, 0, 0};
+      for (int s = 0; s < 5; ++s) {
+        float guess[3];
+        start_guess<G>(m, k, a.mlp, live ? e : 0, x, live, guess);
+        if (!live) continue;
+        double xi[3];
+        int i32 = 0, i64 = 0;
+        bool ok = locate_one<G, F64>(m, k, e, x, guess, xi, i32, i64);
+        c_it32 += i32;
+        c_it64 += i64;
+        if (!ok) {
+          st |= PT_ST_NEWTON_FAIL;
+          live = false;
+          continue;
+        }
+        const double mx = tmax3(xi[0], xi[1], xi[2]);
+        if (mx > 1.0 + k.lost_tol) {
+          st |= PT_ST_LOST;
+          live = false;
+          continue;
+        }
+        if (mx > 1.0 - k.band_ref) st |= PT_ST_NEAR_FACE;
+        // interpolation of rho, rho u at xi
+        R l1[NP], l2[NP], l3[NP], Uv[4];
+        lagr<NP, R>((R)xi[0], Nodes<R>::sol(k), Nodes<R>::solw(k), l1);
+        lagr<NP, R>((R)xi[1], Nodes<R>::sol(k), Nodes<R>::solw(k), l2);
+        lagr<NP, R>((R)xi[2], Nodes<R>::sol(k), Nodes<R>::solw(k), l3);
+        interp4<NP, R>(U + (size_t)e * 5 * N3, l1, l2, l3, Uv);
+        // drag + gravity
+        R irho = R(1) / Uv[0], rel[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) rel[r] = Uv[1 + r] * irho - v[r];
+        R fD = R(1);
+        if (k.drag_law) {
+          R re = Uv[0] * sqrt(rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2]) * d / mu;
+          if (re >= R(800)) st |= PT_ST_REP800;
+          fD = drag_factor<R>(1, re);
+        }
+        const R coef = fD / tau;
+        double xe[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          R acc = (R)k.mask[r] * coef * rel[r] + (R)k.g[r];
+          kx[r] = A[s] * kx[r] + dt * v[r];
+          kv[r] = A[s] * kv[r] + dt * acc;
+          xe[r] = x[r] + (double)(B[s] * kx[r]);
+          v[r] = v[r] + B[s] * kv[r];
+        }
+        track<G, R>(m, k, e, x, xe, v, kx, kv, hits, st, tc);
+        if (st & PT_ST_FROZEN) live = false;
+      }
+      if (live) ++c_steps;
+    }
+    if (inrange && !(a.p.status[ip] & PT_ST_FROZEN)) {
+      a.p.x[ip] = x[0];
+      a.p.x[n + ip] = x[1];
+      a.p.x[2 * n + ip] = x[2];
+      vg[ip] = v[0];
+      vg[n + ip] = v[1];
+      vg[2 * n + ip] = v[2];
+      a.p.elem[ip] = e;
+      a.p.hits[ip] = hits;
+      a.p.status[ip] = st;
+    }
+  }
+  count_add(a.stats, PT_C_STEPS, c_steps);
+  count_add(a.stats, PT_C_IT32, c_it32);
+  count_add(a.stats, PT_C_IT64, c_it64);
+  count_add(a.stats, PT_C_CROSS, (unsigned long long)tc.cross);
+  count_add(a.stats, PT_C_HITS, (unsigned long long)tc.hits);
+  count_add(a.stats, PT_C_SLOW, (unsigned long long)tc.slow);
+}
+
+template <int G, bool F64>
+__global__ void __launch_bounds__(256) k_locate(const LocateArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nround = (a.n + stride - 1) / stride * stride;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nround; i += stride) {
+    const bool inrange = i < a.n;
+    double x[3] = {0, 0, 0};
+    int e = 0;
+    if (inrange) {
+      x[0] = a.x[i];
+      x[1] = a.x[a.n + i];
+      x[2] = a.x[2 * a.n + i];
+      e = a.elem[i];
+    }
+    bool live = inrange && e >= 0 && e < a.m.nelem;
+    if (!live) e = 0;
+    float guess[3];
+    start_guess<G>(a.m, a.k, a.mlp, e, x, live, guess);
+    if (!inrange) continue;
+    double xi[3] = {0, 0, 0};
+    int i32 = 0, i64 = 0;
+    bool ok = live && locate_one<G, F64>(a.m, a.k, e, x, guess, xi, i32, i64);
+    a.xi[i] = xi[0];
+    a.xi[a.n + i] = xi[1];
+    a.xi[2 * a.n + i] = xi[2];
+    if (a.iters) a.iters[i] = i32 + i64;
+    if (a.status) a.status[i] = ok ? 0u : (unsigned)PT_ST_NEWTON_FAIL;
+  }
+}
+
+// Per-particle source of Eq. theory:source with Lagrange weights: returns the
+// element and fills f[4] = (-F, -F.v) and the three 1-D bases; false if the
+// particle is frozen or its inverse map fails.
+template <int G, int NP, bool F64>
+__device__ __forceinline__ bool particle_source(const DepositArgs& a, int64_t ip, int& e,
+                                                float* f, float* l1, float* l2, float* l3) {
+  using R = typename RealOf<F64>::type;
+  constexpr int N3 = NP * NP * NP;
+  const int64_t n = a.p.n;
+  if (a.p.status[ip] & PT_ST_FROZEN) return false;
+  e = a.p.elem[ip];
+  if (e < 0 || e >= a.m.nelem) return false;
+  double x[3] = {a.p.x[ip], a.p.x[n + ip], a.p.x[2 * n + ip]};
+  const R* vg = reinterpret_cast<const R*>(a.p.v);
+  R v[3] = {vg[ip], vg[n + ip], vg[2 * n + ip]};
+  R d = reinterpret_cast<const R*>(a.p.d)[ip];
+  const double* ce = a.m.ce + 3 * (size_t)e;
+  float xf[3] = {(float)(x[0] - __ldg(ce)), (float)(x[1] - __ldg(ce + 1)),
+                 (float)(x[2] - __ldg(ce + 2))};
+  float guess[3];
+  trilinear_guess(a.m, e, xf, guess);
+  double xi[3];
+  int i32 = 0, i64 = 0;
+  if (!locate_one<G, F64>(a.m, a.k, e, x, guess, xi, i32, i64)) return false;
+  R lr1[NP], lr2[NP], lr3[NP], Uv[4];
+  lagr<NP, R>((R)xi[0], Nodes<R>::sol(a.k), Nodes<R>::solw(a.k), lr1);
+  lagr<NP, R>((R)xi[1], Nodes<R>::sol(a.k), Nodes<R>::solw(a.k), lr2);
+  lagr<NP, R>((R)xi[2], Nodes<R>::sol(a.k), Nodes<R>::solw(a.k), lr3);
+  interp4<NP, R>(reinterpret_cast<const R*>(a.U) + (size_t)e * 5 * N3, lr1, lr2, lr3, Uv);
+  const R mu = (R)a.k.mu;
+  R rel[3];
+  R irho = R(1) / Uv[0];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) rel[r] = Uv[1 + r] * irho - v[r];
+  R fD = R(1);
+  if (a.k.drag_law) {
+    R re = Uv[0] * sqrt(rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2]) * d / mu;
+    fD = drag_factor<R>(1, re);
+  }
+  // F = m_p f_D (u - v) / tau_p with m_p / tau_p = 3 pi mu d
+  const R c = R(3.14159265358979323846) * R(3) * mu * d * fD;
+  R Fe = R(0);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    R Fr = c * rel[r];
+    f[r] = (float)(-Fr);
+    Fe -= Fr * v[r];
+  }
+  f[3] = (float)Fe;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    l1[i] = (float)lr1[i];
+    l2[i] = (float)lr2[i];
+    l3[i] = (float)lr3[i];
+  }
+  return true;
+}
+
+// FP32 atomics straight into S (S cleared beforehand)
+template <int G, int NP, bool F64>
+__global__ void __launch_bounds__(256) k_deposit_atomic(const DepositArgs a) {
+  constexpr int N3 = NP * NP * NP;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.p.n; t += stride) {
+    const int64_t ip = a.perm ? (int64_t)a.perm[t] : t;
+    int e;
+    float f[4], l1[NP], l2[NP], l3[NP];
+    if (!particle_source<G, NP, F64>(a, ip, e, f, l1, l2, l3)) continue;
+    float* Se = a.S + (size_t)e * 4 * N3;
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q)
+#pragma unroll 1
+      for (int kk = 0; kk < NP; ++kk)
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+          const float w = f[q] * l3[kk] * l2[j];
+#pragma unroll
+          for (int i = 0; i < NP; ++i) atomicAdd(Se + q * N3 + i + NP * (j + NP * kk), w * l1[i]);
+        }
+  }
+}
+
+// Deterministic segmented reduction: one block per element; the element's
+// particles (a segment of the element-sorted order) are put in index order,
+// their sources staged in shared memory, and every output node sums them in
+// that fixed order -- S_e[q][ijk] = sum_p f_q(p) l_i(p) l_j(p) l_k(p).
+constexpr int SEG_TILE = 128;
+template <int G, int NP, bool F64>
+__global__ void __launch_bounds__(256) k_deposit_segmented(const DepositArgs a) {
+  constexpr int N3 = NP * NP * NP;
+  __shared__ int idx[SEG_TILE];
+  __shared__ float sf[SEG_TILE][4];
+  __shared__ float sl[SEG_TILE][3][NP];
+  __shared__ int sok[SEG_TILE];
+  for (int e = blockIdx.x; e < a.m.nelem; e += gridDim.x) {
+    const int beg = a.offs[e], end = a.offs[e + 1];
+    // outputs owned by this thread: o = threadIdx.x + 256 * r, r < ceil(4 N3 / 256)
+    constexpr int NO = (4 * N3 + 255) / 256;
+    float acc[NO];
+#pragma unroll
+    for (int r = 0; r < NO; ++r) acc[r] = 0.f;
+    for (int c0 = beg; c0 < end; c0 += SEG_TILE) {
+      const int cnt = min(SEG_TILE, end - c0);
+      __syncthreads();
+      // rank-sort this chunk's particle indices (the segment order from the
+      // atomic scatter is arbitrary; index order makes the sum reproducible)
+      if (threadIdx.x < cnt) {
+        const int my = a.perm[c0 + threadIdx.x];
+        int rank = 0;
+        for (int j = 0; j < cnt; ++j) rank += a.perm[c0 + j] < my;
+        idx[rank] = my;
+      }
+      __syncthreads();
+      if (threadIdx.x < cnt) {
+        int ee;
+        float f[4], l1[NP], l2[NP], l3[NP];
+        bool ok = particle_source<G, NP, F64>(a, idx[threadIdx.x], ee, f, l1, l2, l3);
+        sok[threadIdx.x] = ok;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sf[threadIdx.x][q] = ok ? f[q] : 0.f;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          sl[threadIdx.x][0][i] = l1[i];
+          sl[threadIdx.x][1][i] = l2[i];
+          sl[threadIdx.x][2][i] = l3[i];
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < NO; ++r) {
+        const int o = threadIdx.x + 256 * r;
+        if (o < 4 * N3) {
+          const int q = o / N3, node = o - q * N3;
+          const int i = node % NP, j = (node / NP) % NP, kk = node / (NP * NP);
+          float s = acc[r];
+          for (int p = 0; p < cnt; ++p)
+            if (sok[p]) s = fmaf(sf[p][q] * sl[p][0][i], sl[p][1][j] * sl[p][2][kk], s);
+          acc[r] = s;
+        }
+      }
+    }
+    float* Se = a.S + (size_t)e * 4 * N3;
+#pragma unroll
+    for (int r = 0; r < NO; ++r) {
+      const int o = threadIdx.x + 256 * r;
+      if (o < 4 * N3) Se[o] = acc[r];
+    }
+  }
+}
+
+// launch helpers for one (G, mode) family
+template <int G, bool F64>
+struct Family {
+  template <int NP>
+  static int push(const PushArgs& a, int grid, int block, cudaStream_t s) {
+    k_push<G, NP, F64><<<grid, block, 0, s>>>(a);
+    return (int)cudaGetLastError();
+  }
+  template <int NP>
+  static int dep(int mode, const DepositArgs& a, int grid, int block, cudaStream_t s) {
+    if (mode == 0)
+      k_deposit_atomic<G, NP, F64><<<grid, block, 0, s>>>(a);
+    else
+      k_deposit_segmented<G, NP, F64><<<grid, 256, 0, s>>>(a);
+    return (int)cudaGetLastError();
+  }
+  template <int NP>
+  static int occ(int block) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<G, NP, F64>, block, 0);
+    return nb;
+  }
+  static int push_np(int np, const PushArgs& a, int grid, int block, cudaStream_t s) {
+    switch (np) {
+      case 2: return push<2>(a, grid, block, s);
+      case 3: return push<3>(a, grid, block, s);
+      case 4: return push<4>(a, grid, block, s);
+      case 5: return push<5>(a, grid, block, s);
+      case 6: return push<6>(a, grid, block, s);
+      case 7: return push<7>(a, grid, block, s);
+      case 8: return push<8>(a, grid, block, s);
+    }
+    return (int)cudaErrorInvalidValue;
+  }
+  static int dep_np(int np, int mode, const DepositArgs& a, int grid, int block, cudaStream_t s) {
+    switch (np) {
+      case 2: return dep<2>(mode, a, grid, block, s);
+      case 3: return dep<3>(mode, a, grid, block, s);
+      case 4: return dep<4>(mode, a, grid, block, s);
+      case 5: return dep<5>(mode, a, grid, block, s);
+      case 6: return dep<6>(mode, a, grid, block, s);
+      case 7: return dep<7>(mode, a, grid, block, s);
+      case 8: return dep<8>(mode, a, grid, block, s);
+    }
+    return (int)cudaErrorInvalidValue;
+  }
+  static int occ_np(int np, int block) {
+    switch (np) {
+      case 2: return occ<2>(block);
+      case 3: return occ<3>(block);
+      case 4: return occ<4>(block);
+      case 5: return occ<5>(block);
+      case 6: return occ<6>(block);
+      case 7: return occ<7>(block);
+      case 8: return occ<8>(block);
+    }
+    return 0;
+  }
+  static int locate(const LocateArgs& a, int grid, int block, cudaStream_t s) {
+    k_locate<G, F64><<<grid, block, 0, s>>>(a);
+    return (int)cudaGetLastError();
+  }
+};
+
+}  // namespace pt
+
+#define PT_DEFINE_FAMILY(G, F64, NAME)                                                       \
+  namespace pt {                                                                             \
+  int NAME##_push(int np, const PushArgs& a, int grid, int block, void* s) {                 \
+    return Family<G, F64>::push_np(np, a, grid, block, (cudaStream_t)s);                     \
+  }                                                                                          \
+  int NAME##_dep(int np, int mode, const DepositArgs& a, int grid, int block, void* s) {     \
+    return Family<G, F64>::dep_np(np, mode, a, grid, block, (cudaStream_t)s);                \
+  }                                                                                          \
+  int NAME##_occ(int np, int block) { return Family<G, F64>::occ_np(np, block); }            \
+  int NAME##_loc(const LocateArgs& a, int grid, int block, void* s) {                        \
+    return Family<G, F64>::locate(a, grid, block, (cudaStream_t)s);                          \
+  }                                                                                          \
+  }
