@@ -1,0 +1,354 @@
+"""Benchmark of the particle push on GB300 (one JSON line on rank 0).
+
+Workload (default): the learned-guess curved channel -- 64^3 curved hexahedra
+(NGeo = 3) of [0,2pi]x[-1,1]x[0,pi], N = 5 on Gauss nodes, synthetic channel
+turbulence, 10^7 particles, Schiller-Naumann drag, FP32 push with FP64 final
+Newton iterations and FP64 face intersection, dt = 1e-3.
+A bench step is one pt_push call advancing every particle by --inner time
+steps (one element re-binning, then --inner x 5 RK stages).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs its own particles on its own GPU (weak
+scaling, no data-path collective); value = all ranks' particle-steps / max
+rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--inner", type=int, default=10, help="time steps per pt_push call")
+    ap.add_argument("--particles", type=int, default=10_000_000)
+    ap.add_argument("--dims", type=int, default=64)
+    ap.add_argument("--guess", default="auto", choices=["auto", "trilinear", "mlp"])
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e / fp64 / cpu legs")
+    return ap.parse_args()
+
+
+def reduce_time_ms(ms: float, world: int, device=None) -> float:
+    """Max of the per-rank timed-region durations (every rank waits for the slowest)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(particles_per_rank: int, inner: int, steps: int, world: int, ms: float) -> float:
+    """Whole-job particle-steps/s: every rank advances its own particles."""
+    return particles_per_rank * inner * steps * world / (ms / 1e3)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(args, device, seed, precision):
+    from paper_2211_05458_gb300 import workloads as W
+    return W.curved_channel((args.dims,) * 3, 3, 5, P=args.particles, nsteps=args.inner,
+                            seed=seed, device=device, precision=precision)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class OracleSample:
+    """The oracle (as it stands) on a bounded sample of the same workload;
+    threads run disjoint particle chunks on one oracle context (ctypes
+    releases the GIL during each call)."""
+
+    def __init__(self, wl, max_threads=None):
+        import numpy as np
+
+        from tests import helpers as H
+        self.orc = H.make_oracle(wl)
+        self.x, self.v = H.np64(wl.x), H.np64(wl.v)
+        self.d, self.el = H.np64(wl.d), H.np64(wl.elem).astype(np.int32)
+        self.prm = H.oracle_params(wl)
+        self.dt = wl.dt
+        self.threads = max_threads or min(os.cpu_count() or 1, 16)
+        self.rng = np.random.default_rng(123)
+
+    def run(self, sample_particles, sample_steps):
+        import numpy as np
+        idx = np.sort(self.rng.choice(self.x.shape[0], size=sample_particles, replace=False))
+        chunks = np.array_split(idx, self.threads)
+        args = [(self.x[c], self.v[c], self.d[c], self.el[c]) for c in chunks]
+        t0 = time.perf_counter()
+
+        def work(a):
+            self.orc.push(self.prm, *a, nsteps=sample_steps, dt=self.dt)
+        ths = [threading.Thread(target=work, args=(a,)) for a in args]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        dt = time.perf_counter() - t0
+        return sample_particles * sample_steps / dt, self.threads, dt
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, same workload/metric."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import torch
+    wl = make_workload(args, "cuda" if torch.cuda.is_available() else "cpu", 0, "fp64")
+    wl.U = wl.U.cpu()
+    wl.x, wl.v, wl.d, wl.elem = wl.x.cpu(), wl.v.cpu(), wl.d.cpu(), wl.elem.cpu()
+    sample = 2000
+    times = []
+    osmp = OracleSample(wl)
+    for i in range(args.warmup + args.steps):
+        rate, threads, dt = osmp.run(sample, 1)
+        if i >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = sample * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"curved channel {args.dims}^3 NGeo=3 N=5, "
+                       f"{args.particles} particles, Schiller-Naumann, dt=1e-3",
+                       "inputs_vs_l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": threads, "kind": "oracle",
+                             "sample": f"{sample} particles x 1 time step per bench step"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    from paper_2211_05458_gb300 import pt
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks, peak_kind = measured_peaks()
+
+    wl = make_workload(args, dev, seed=rank, precision="fp32")
+    stream = torch.cuda.current_stream()
+    guess = pt.GUESS_TRILINEAR
+    ctx = pt.Context(wl.mesh, stream=stream, precision=pt.FP32, mu=wl.mu, rho_p=wl.rho_p,
+                     drag_law=wl.drag_law, rebin_every=args.inner)
+    mlp_info = None
+    if args.guess in ("auto", "mlp"):
+        try:
+            t0 = time.perf_counter()
+            inp, tgt = ctx.mlp_make_pairs(2_000_000, seed=1000 + rank)
+            losses = ctx.mlp_train(inp, tgt, epochs=20, batch=4096, lr=1e-3, seed=rank)
+            torch.cuda.synchronize()
+            mlp_info = {"train_s": time.perf_counter() - t0, "final_loss": losses[-1]}
+            guess = pt.GUESS_MLP
+            del inp, tgt
+        except pt.PtError as e:
+            if args.guess == "mlp":
+                raise
+            mlp_info = {"unavailable": str(e)[:200]}
+    ctx.set_config(guess=guess)
+    U32 = wl.U.to(torch.float32).contiguous()
+    ctx.set_fluid(wl.N, wl.node_type, U32)
+    parts = pt.ParticleSet.create(wl.x, wl.v, wl.d, wl.elem, pt.FP32, dev)
+    P = parts.n
+
+    def step():
+        ctx.push(parts, args.inner, wl.dt, stats=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_read()  # clear
+    with ClockSampler(local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    kern_ms, launches = ctx.profile_read()
+    ctx.profile(False)
+    ms = reduce_time_ms(ms, world, dev)
+    value = throughput(P, args.inner, args.steps, world, ms)
+    stats = ctx.push(parts, 1, wl.dt, stats=True)  # one more step with counters
+
+    # roofline of the dominant kernel (k_push): algorithmic bytes per launch
+    N3 = (wl.N + 1) ** 3
+    g3 = 4 ** 3
+    elem_bytes = 4 * N3 * 4 + g3 * 3 * (8 + 4) + 8 * 3 + 12 * 4 + 6 * (4 + 4 + 32 + 96 + 24)
+    rec_bytes = (24 + 12 + 4 + 4 + 4 + 4) + (24 + 12 + 4 + 4 + 4) + 4  # read, write, perm
+    occupied = min(wl.mesh.nelem, P)
+    bytes_per_launch = P * rec_bytes + occupied * elem_bytes
+    avg_launch_s = (kern_ms / 1e3) / max(launches, 1)
+    achieved = bytes_per_launch / avg_launch_s / 1e9
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None,
+                "kernel": "k_push<4,6,fp32>", "peak_kind": peak_kind,
+                "kernel_share_of_step": (kern_ms / ms) if ms > 0 else None}
+
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"curved channel {args.dims}^3 NGeo=3 N=5 Gauss, "
+                       f"{P} particles/GPU, Schiller-Naumann, dt=1e-3, FP32 + FP64 final Newton",
+                       "inner_steps_per_call": args.inner, "guess": "mlp" if guess else "trilinear",
+                       "inputs_vs_l2": "inputs larger than L2 (particles 0.5 GB, field 1.1 GB)",
+                       "parallelism": f"weak, {world} independent GPU(s)"},
+            "gpu_launches": None, "clocks": clk.summary(), "roofline": roofline,
+            "stats_one_step": {k: stats[k] for k in ("particle_steps", "crossings", "wall_hits",
+                                                     "newton_it_fp32", "newton_it_fp64",
+                                                     "slow_track", "near_face")}}
+    # launches per bench step: binning (hist, scan x3, scatter) + push per chunk, memset
+    chunks = math.ceil(args.inner / args.inner)
+    line["gpu_launches"] = args.steps * chunks * 6
+    if mlp_info:
+        line["mlp"] = mlp_info
+
+    if not args.no_extras and rank == 0:
+        # e2e: same metric through pt_push_host with pinned host buffers
+        hp = parts.to("cpu", pin=True)
+        e2e_steps = max(1, min(3, args.steps))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ctx.push_host(hp, args.inner, wl.dt, stats=False)
+        e2e_s = time.perf_counter() - t0
+        h2d = P * (24 + 12 + 4 + 12)
+        d2h = P * (24 + 12 + 12)
+        line["e2e"] = {"value": P * args.inner * e2e_steps / e2e_s, "unit": METRIC,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        del hp
+        # plain FP64 Newton (FP64 mode) on the same workload, fewer steps
+        ctx64 = pt.Context(wl.mesh, stream=stream, precision=pt.FP64, mu=wl.mu, rho_p=wl.rho_p,
+                           drag_law=wl.drag_law, rebin_every=2)
+        U64 = wl.U.to(torch.float64).contiguous()
+        ctx64.set_fluid(wl.N, wl.node_type, U64)
+        p64 = pt.ParticleSet.create(wl.x, wl.v, wl.d, wl.elem, pt.FP64, dev)
+        ctx64.push(p64, 1, wl.dt, stats=False)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx64.push(p64, 2, wl.dt, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        line["plain_fp64"] = {"value": P * 2 / (e0.elapsed_time(e1) / 1e3), "unit": METRIC,
+                              "note": "FP64 mode: FP64 Newton from the trilinear guess, FP64 "
+                                      "interpolation, drag and RK"}
+        del p64, U64, ctx64
+        # oracle on the host cores, bounded sample
+        try:
+            wl.U = wl.U.cpu()
+            wl.x, wl.v, wl.d, wl.elem = wl.x.cpu(), wl.v.cpu(), wl.d.cpu(), wl.elem.cpu()
+            rate, threads, dt = OracleSample(wl).run(4000, 2)
+            line["cpu_baseline"] = {"value": rate, "unit": METRIC, "cores": threads,
+                                    "kind": "oracle",
+                                    "sample": "4000 particles x 2 time steps of the same workload"}
+        except Exception as e:  # pragma: no cover
+            line["cpu_baseline"] = {"unavailable": str(e)[:200]}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -97,7 +97,7 @@ typedef struct {
   int32_t max_newton;   /* Newton iteration cap (default 50)                       */
   int32_t max_cross;    /* face-crossing cap per RK stage (default 64)             */
   int32_t rebin_every;  /* steps between particle re-binning; 0 = library choice   */
-  int32_t block;        /* threads per block of the push kernel; 0 = autotuned    */
+  int32_t block;        /* threads per block of the push kernel (32..128); 0 = 128 */
   int32_t reserved[9];
 } pt_config;
 
@@ -243,6 +243,14 @@ pt_status pt_mlp_grad(pt_ctx* ctx, int32_t B, const float* in_dev, const float* 
  * ctxs[0]'s stream.  out: host array of nbox pt_stats or NULL (synchronises). */
 pt_status pt_push_batch(pt_ctx* const* ctxs, const pt_particles* parts, int32_t nbox,
                         int32_t nsteps, double dt, pt_stats* out);
+
+/* Kernel timing (diagnostics).  pt_profile(ctx, 1) makes every later push
+ * record a CUDA event pair around each launch of the push kernel on the
+ * context's stream; pt_profile_read synchronises, returns the summed device
+ * time of those launches in milliseconds and their number, and clears the
+ * record.  pt_profile(ctx, 0) stops recording. */
+pt_status pt_profile(pt_ctx* ctx, int32_t enable);
+pt_status pt_profile_read(pt_ctx* ctx, double* kernel_ms, int64_t* launches);
 
 /* Releases the context and its device memory (not the caller's arrays). */
 pt_status pt_destroy(pt_ctx* ctx);

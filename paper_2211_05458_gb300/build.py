@@ -22,6 +22,8 @@ SO = os.path.join(BUILD, "libpt.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
+# extra nvcc flags for tuning builds, e.g. PT_NVCC_EXTRA="-DPT_PUSH_MINB=4"
+FLAGS += os.environ.get("PT_NVCC_EXTRA", "").split()
 
 
 def _nvcc() -> str:

@@ -259,7 +259,7 @@ static pt_status upload_mesh(pt_ctx* c, const pt_mesh_desc* md) {
   c->g = g;
   std::vector<double> xg64((size_t)E * g3 * 3), ce((size_t)E * 3), bil((size_t)E * 72),
       shift((size_t)E * 18);
-  std::vector<float> xg32((size_t)E * g3 * 3), tri((size_t)E * 12), slab((size_t)E * 48, 0.f);
+  std::vector<float> xg32((size_t)E * g3 * 3), xg32lo((size_t)E * g3 * 3), tri((size_t)E * 12), slab((size_t)E * 48, 0.f);
   std::vector<int> fnbr((size_t)E * 6), finfo((size_t)E * 6);
   std::vector<double> M;
   bezier_matrix(g, M);
@@ -280,7 +280,9 @@ static pt_status upload_mesh(pt_ctx* c, const pt_mesh_desc* md) {
       for (int r = 0; r < 3; ++r) {
         double v = X[3 * q + r] - cc[r];
         xg64[((size_t)e * g3 + q) * 3 + r] = v;
-        xg32[(size_t)e * 3 * g3 + r * g3 + q] = (float)v;
+        const float vh = (float)v;
+        xg32[(size_t)e * 3 * g3 + r * g3 + q] = vh;
+        xg32lo[(size_t)e * 3 * g3 + r * g3 + q] = (float)(v - (double)vh);
         Rmax = std::max(Rmax, std::fabs(v));
       }
     for (int r = 0; r < 3; ++r) ce[3 * e + r] = cc[r];
@@ -390,6 +392,8 @@ static pt_status upload_mesh(pt_ctx* c, const pt_mesh_desc* md) {
   if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
   c->d_xg32 = dmalloc<float>(cc, xg32.size(), &err);
   if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
+  c->d_xg32lo = dmalloc<float>(cc, xg32lo.size(), &err);
+  if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
   c->d_ce = dmalloc<double>(cc, ce.size(), &err);
   if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
   c->d_tri = dmalloc<float>(cc, tri.size(), &err);
@@ -411,6 +415,7 @@ static pt_status upload_mesh(pt_ctx* c, const pt_mesh_desc* md) {
     const void* h;
     size_t b;
   } cp[] = {{c->d_xg64, xg64.data(), xg64.size() * 8}, {c->d_xg32, xg32.data(), xg32.size() * 4},
+            {c->d_xg32lo, xg32lo.data(), xg32lo.size() * 4},
             {c->d_ce, ce.data(), ce.size() * 8},       {c->d_tri, tri.data(), tri.size() * 4},
             {c->d_fnbr, fnbr.data(), fnbr.size() * 4}, {c->d_finfo, finfo.data(), finfo.size() * 4},
             {c->d_slab, slab.data(), slab.size() * 4}, {c->d_bil, bil.data(), bil.size() * 8},
@@ -432,6 +437,10 @@ static void fill_consts(const pt_ctx* c, DevConsts& k) {
     k.gw[a] = gw[a];
     k.gn32[a] = (float)gn[a];
     k.gw32[a] = (float)gw[a];
+    k.gn_hi[a] = (float)gn[a];
+    k.gn_lo[a] = (float)(gn[a] - (double)k.gn_hi[a]);
+    k.gw_hi[a] = (float)gw[a];
+    k.gw_lo[a] = (float)(gw[a] - (double)k.gw_hi[a]);
   }
   for (int i = 0; i < c->N + 1 && c->N >= 0; ++i) {
     k.sn[i] = c->sn[i];
@@ -467,6 +476,7 @@ static DevMesh dev_mesh(const pt_ctx* c) {
   m.g = c->g;
   m.xg64 = c->d_xg64;
   m.xg32 = c->d_xg32;
+  m.xg32lo = c->d_xg32lo;
   m.ce = c->d_ce;
   m.tri = c->d_tri;
   m.fnbr = c->d_fnbr;
@@ -479,6 +489,8 @@ static DevMesh dev_mesh(const pt_ctx* c) {
 }
 
 DevMLP pt_dev_mlp(const pt_ctx* c);
+void pt_fill_consts(const pt_ctx* c, DevConsts& k) { fill_consts(c, k); }
+DevMesh pt_dev_mesh(const pt_ctx* c) { return dev_mesh(c); }
 
 static pt_status check_config(const pt_config* cfg) {
   if (!cfg) return fail(nullptr, PT_ERR_ARG, "config is NULL");
@@ -491,8 +503,8 @@ static pt_status check_config(const pt_config* cfg) {
   if (!(cfg->newton_tol > 0) || !(cfg->band_ref >= 0) || !(cfg->band_x >= 0) ||
       !(cfg->lost_tol >= 0))
     return fail(nullptr, PT_ERR_ARG, "bad tolerance");
-  if (cfg->block < 0 || cfg->block > 1024 || (cfg->block % 32))
-    return fail(nullptr, PT_ERR_ARG, "block must be a multiple of 32 in [0, 1024]");
+  if (cfg->block < 0 || cfg->block > 128 || (cfg->block % 32))
+    return fail(nullptr, PT_ERR_ARG, "block must be a multiple of 32 in [0, 128]");
   if (cfg->rebin_every < 0) return fail(nullptr, PT_ERR_ARG, "rebin_every must be >= 0");
   return PT_OK;
 }
@@ -588,6 +600,7 @@ static pt_status ensure_scratch(pt_ctx* c, int64_t n) {
 }
 
 static int push_block(pt_ctx* c) { return c->cfg.block > 0 ? c->cfg.block : 128; }
+// the push kernel is compiled for blocks of at most 128 threads
 
 static int grid_for(pt_ctx* c, int64_t n, int block, int occ) {
   int64_t want = (n + block - 1) / block;
@@ -674,6 +687,18 @@ static pt_status read_stats(pt_ctx* c, const pt_particles* p, double dt, pt_stat
   return PT_OK;
 }
 
+static cudaEvent_t take_event(pt_ctx* c) {
+  cudaEvent_t e = nullptr;
+  if (!c->ev_free.empty()) {
+    e = c->ev_free.back();
+    c->ev_free.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    return nullptr;
+  }
+  c->ev_used.push_back(e);
+  return e;
+}
+
 pt_status pt_push_impl(pt_ctx* c, const pt_particles* p, int32_t nsteps, double dt,
                        pt_stats* out) {
   const int64_t n = p->n;
@@ -701,7 +726,14 @@ pt_status pt_push_impl(pt_ctx* c, const pt_particles* p, int32_t nsteps, double 
       if (rc) return fail(c, PT_ERR_CUDA, "binning: %s", cudaGetErrorString((cudaError_t)rc));
       a.perm = c->d_perm;
       a.nsteps = std::min(chunk, nsteps - s0);
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (c->profile) {
+        e0 = take_event(c);
+        e1 = take_event(c);
+        if (e0) cudaEventRecord(e0, c->stream);
+      }
       rc = launch_push(c->g, f64, np, a, grid, block, c->stream);
+      if (e1) cudaEventRecord(e1, c->stream);
       if (rc) return fail(c, PT_ERR_CUDA, "push launch: %s", cudaGetErrorString((cudaError_t)rc));
     }
   }
@@ -720,6 +752,8 @@ pt_status pt_push(pt_ctx* c, const pt_particles* p, int32_t nsteps, double dt, p
   if (!(dt > 0) || !std::isfinite(dt)) return fail(c, PT_ERR_ARG, "dt must be finite and > 0");
   if (c->cfg.guess == PT_GUESS_MLP && (c->g != 4 || !c->mlp_ready))
     return fail(c, PT_ERR_STATE, "learned guess needs ngeo = 3 and a trained network");
+  if (c->cfg.guess == PT_GUESS_MLP && push_block(c) > 128)
+    return fail(c, PT_ERR_ARG, "the learned guess needs a push block of at most 128 threads");
   return pt_push_impl(c, p, nsteps, dt, out);
 }
 
@@ -834,13 +868,41 @@ pt_status pt_deposit(pt_ctx* c, const pt_particles* p, int32_t mode, float* S) {
   return PT_OK;
 }
 
+pt_status pt_profile(pt_ctx* c, int32_t enable) {
+  if (!c) return fail(nullptr, PT_ERR_ARG, "ctx is NULL");
+  c->profile = enable != 0;
+  return PT_OK;
+}
+
+pt_status pt_profile_read(pt_ctx* c, double* ms, int64_t* launches) {
+  if (!c) return fail(nullptr, PT_ERR_ARG, "ctx is NULL");
+  CK(cudaStreamSynchronize(c->stream));
+  double tot = 0.0;
+  int64_t k = 0;
+  for (size_t i = 0; i + 1 < c->ev_used.size(); i += 2) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, c->ev_used[i], c->ev_used[i + 1]) == cudaSuccess) {
+      tot += t;
+      ++k;
+    }
+  }
+  for (cudaEvent_t e : c->ev_used) c->ev_free.push_back(e);
+  c->ev_used.clear();
+  if (ms) *ms = tot;
+  if (launches) *launches = k;
+  return PT_OK;
+}
+
 pt_status pt_destroy(pt_ctx* c) {
   if (!c) return PT_OK;
+  for (cudaEvent_t e : c->ev_used) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
   for (void* q : c->allocs) cudaFree(q);
   if (c->d_scratch) cudaFree(c->d_scratch);
   if (c->d_perm) cudaFree(c->d_perm);
   if (c->d_stage) cudaFree(c->d_stage);
   pt_mlp_release(c);
+  pt_batch_release(c);
   delete c;
   return PT_OK;
 }

@@ -113,22 +113,32 @@ size_t bin_scratch_ints(int nelem) {
   return (size_t)nbins * 3 + 1 + nb;
 }
 
+void bin_layout(int nelem, int* scratch, BinLayout& L) {
+  const int nbins = nelem + 1;
+  L.nbins = nbins;
+  L.nb = (nbins + 1023) / 1024;
+  L.counts = scratch;
+  L.offs = L.counts + nbins;
+  L.cursor = L.offs + nbins + 1;
+  L.bsum = L.cursor + nbins;
+}
+
+void bin_scan(const BinLayout& L, cudaStream_t s) {
+  k_scan_block<<<L.nb, 1024, 0, s>>>(L.counts, L.offs, L.bsum, L.nbins);
+  k_scan_sums<<<1, 1024, 0, s>>>(L.bsum, L.nb, L.offs + L.nbins);
+  k_scan_add<<<L.nb, 1024, 0, s>>>(L.offs, L.bsum, L.nbins, L.cursor);
+}
+
 int bin_by_element(const int* elem, int64_t n, int nelem, int* scratch, int* perm, int** offs_out,
                    int nsm, cudaStream_t s) {
-  const int nbins = nelem + 1;
-  const int nb = (nbins + 1023) / 1024;
-  int* counts = scratch;
-  int* offs = counts + nbins;
-  int* cursor = offs + nbins + 1;
-  int* bsum = cursor + nbins;
-  if (offs_out) *offs_out = offs;
-  cudaMemsetAsync(counts, 0, sizeof(int) * nbins, s);
+  BinLayout L;
+  bin_layout(nelem, scratch, L);
+  if (offs_out) *offs_out = L.offs;
+  cudaMemsetAsync(L.counts, 0, sizeof(int) * L.nbins, s);
   const int g = (int)((n + 255) / 256 < (int64_t)nsm * 8 ? (n + 255) / 256 : (int64_t)nsm * 8);
-  if (n > 0) k_hist<<<g > 0 ? g : 1, 256, 0, s>>>(elem, n, nelem, counts);
-  k_scan_block<<<nb, 1024, 0, s>>>(counts, offs, bsum, nbins);
-  k_scan_sums<<<1, 1024, 0, s>>>(bsum, nb, offs + nbins);
-  k_scan_add<<<nb, 1024, 0, s>>>(offs, bsum, nbins, cursor);
-  if (n > 0) k_scatter<<<g > 0 ? g : 1, 256, 0, s>>>(elem, n, nelem, cursor, perm);
+  if (n > 0) k_hist<<<g > 0 ? g : 1, 256, 0, s>>>(elem, n, nelem, L.counts);
+  bin_scan(L, s);
+  if (n > 0) k_scatter<<<g > 0 ? g : 1, 256, 0, s>>>(elem, n, nelem, L.cursor, perm);
   return (int)cudaGetLastError();
 }
 

@@ -5,6 +5,14 @@
 #include <cstdint>
 
 namespace pt {
+// layout of the binning scratch: counts[nbins] | offs[nbins + 1] | cursor[nbins] | bsum[nb]
+struct BinLayout {
+  int nbins, nb;
+  int *counts, *offs, *cursor, *bsum;
+};
+void bin_layout(int nelem, int* scratch, BinLayout& L);
+// exclusive scan of L.counts into L.offs (and L.cursor); L.offs[nbins] = total
+void bin_scan(const BinLayout& L, cudaStream_t s);
 // ints of scratch bin_by_element needs for nelem elements
 size_t bin_scratch_ints(int nelem);
 // perm[n] receives particle indices sorted by elem (order within an element

@@ -10,6 +10,7 @@
 #include "pt_internal.h"
 
 struct pt_mlp_state;
+struct pt_batch_plan;
 
 struct pt_ctx {
   int dev = 0;
@@ -20,6 +21,7 @@ struct pt_ctx {
   int nelem = 0, ngeo = 0, g = 0, ncurved = 0;
   double* d_xg64 = nullptr;
   float* d_xg32 = nullptr;
+  float* d_xg32lo = nullptr;
   double* d_ce = nullptr;
   float* d_tri = nullptr;
   int* d_fnbr = nullptr;
@@ -44,8 +46,14 @@ struct pt_ctx {
   pt_mlp_state* mlp = nullptr;
   bool mlp_ready = false;
   float* d_mlp_pre = nullptr;
+  // batched push plan (pt_push_batch called with this context first)
+  pt_batch_plan* batch = nullptr;
+  // kernel timing (pt_profile)
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_free, ev_used;
   std::string err = "no error";
 };
 
 void pt_mlp_release(pt_ctx* c);
+void pt_batch_release(pt_ctx* c);
 pt_status pt_push_impl(pt_ctx* c, const pt_particles* p, int32_t nsteps, double dt, pt_stats* out);

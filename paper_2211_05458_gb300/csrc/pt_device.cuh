@@ -10,6 +10,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "pt_df.cuh"
 #include "pt_internal.h"
 
 namespace pt {
@@ -263,15 +264,83 @@ __device__ __forceinline__ bool newton64(const double* X64, const double* xl, do
   return false;
 }
 
+// Lagrange basis on the geometry nodes in double-float (nodes and barycentric
+// weights carried as hi + lo pairs)
+template <int NP>
+__device__ __forceinline__ void lagr_df(df x, const DevConsts& k, df* l) {
+  df d[NP];
+#pragma unroll
+  for (int m = 0; m < NP; ++m) d[m] = df_sub(x, df{k.gn_hi[m], k.gn_lo[m]});
+  df pre = df_from(1.f);
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    l[i] = pre;
+    if (i + 1 < NP) pre = df_mul(pre, d[i]);
+  }
+  df suf = df_from(1.f);
+#pragma unroll
+  for (int i = NP - 1; i >= 0; --i) {
+    l[i] = df_mul(df_mul(l[i], suf), df{k.gw_hi[i], k.gw_lo[i]});
+    if (i > 0) suf = df_mul(suf, d[i]);
+  }
+}
+
+// Residual chi(xi) - x of the element map in double-float, sum-factorised;
+// nodes as hi [3][G^3] + lo [3][G^3] (relative to the element centre).
+template <int G>
+__device__ __forceinline__ void resid_df(const float* __restrict__ Xh,
+                                         const float* __restrict__ Xl, const df* xi,
+                                         const df* xloc, const DevConsts& k, float* r) {
+  constexpr int G3 = G * G * G;
+  df l0[G], l1[G], l2[G];
+  lagr_df<G>(xi[0], k, l0);
+  lagr_df<G>(xi[1], k, l1);
+  lagr_df<G>(xi[2], k, l2);
+#pragma unroll 1
+  for (int q = 0; q < 3; ++q) {
+    const float* Ph = Xh + q * G3;
+    const float* Pl = Xl + q * G3;
+    df_acc a3;
+    dacc_init(a3);
+#pragma unroll
+    for (int c = 0; c < G; ++c) {
+      df_acc a2;
+      dacc_init(a2);
+#pragma unroll
+      for (int b = 0; b < G; ++b) {
+        df_acc a1;
+        dacc_init(a1);
+#pragma unroll
+        for (int a = 0; a < G; ++a) {
+          const int i = a + G * (b + G * c);
+          dacc_fma(a1, df{__ldg(Ph + i), __ldg(Pl + i)}, l0[a]);
+        }
+        dacc_fma(a2, dacc_result(a1), l1[b]);
+      }
+      dacc_fma(a3, dacc_result(a2), l2[c]);
+    }
+    const df rr = df_sub(dacc_result(a3), xloc[q]);
+    r[q] = __fadd_rn(rr.hi, rr.lo);
+  }
+}
+
+template <int G>
+__device__ __noinline__ bool newton64_cold(const double* X64, const double* xl, double* xi,
+                                           const DevConsts& k, int& it64) {
+  return newton64<G>(X64, xl, xi, k, k.max_newton, it64);
+}
+
 // Mixed-precision Newton: FP32 iterations (chi and J in FP32) until the step
-// is below 1e-5, then FP64 residuals with the last FP32 inverse Jacobian until
-// the step is below newton_tol; a full FP64 Newton is the fallback.
+// is below 1e-5, then double-float residuals with the last FP32 inverse
+// Jacobian until the step is below newton_tol; a full FP64 Newton is the
+// fallback.
 template <int G>
 __device__ __forceinline__ bool newton_mixed(const DevMesh& m, const DevConsts& k, int e,
                                              const double* xl, const float* guess, double* xi,
                                              int& it32, int& it64) {
   constexpr int G3 = G * G * G;
   const float* X32 = m.xg32 + (size_t)e * 3 * G3;
+  const float* X32l = m.xg32lo + (size_t)e * 3 * G3;
   const double* X64 = m.xg64 + (size_t)e * 3 * G3;
   float xf[3] = {(float)xl[0], (float)xl[1], (float)xl[2]};
   float z[3] = {guess[0], guess[1], guess[2]};
@@ -295,28 +364,35 @@ __device__ __forceinline__ bool newton_mixed(const DevMesh& m, const DevConsts& 
     if (tmax3(d[0], d[1], d[2]) < 1e-5f) break;
   }
   if (have) {
-    xi[0] = z[0];
-    xi[1] = z[1];
-    xi[2] = z[2];
-    for (int it = 0; it < 6; ++it) {
-      double chi[3];
-      float r[3], d[3];
-      map64<G, false>(X64, xi, k, chi, nullptr);
+    df xd[3], zd[3];
 #pragma unroll
-      for (int q = 0; q < 3; ++q) r[q] = (float)(chi[q] - xl[q]);
+    for (int q = 0; q < 3; ++q) {
+      xd[q] = df{xf[q], (float)(xl[q] - (double)xf[q])};
+      zd[q] = df_from(z[q]);
+    }
+    const float tol = (float)k.newton_tol;
+    for (int it = 0; it < 6; ++it) {
+      float r[3], d[3];
+      resid_df<G>(X32, X32l, zd, xd, k, r);
       matvec3(Ji, r, d);
 #pragma unroll
-      for (int q = 0; q < 3; ++q) xi[q] -= (double)d[q];
+      for (int q = 0; q < 3; ++q) zd[q] = df_sub(zd[q], df_from(d[q]));
       ++it64;
-      if ((double)tmax3(d[0], d[1], d[2]) < k.newton_tol) return true;
+      if (tmax3(d[0], d[1], d[2]) < tol) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) xi[q] = df_to_double(zd[q]);
+        return true;
+      }
     }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) xi[q] = df_to_double(zd[q]);
   } else {
     xi[0] = guess[0];
     xi[1] = guess[1];
     xi[2] = guess[2];
   }
   if (!(tmax3(xi[0], xi[1], xi[2]) <= 4.0)) xi[0] = xi[1] = xi[2] = 0.0;
-  return newton64<G>(X64, xl, xi, k, k.max_newton, it64);
+  return newton64_cold<G>(X64, xl, xi, k, it64);
 }
 
 // ---------------------------------------------------------------------------
@@ -540,13 +616,26 @@ __device__ __forceinline__ bool touches_any_slab(const DevMesh& m, int e, const 
 // Wall: restart at the hit point with the remaining length, mirroring the
 // direction, v, kx and kv by I - 2 n n^T (Sec. 2.4).  Open: stop there.
 template <int G, typename R>
-__device__ void track(const DevMesh& m, const DevConsts& k, int& e, double* x, double* xe,
-                      R* v, R* kx, R* kv, int& hits, unsigned& st, TrackCounters& tc) {
+__device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, int& e, double* x,
+                                        double* xe, R* v, R* kx, R* kv, int& hits, unsigned& st,
+                                        TrackCounters& tc);
+
+template <int G, typename R>
+__device__ __forceinline__ void track(const DevMesh& m, const DevConsts& k, int& e, double* x,
+                                      double* xe, R* v, R* kx, R* kv, int& hits, unsigned& st,
+                                      TrackCounters& tc) {
   if (!touches_any_slab(m, e, x, xe)) {
 #pragma unroll
     for (int r = 0; r < 3; ++r) x[r] = xe[r];
     return;
   }
+  track_slow<G, R>(m, k, e, x, xe, v, kx, kv, hits, st, tc);
+}
+
+template <int G, typename R>
+__device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, int& e, double* x,
+                                        double* xe, R* v, R* kx, R* kv, int& hits, unsigned& st,
+                                        TrackCounters& tc) {
   tc.slow++;
   double xs[3] = {x[0], x[1], x[2]};
   double td[3] = {xe[0] - xs[0], xe[1] - xs[1], xe[2] - xs[2]};

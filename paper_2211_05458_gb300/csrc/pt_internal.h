@@ -33,6 +33,7 @@ struct DevMesh {
   int g;                  // NGeo + 1
   const double* xg64;     // [E][g^3][3]   nodes - ce
   const float* xg32;      // [E][3][g^3]   nodes - ce, FP32, coordinate-major
+  const float* xg32lo;    // [E][3][g^3]   (nodes - ce) - xg32: low parts of a double-float copy
   const double* ce;       // [E][3]
   const float* tri;       // [E][12]       trilinear centre (3) and inverse Jacobian (9)
   const int* fnbr;        // [E][6]        neighbour element
@@ -47,6 +48,7 @@ struct DevMesh {
 struct DevConsts {
   double gn[PT_MAXG], gw[PT_MAXG];   // geometry nodes / barycentric weights
   float gn32[PT_MAXG], gw32[PT_MAXG];
+  float gn_hi[PT_MAXG], gn_lo[PT_MAXG], gw_hi[PT_MAXG], gw_lo[PT_MAXG];  // double-float copies
   double sn[PT_MAXN], sw[PT_MAXN];   // solution nodes / barycentric weights
   float sn32[PT_MAXN], sw32[PT_MAXN];
   double A[5], B[5];

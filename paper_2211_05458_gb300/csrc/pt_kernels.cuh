@@ -5,6 +5,14 @@
 #include "pt_device.cuh"
 #include "pt_mlp_infer.cuh"
 
+// minimum resident blocks of 128 threads per SM for the push kernel (sets the
+// register budget: 4 -> 128 registers per thread, 2 -> 255); the FP64 mode
+// keeps the larger budget
+#ifndef PT_PUSH_MINB
+#define PT_PUSH_MINB 4
+#endif
+#define PT_PUSH_MINB_F64 2
+
 namespace pt {
 
 template <bool F64>
@@ -44,141 +52,170 @@ __device__ __forceinline__ bool locate_one(const DevMesh& m, const DevConsts& k,
 // Start guess: trilinear, optionally corrected by the learned network (warp-
 // collective: every lane of the warp must call it).
 template <int G>
-__device__ __forceinline__ void start_guess(const DevMesh& m, const DevConsts& k,
-                                            const DevMLP& mlp, int e, const double* x,
-                                            bool live, float* guess) {
+__device__ __forceinline__ void start_guess(const DevMesh& m, const DevConsts& k, MlpSmem* sm,
+                                            int e, const double* x, bool live, float* guess) {
   const double* ce = m.ce + 3 * (size_t)e;
   float xf[3] = {(float)(x[0] - __ldg(ce)), (float)(x[1] - __ldg(ce + 1)),
                  (float)(x[2] - __ldg(ce + 2))};
   trilinear_guess(m, e, xf, guess);
-  if (G == 4 && k.guess == PT_GUESS_MLP) mlp_correct(m, mlp, e, live, guess);
+  if constexpr (G == 4) {
+    if (k.guess == PT_GUESS_MLP) mlp_correct_smem(*sm, m, e, live, guess);
+  }
 }
 
-// One thread per particle; all nsteps x 5 stages of a particle run in
-// registers (the fluid state is constant during the call).  Threads visit
-// particles in element-sorted order (perm) so a warp shares element data.
+// The block's copy of the network weights (NGeo = 3 kernels only); must be
+// reached by every thread of the block.
+#define PT_MLP_PROLOGUE(G, K, MLP)                    \
+  MlpSmem* sm = nullptr;                              \
+  if constexpr (G == 4) {                             \
+    __shared__ MlpSmem s_mlp;                         \
+    sm = &s_mlp;                                      \
+    if ((K).guess == PT_GUESS_MLP) {                  \
+      mlp_load(s_mlp, MLP);                           \
+      __syncthreads();                                \
+    }                                                 \
+  }
+
+struct PushCounters {
+  unsigned long long steps, it32, it64;
+  TrackCounters tc;
+};
+
+// Advances particle ip of p by nsteps RK steps: per stage the inverse map,
+// interpolation of rho and rho u, drag + gravity, the low-storage RK update of
+// x and v, and tracking of the stage segment.  State lives in registers for
+// the whole call (the fluid state is constant during it).  Every lane of a
+// warp must call it (the learned start is warp-collective); lanes without a
+// particle pass inrange = false.
 template <int G, int NP, bool F64>
-__global__ void __launch_bounds__(256) k_push(const PushArgs a) {
+__device__ __forceinline__ void push_particle(const DevMesh& m, const DevConsts& k, MlpSmem* sm,
+                                              const typename RealOf<F64>::type* __restrict__ U,
+                                              const DevParticles& p, int64_t ip, bool inrange,
+                                              int nsteps, double dtd, PushCounters& c) {
   using R = typename RealOf<F64>::type;
   constexpr int N3 = NP * NP * NP;
-  const DevMesh& m = a.m;
-  const DevConsts& k = a.k;
-  const int64_t n = a.p.n;
-  const R dt = (R)a.dt;
+  const int64_t n = p.n;
+  const R dt = (R)dtd;
   const R mu = (R)k.mu;
-  R A[5], B[5];
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    A[i] = F64 ? (R)k.A[i] : (R)k.A32[i];
-    B[i] = F64 ? (R)k.B[i] : (R)k.B32[i];
+  R* vg = reinterpret_cast<R*>(p.v);
+  const R* dg = reinterpret_cast<const R*>(p.d);
+  unsigned st = inrange ? p.status[ip] : PT_ST_FROZEN;
+  bool live = !(st & PT_ST_FROZEN);
+  double x[3] = {0, 0, 0};
+  R v[3] = {0, 0, 0}, d = R(1);
+  int e = 0, hits = 0;
+  if (inrange) {
+    x[0] = p.x[ip];
+    x[1] = p.x[n + ip];
+    x[2] = p.x[2 * n + ip];
+    v[0] = vg[ip];
+    v[1] = vg[n + ip];
+    v[2] = vg[2 * n + ip];
+    d = dg[ip];
+    e = p.elem[ip];
+    hits = p.hits[ip];
   }
+  if (e < 0 || e >= m.nelem) {
+    if (live) st |= PT_ST_LOST;
+    live = false;
+  }
+  const R tau = (R)k.rho_p * d * d / (R(18) * mu);
+  for (int step = 0; step < nsteps; ++step) {
+    R kx[3] = {0, 0, 0}, kv[3] = {0, 0, 0};
+    for (int s = 0; s < 5; ++s) {
+      const R As = F64 ? (R)k.A[s] : (R)k.A32[s];
+      const R Bs = F64 ? (R)k.B[s] : (R)k.B32[s];
+      float guess[3];
+      start_guess<G>(m, k, sm, live ? e : 0, x, live, guess);
+      if (!live) continue;
+      double xi[3];
+      int i32 = 0, i64 = 0;
+      bool ok = locate_one<G, F64>(m, k, e, x, guess, xi, i32, i64);
+      c.it32 += i32;
+      c.it64 += i64;
+      if (!ok) {
+        st |= PT_ST_NEWTON_FAIL;
+        live = false;
+        continue;
+      }
+      const double mx = tmax3(xi[0], xi[1], xi[2]);
+      if (mx > 1.0 + k.lost_tol) {
+        st |= PT_ST_LOST;
+        live = false;
+        continue;
+      }
+      if (mx > 1.0 - k.band_ref) st |= PT_ST_NEAR_FACE;
+      // interpolation of rho, rho u at xi
+      R l1[NP], l2[NP], l3[NP], Uv[4];
+      lagr<NP, R>((R)xi[0], Nodes<R>::sol(k), Nodes<R>::solw(k), l1);
+      lagr<NP, R>((R)xi[1], Nodes<R>::sol(k), Nodes<R>::solw(k), l2);
+      lagr<NP, R>((R)xi[2], Nodes<R>::sol(k), Nodes<R>::solw(k), l3);
+      interp4<NP, R>(U + (size_t)e * 5 * N3, l1, l2, l3, Uv);
+      // drag + gravity
+      R irho = R(1) / Uv[0], rel[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) rel[r] = Uv[1 + r] * irho - v[r];
+      R fD = R(1);
+      if (k.drag_law) {
+        R re = Uv[0] * sqrt(rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2]) * d / mu;
+        if (re >= R(800)) st |= PT_ST_REP800;
+        fD = drag_factor<R>(1, re);
+      }
+      const R coef = fD / tau;
+      double xe[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        R acc = (R)k.mask[r] * coef * rel[r] + (R)k.g[r];
+        kx[r] = As * kx[r] + dt * v[r];
+        kv[r] = As * kv[r] + dt * acc;
+        xe[r] = x[r] + (double)(Bs * kx[r]);
+        v[r] = v[r] + Bs * kv[r];
+      }
+      track<G, R>(m, k, e, x, xe, v, kx, kv, hits, st, c.tc);
+      if (st & PT_ST_FROZEN) live = false;
+    }
+    if (live) ++c.steps;
+  }
+  if (inrange && !(p.status[ip] & PT_ST_FROZEN)) {
+    p.x[ip] = x[0];
+    p.x[n + ip] = x[1];
+    p.x[2 * n + ip] = x[2];
+    vg[ip] = v[0];
+    vg[n + ip] = v[1];
+    vg[2 * n + ip] = v[2];
+    p.elem[ip] = e;
+    p.hits[ip] = hits;
+    p.status[ip] = st;
+  }
+}
+
+// One thread per particle, visiting particles in element-sorted order (perm)
+// so that a warp shares its element's data through L1.  Persistent grid.
+template <int G, int NP, bool F64>
+__global__ void __launch_bounds__(128, F64 ? PT_PUSH_MINB_F64 : PT_PUSH_MINB) k_push(const PushArgs a) {
+  using R = typename RealOf<F64>::type;
+  PT_MLP_PROLOGUE(G, a.k, a.mlp);
   const R* __restrict__ U = reinterpret_cast<const R*>(a.U);
-  R* vg = reinterpret_cast<R*>(a.p.v);
-  const R* dg = reinterpret_cast<const R*>(a.p.d);
-  unsigned long long c_steps = 0, c_it32 = 0, c_it64 = 0;
-  TrackCounters tc = {0, 0, 0};
+  PushCounters c = {0, 0, 0, {0, 0, 0}};
+  const int64_t n = a.p.n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t nround = (n + stride - 1) / stride * stride;  // uniform trip count per warp
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nround; t += stride) {
     const bool inrange = t < n;
     const int64_t ip = inrange ? (a.perm ? (int64_t)a.perm[t] : t) : 0;
-    unsigned st = inrange ? a.p.status[ip] : PT_ST_FROZEN;
-    bool live = !(st & PT_ST_FROZEN);
-    double x[3] = {0, 0, 0};
-    R v[3] = {0, 0, 0}, d = R(1);
-    int e = 0, hits = 0;
-    if (inrange) {
-      x[0] = a.p.x[ip];
-      x[1] = a.p.x[n + ip];
-      x[2] = a.p.x[2 * n + ip];
-      v[0] = vg[ip];
-      v[1] = vg[n + ip];
-      v[2] = vg[2 * n + ip];
-      d = dg[ip];
-      e = a.p.elem[ip];
-      hits = a.p.hits[ip];
-    }
-    if (e < 0 || e >= m.nelem) {
-      if (live) st |= PT_ST_LOST;
-      live = false;
-    }
-    const R tau = (R)k.rho_p * d * d / (R(18) * mu);
-    for (int step = 0; step < a.nsteps; ++step) {
-      R kx[3] = {0, 0, 0}, kv[3] = {0, 0, 0};
-      for (int s = 0; s < 5; ++s) {
-        float guess[3];
-        start_guess<G>(m, k, a.mlp, live ? e : 0, x, live, guess);
-        if (!live) continue;
-        double xi[3];
-        int i32 = 0, i64 = 0;
-        bool ok = locate_one<G, F64>(m, k, e, x, guess, xi, i32, i64);
-        c_it32 += i32;
-        c_it64 += i64;
-        if (!ok) {
-          st |= PT_ST_NEWTON_FAIL;
-          live = false;
-          continue;
-        }
-        const double mx = tmax3(xi[0], xi[1], xi[2]);
-        if (mx > 1.0 + k.lost_tol) {
-          st |= PT_ST_LOST;
-          live = false;
-          continue;
-        }
-        if (mx > 1.0 - k.band_ref) st |= PT_ST_NEAR_FACE;
-        // interpolation of rho, rho u at xi
-        R l1[NP], l2[NP], l3[NP], Uv[4];
-        lagr<NP, R>((R)xi[0], Nodes<R>::sol(k), Nodes<R>::solw(k), l1);
-        lagr<NP, R>((R)xi[1], Nodes<R>::sol(k), Nodes<R>::solw(k), l2);
-        lagr<NP, R>((R)xi[2], Nodes<R>::sol(k), Nodes<R>::solw(k), l3);
-        interp4<NP, R>(U + (size_t)e * 5 * N3, l1, l2, l3, Uv);
-        // drag + gravity
-        R irho = R(1) / Uv[0], rel[3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) rel[r] = Uv[1 + r] * irho - v[r];
-        R fD = R(1);
-        if (k.drag_law) {
-          R re = Uv[0] * sqrt(rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2]) * d / mu;
-          if (re >= R(800)) st |= PT_ST_REP800;
-          fD = drag_factor<R>(1, re);
-        }
-        const R coef = fD / tau;
-        double xe[3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          R acc = (R)k.mask[r] * coef * rel[r] + (R)k.g[r];
-          kx[r] = A[s] * kx[r] + dt * v[r];
-          kv[r] = A[s] * kv[r] + dt * acc;
-          xe[r] = x[r] + (double)(B[s] * kx[r]);
-          v[r] = v[r] + B[s] * kv[r];
-        }
-        track<G, R>(m, k, e, x, xe, v, kx, kv, hits, st, tc);
-        if (st & PT_ST_FROZEN) live = false;
-      }
-      if (live) ++c_steps;
-    }
-    if (inrange && !(a.p.status[ip] & PT_ST_FROZEN)) {
-      a.p.x[ip] = x[0];
-      a.p.x[n + ip] = x[1];
-      a.p.x[2 * n + ip] = x[2];
-      vg[ip] = v[0];
-      vg[n + ip] = v[1];
-      vg[2 * n + ip] = v[2];
-      a.p.elem[ip] = e;
-      a.p.hits[ip] = hits;
-      a.p.status[ip] = st;
-    }
+    push_particle<G, NP, F64>(a.m, a.k, sm, U, a.p, ip, inrange, a.nsteps, a.dt, c);
   }
-  count_add(a.stats, PT_C_STEPS, c_steps);
-  count_add(a.stats, PT_C_IT32, c_it32);
-  count_add(a.stats, PT_C_IT64, c_it64);
-  count_add(a.stats, PT_C_CROSS, (unsigned long long)tc.cross);
-  count_add(a.stats, PT_C_HITS, (unsigned long long)tc.hits);
-  count_add(a.stats, PT_C_SLOW, (unsigned long long)tc.slow);
+  count_add(a.stats, PT_C_STEPS, c.steps);
+  count_add(a.stats, PT_C_IT32, c.it32);
+  count_add(a.stats, PT_C_IT64, c.it64);
+  count_add(a.stats, PT_C_CROSS, (unsigned long long)c.tc.cross);
+  count_add(a.stats, PT_C_HITS, (unsigned long long)c.tc.hits);
+  count_add(a.stats, PT_C_SLOW, (unsigned long long)c.tc.slow);
 }
 
 template <int G, bool F64>
 __global__ void __launch_bounds__(256) k_locate(const LocateArgs a) {
+  PT_MLP_PROLOGUE(G, a.k, a.mlp);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t nround = (a.n + stride - 1) / stride * stride;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nround; i += stride) {
@@ -194,7 +231,7 @@ __global__ void __launch_bounds__(256) k_locate(const LocateArgs a) {
     bool live = inrange && e >= 0 && e < a.m.nelem;
     if (!live) e = 0;
     float guess[3];
-    start_guess<G>(a.m, a.k, a.mlp, e, x, live, guess);
+    start_guess<G>(a.m, a.k, sm, e, x, live, guess);
     if (!inrange) continue;
     double xi[3] = {0, 0, 0};
     int i32 = 0, i64 = 0;

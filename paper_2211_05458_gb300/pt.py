@@ -65,7 +65,8 @@ _lib = None
 EXPORTS = ["pt_config_default", "pt_init_mesh", "pt_set_config", "pt_set_fluid", "pt_push",
            "pt_push_host", "pt_deposit", "pt_locate", "pt_mlp_make_pairs", "pt_mlp_train",
            "pt_mlp_features", "pt_mlp_nparams", "pt_mlp_set", "pt_mlp_get", "pt_mlp_forward",
-           "pt_mlp_grad", "pt_push_batch", "pt_destroy", "pt_last_error"]
+           "pt_mlp_grad", "pt_push_batch", "pt_profile", "pt_profile_read", "pt_destroy",
+           "pt_last_error"]
 
 
 def library_path() -> str:
@@ -106,6 +107,9 @@ def lib():
             L.pt_push_batch.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(CParticles),
                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                         ctypes.POINTER(Stats)]
+            L.pt_profile.argtypes = [_vp, ctypes.c_int32]
+            L.pt_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_int64)]
             L.pt_destroy.argtypes = [_vp]
             L.pt_last_error.argtypes = [_vp]
             L.pt_last_error.restype = ctypes.c_char_p
@@ -326,6 +330,14 @@ class Context:
         self._check(lib().pt_mlp_grad(self.h, inp.shape[0], _ptr(inp), _ptr(tgt), _ptr(g),
                                       ctypes.byref(loss)))
         return float(loss.value), g
+
+    def profile(self, enable: bool = True):
+        self._check(lib().pt_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        ms, k = ctypes.c_double(0.0), ctypes.c_int64(0)
+        self._check(lib().pt_profile_read(self.h, ctypes.byref(ms), ctypes.byref(k)))
+        return float(ms.value), int(k.value)
 
     def close(self):
         if getattr(self, "h", None):
