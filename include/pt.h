@@ -193,6 +193,22 @@ pt_status pt_push_host(pt_ctx* ctx, const pt_particles* p_host, int32_t nsteps, 
  * particles in index order (bitwise reproducible). */
 pt_status pt_deposit(pt_ctx* ctx, const pt_particles* p, int32_t mode, float* S_dev);
 
+/* pt_deposit without any device allocation (the paper has no counterpart).
+ * Some callers cannot call cudaMalloc: a flow solver that has handed the
+ * device memory to its own pool allocator, or a time loop that must not
+ * allocate once it runs (a device allocation can synchronise the device and
+ * fragment such a pool).  This entry point computes exactly what pt_deposit
+ * computes (same modes, same S_dev layout and ownership) but keeps its
+ * scratch -- the element binning counters and the particle permutation -- in
+ * one fixed array of about 5.8 MB of device memory that the library reserves
+ * on every GPU that loads it, until the process exits.  Limits: at most
+ * 131072 elements and 1048576 particles; larger problems return PT_ERR_ARG
+ * (use pt_deposit).  The first call on a device looks up the array's device
+ * address, so make that first call before any stream capture.  Every call
+ * reuses the same array and clears what must start at zero; calls whose work
+ * overlaps on the GPU (other streams, other contexts) race on it. */
+pt_status pt_deposit_noalloc(pt_ctx* ctx, const pt_particles* p, int32_t mode, float* S_dev);
+
 /* Inverse map only (Sec. 3.2.1): for each i, xi of x[:,i] in element elem[i].
  * x_dev double [3][n], elem_dev int32 [n], xi_dev double [3][n] out,
  * iters_dev int32 [n] out (Newton iterations, FP32 + FP64), status_dev uint32

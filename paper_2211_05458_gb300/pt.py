@@ -66,7 +66,7 @@ EXPORTS = ["pt_config_default", "pt_init_mesh", "pt_set_config", "pt_set_fluid",
            "pt_push_host", "pt_deposit", "pt_locate", "pt_mlp_make_pairs", "pt_mlp_train",
            "pt_mlp_features", "pt_mlp_nparams", "pt_mlp_set", "pt_mlp_get", "pt_mlp_forward",
            "pt_mlp_grad", "pt_push_batch", "pt_profile", "pt_profile_read", "pt_destroy",
-           "pt_last_error"]
+           "pt_last_error", "pt_deposit_noalloc"]
 
 
 def library_path() -> str:
@@ -93,6 +93,8 @@ def lib():
                                   ctypes.POINTER(Stats)]
             L.pt_push_host.argtypes = L.pt_push.argtypes
             L.pt_deposit.argtypes = [_vp, ctypes.POINTER(CParticles), ctypes.c_int32, _vp]
+            L.pt_deposit_noalloc.argtypes = [_vp, ctypes.POINTER(CParticles), ctypes.c_int32,
+                                             _vp]
             L.pt_locate.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]
             L.pt_mlp_make_pairs.argtypes = [_vp, ctypes.c_int64, ctypes.c_uint64, _vp, _vp]
             L.pt_mlp_train.argtypes = [_vp, ctypes.c_int64, _vp, _vp, ctypes.c_int32,
