@@ -303,6 +303,24 @@ def main():
         line["mlp"] = mlp_info
 
     if not args.no_extras and rank == 0:
+        # the same FP32 push with the trilinear Newton start (no learned correction)
+        if guess == pt.GUESS_MLP:
+            ctx.set_config(guess=pt.GUESS_TRILINEAR)
+            ptri = pt.ParticleSet.create(wl.x, wl.v, wl.d, wl.elem, pt.FP32, dev)
+            ctx.push(ptri, args.inner, wl.dt, stats=False)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                ctx.push(ptri, args.inner, wl.dt, stats=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            line["fp32_trilinear"] = {"value": P * args.inner * 3 / (e0.elapsed_time(e1) / 1e3),
+                                      "unit": METRIC,
+                                      "note": "same FP32 push, trilinear Newton start"}
+            ctx.set_config(guess=guess)
+            del ptri
         # e2e: same metric through pt_push_host with pinned host buffers
         hp = parts.to("cpu", pin=True)
         e2e_steps = max(1, min(3, args.steps))

@@ -260,7 +260,7 @@ static pt_status upload_mesh(pt_ctx* c, const pt_mesh_desc* md) {
   std::vector<double> xg64((size_t)E * g3 * 3), ce((size_t)E * 3), bil((size_t)E * 72),
       shift((size_t)E * 18);
   std::vector<float> xg32((size_t)E * g3 * 3), xg32lo((size_t)E * g3 * 3), tri((size_t)E * 12), slab((size_t)E * 48, 0.f);
-  std::vector<int> fnbr((size_t)E * 6), finfo((size_t)E * 6);
+  std::vector<int> fnbr((size_t)E * 6), finfo((size_t)E * 6), tmask((size_t)E, 0);
   std::vector<double> M;
   bezier_matrix(g, M);
   const double bx = c->cfg.band_x;
@@ -293,6 +293,25 @@ static pt_status upload_mesh(pt_ctx* c, const pt_mesh_desc* md) {
         for (int d = 0; d < 3; ++d) Jc[3 * r + d] += ((q >> d) & 1 ? 1.0 : -1.0) * cr[q][r] / 8.0;
     if (!inv3h(Jc, Ji))
       return fail(nullptr, PT_ERR_ARG, "element %d: degenerate corner Jacobian", e);
+    // coordinates that equal the trilinear interpolant of the corners at every
+    // node (to 1e-14 of the element radius) use the 8-corner form on the GPU
+    for (int r = 0; r < 3; ++r) {
+      double dev = 0.0;
+      for (int cz = 0; cz < g; ++cz)
+        for (int b = 0; b < g; ++b)
+          for (int a = 0; a < g; ++a) {
+            double xi[3] = {-1.0 + 2.0 * a / (g - 1), -1.0 + 2.0 * b / (g - 1),
+                            -1.0 + 2.0 * cz / (g - 1)};
+            double t = 0.0;
+            for (int q = 0; q < 8; ++q) {
+              double w = 1.0;
+              for (int d = 0; d < 3; ++d) w *= 0.5 * (1.0 + (((q >> d) & 1) ? xi[d] : -xi[d]));
+              t += w * (cr[q][r] - cc[r]);
+            }
+            dev = std::max(dev, std::fabs(xg64[((size_t)e * g3 + a + g * (b + g * cz)) * 3 + r] - t));
+          }
+      if (dev <= 1e-14 * Rmax) tmask[e] |= 1 << r;
+    }
     for (int r = 0; r < 3; ++r) tri[12 * e + r] = 0.f;
     for (int q = 0; q < 9; ++q) tri[12 * e + 3 + q] = (float)Ji[q];
     // faces
@@ -376,6 +395,24 @@ static pt_status upload_mesh(pt_ctx* c, const pt_mesh_desc* md) {
           hi = std::max(hi, pr);
         }
       double margin = bx + 4e-6 * Rmax + 1e-12;
+      // bound on the distance between the face and its bilinear patch: the
+      // Bezier control points of their difference enclose it
+      double devmax = 0.0;
+      if (kind == PT_FACE_CURVED) {
+        for (int km = 0; km < g; ++km)
+          for (int kt = 0; kt < g; ++kt) {
+            double cp[3] = {0, 0, 0};
+            for (int mm = 0; mm < g; ++mm)
+              for (int kk = 0; kk < g; ++kk) {
+                double s = -1.0 + 2.0 * mm / (g - 1), t = -1.0 + 2.0 * kk / (g - 1);
+                for (int r = 0; r < 3; ++r) {
+                  double bl = Bf[r] * s * t + Bf[3 + r] * s + Bf[6 + r] * t + Bf[9 + r];
+                  cp[r] += M[km * g + mm] * M[kt * g + kk] * (P[3 * (mm + g * kk) + r] - bl);
+                }
+              }
+            devmax = std::max(devmax, std::sqrt(cp[0] * cp[0] + cp[1] * cp[1] + cp[2] * cp[2]));
+          }
+      }
       float* S = &slab[48 * (size_t)e + 8 * f];
       S[0] = nf32[0];
       S[1] = nf32[1];
@@ -383,6 +420,7 @@ static pt_status upload_mesh(pt_ctx* c, const pt_mesh_desc* md) {
       S[3] = (float)(lo - margin);
       S[4] = (float)(hi + margin);
       S[5] = (float)Rmax;
+      S[6] = (float)(devmax * (1.0 + 1e-6) + 1e-12 * Rmax);
     }
   }
   c->ncurved = ncurved;
@@ -397,6 +435,8 @@ static pt_status upload_mesh(pt_ctx* c, const pt_mesh_desc* md) {
   c->d_ce = dmalloc<double>(cc, ce.size(), &err);
   if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
   c->d_tri = dmalloc<float>(cc, tri.size(), &err);
+  if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
+  c->d_tmask = dmalloc<int>(cc, tmask.size(), &err);
   if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
   c->d_fnbr = dmalloc<int>(cc, fnbr.size(), &err);
   if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
@@ -417,6 +457,7 @@ static pt_status upload_mesh(pt_ctx* c, const pt_mesh_desc* md) {
   } cp[] = {{c->d_xg64, xg64.data(), xg64.size() * 8}, {c->d_xg32, xg32.data(), xg32.size() * 4},
             {c->d_xg32lo, xg32lo.data(), xg32lo.size() * 4},
             {c->d_ce, ce.data(), ce.size() * 8},       {c->d_tri, tri.data(), tri.size() * 4},
+            {c->d_tmask, tmask.data(), tmask.size() * 4},
             {c->d_fnbr, fnbr.data(), fnbr.size() * 4}, {c->d_finfo, finfo.data(), finfo.size() * 4},
             {c->d_slab, slab.data(), slab.size() * 4}, {c->d_bil, bil.data(), bil.size() * 8},
             {c->d_shift, shift.data(), shift.size() * 8}};
@@ -479,6 +520,7 @@ static DevMesh dev_mesh(const pt_ctx* c) {
   m.xg32lo = c->d_xg32lo;
   m.ce = c->d_ce;
   m.tri = c->d_tri;
+  m.tmask = c->d_tmask;
   m.fnbr = c->d_fnbr;
   m.finfo = c->d_finfo;
   m.slab = c->d_slab;

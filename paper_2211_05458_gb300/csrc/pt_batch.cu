@@ -85,11 +85,11 @@ __global__ void __launch_bounds__(128, PT_PUSH_MINB) k_push_batch(const BatchArg
     const float* U = reinterpret_cast<const float*>(bx.U);
     PushCounters c = {0, 0, 0, {0, 0, 0}};
     switch (bx.np) {
-      case 4: push_particle<G, 4, false>(bx.m, bx.k, nullptr, U, bx.p, ip, true, a.nsteps, a.dt, c); break;
-      case 5: push_particle<G, 5, false>(bx.m, bx.k, nullptr, U, bx.p, ip, true, a.nsteps, a.dt, c); break;
-      case 6: push_particle<G, 6, false>(bx.m, bx.k, nullptr, U, bx.p, ip, true, a.nsteps, a.dt, c); break;
-      case 7: push_particle<G, 7, false>(bx.m, bx.k, nullptr, U, bx.p, ip, true, a.nsteps, a.dt, c); break;
-      default: push_particle<G, 8, false>(bx.m, bx.k, nullptr, U, bx.p, ip, true, a.nsteps, a.dt, c); break;
+      case 4: push_particle_f32<G, 4, false>(bx.m, bx.k, nullptr, nullptr, U, bx.p, ip, true, a.nsteps, a.dt, c); break;
+      case 5: push_particle_f32<G, 5, false>(bx.m, bx.k, nullptr, nullptr, U, bx.p, ip, true, a.nsteps, a.dt, c); break;
+      case 6: push_particle_f32<G, 6, false>(bx.m, bx.k, nullptr, nullptr, U, bx.p, ip, true, a.nsteps, a.dt, c); break;
+      case 7: push_particle_f32<G, 7, false>(bx.m, bx.k, nullptr, nullptr, U, bx.p, ip, true, a.nsteps, a.dt, c); break;
+      default: push_particle_f32<G, 8, false>(bx.m, bx.k, nullptr, nullptr, U, bx.p, ip, true, a.nsteps, a.dt, c); break;
     }
     const int slot = b < kMaxBoxCounters ? b : kMaxBoxCounters - 1;
     if (c.steps) atomicAdd(&sc[slot][0], c.steps);

@@ -24,6 +24,7 @@ struct pt_ctx {
   float* d_xg32lo = nullptr;
   double* d_ce = nullptr;
   float* d_tri = nullptr;
+  int* d_tmask = nullptr;
   int* d_fnbr = nullptr;
   int* d_finfo = nullptr;
   float* d_slab = nullptr;

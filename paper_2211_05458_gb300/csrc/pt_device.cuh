@@ -132,48 +132,71 @@ __device__ __forceinline__ void matvec3(const T* M, const T* v, T* o) {
 
 // FP32, nodes coordinate-major [3][G^3]; chi and Jacobian J[r][q] = d chi_r / d xi_q
 template <int G>
-__device__ __forceinline__ void map_j32(const float* __restrict__ X, const float* xi,
+__device__ __forceinline__ int corner_node(int q) {
+  return ((q & 1) ? G - 1 : 0) + G * (((q & 2) ? G - 1 : 0) + G * ((q & 4) ? G - 1 : 0));
+}
+
+// FP32, nodes coordinate-major [3][G^3]; chi and Jacobian J[r][q] = d chi_r / d xi_q.
+// Coordinates flagged in tm are trilinear in xi: their 8-corner form is used.
+template <int G>
+__device__ __forceinline__ void map_j32(const float* __restrict__ X, const float* xi, int tm,
                                         const DevConsts& k, float* chi, float* J) {
   constexpr int G3 = G * G * G;
   float l0[G], d0[G], l1[G], d1[G], l2[G], d2[G];
-  lagr_d<G, float>(xi[0], k.gn32, k.gw32, l0, d0);
-  lagr_d<G, float>(xi[1], k.gn32, k.gw32, l1, d1);
-  lagr_d<G, float>(xi[2], k.gn32, k.gw32, l2, d2);
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    chi[r] = 0.f;
-    J[3 * r] = J[3 * r + 1] = J[3 * r + 2] = 0.f;
+  if (tm != 7) {
+    lagr_d<G, float>(xi[0], k.gn32, k.gw32, l0, d0);
+    lagr_d<G, float>(xi[1], k.gn32, k.gw32, l1, d1);
+    lagr_d<G, float>(xi[2], k.gn32, k.gw32, l2, d2);
   }
+  const float hp[3] = {0.5f * (1.f + xi[0]), 0.5f * (1.f + xi[1]), 0.5f * (1.f + xi[2])};
+  const float hm[3] = {0.5f * (1.f - xi[0]), 0.5f * (1.f - xi[1]), 0.5f * (1.f - xi[2])};
+  // one coordinate at a time; the loops over c and r stay rolled so that the
+  // hot loop's code stays small
+#pragma unroll 1
+  for (int r = 0; r < 3; ++r) {
+    const float* Xr = X + r * G3;
+    float cr = 0.f, j0 = 0.f, j1 = 0.f, j2 = 0.f;
+    if ((tm >> r) & 1) {
 #pragma unroll
-  for (int c = 0; c < G; ++c) {
-    float T0[3] = {0.f, 0.f, 0.f}, T1[3] = {0.f, 0.f, 0.f}, T2[3] = {0.f, 0.f, 0.f};
+      for (int q = 0; q < 8; ++q) {
+        const float xv = __ldg(Xr + corner_node<G>(q));
+        const float a0 = (q & 1) ? hp[0] : hm[0], a1 = (q & 2) ? hp[1] : hm[1],
+                    a2 = (q & 4) ? hp[2] : hm[2];
+        const float s0 = (q & 1) ? 0.5f : -0.5f, s1 = (q & 2) ? 0.5f : -0.5f,
+                    s2 = (q & 4) ? 0.5f : -0.5f;
+        cr = fmaf(xv, a0 * a1 * a2, cr);
+        j0 = fmaf(xv, s0 * a1 * a2, j0);
+        j1 = fmaf(xv, a0 * s1 * a2, j1);
+        j2 = fmaf(xv, a0 * a1 * s2, j2);
+      }
+    } else {
+#pragma unroll 1
+      for (int c = 0; c < G; ++c) {
+        float T0 = 0.f, T1 = 0.f, T2 = 0.f;
 #pragma unroll
-    for (int b = 0; b < G; ++b) {
-      float s[3] = {0.f, 0.f, 0.f}, s1[3] = {0.f, 0.f, 0.f};
+        for (int b = 0; b < G; ++b) {
+          float sv = 0.f, s1 = 0.f;
 #pragma unroll
-      for (int a = 0; a < G; ++a) {
-        const int q = a + G * (b + G * c);
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          float xv = __ldg(X + r * G3 + q);
-          s[r] = fmaf(xv, l0[a], s[r]);
-          s1[r] = fmaf(xv, d0[a], s1[r]);
+          for (int a = 0; a < G; ++a) {
+            const float xv = __ldg(Xr + a + G * (b + G * c));
+            sv = fmaf(xv, l0[a], sv);
+            s1 = fmaf(xv, d0[a], s1);
+          }
+          T0 = fmaf(sv, l1[b], T0);
+          T1 = fmaf(s1, l1[b], T1);
+          T2 = fmaf(sv, d1[b], T2);
         }
-      }
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        T0[r] = fmaf(s[r], l1[b], T0[r]);
-        T1[r] = fmaf(s1[r], l1[b], T1[r]);
-        T2[r] = fmaf(s[r], d1[b], T2[r]);
+        const float lc = l2[c], dc = d2[c];
+        cr = fmaf(T0, lc, cr);
+        j0 = fmaf(T1, lc, j0);
+        j1 = fmaf(T2, lc, j1);
+        j2 = fmaf(T0, dc, j2);
       }
     }
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      chi[r] = fmaf(T0[r], l2[c], chi[r]);
-      J[3 * r] = fmaf(T1[r], l2[c], J[3 * r]);
-      J[3 * r + 1] = fmaf(T2[r], l2[c], J[3 * r + 1]);
-      J[3 * r + 2] = fmaf(T0[r], d2[c], J[3 * r + 2]);
-    }
+    chi[r] = cr;
+    J[3 * r] = j0;
+    J[3 * r + 1] = j1;
+    J[3 * r + 2] = j2;
   }
 }
 
@@ -286,38 +309,66 @@ __device__ __forceinline__ void lagr_df(df x, const DevConsts& k, df* l) {
 }
 
 // Residual chi(xi) - x of the element map in double-float, sum-factorised;
-// nodes as hi [3][G^3] + lo [3][G^3] (relative to the element centre).
+// nodes as hi [3][G^3] + lo [3][G^3] (relative to the element centre);
+// coordinates flagged in tm use the 8-corner trilinear form.
 template <int G>
 __device__ __forceinline__ void resid_df(const float* __restrict__ Xh,
-                                         const float* __restrict__ Xl, const df* xi,
+                                         const float* __restrict__ Xl, const df* xi, int tm,
                                          const df* xloc, const DevConsts& k, float* r) {
   constexpr int G3 = G * G * G;
   df l0[G], l1[G], l2[G];
-  lagr_df<G>(xi[0], k, l0);
-  lagr_df<G>(xi[1], k, l1);
-  lagr_df<G>(xi[2], k, l2);
+  if (tm != 7) {
+    lagr_df<G>(xi[0], k, l0);
+    lagr_df<G>(xi[1], k, l1);
+    lagr_df<G>(xi[2], k, l2);
+  }
+  df w8[8];
+  if (tm != 0) {
+    df hp[3], hm[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const df up = df_add(df_from(1.f), xi[d]);
+      const df dn = df_sub(df_from(1.f), xi[d]);
+      hp[d] = df{0.5f * up.hi, 0.5f * up.lo};
+      hm[d] = df{0.5f * dn.hi, 0.5f * dn.lo};
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const df w01 = df_mul((q & 1) ? hp[0] : hm[0], (q & 2) ? hp[1] : hm[1]);
+      w8[q] = df_mul(w01, hm[2]);
+      w8[q + 4] = df_mul(w01, hp[2]);
+    }
+  }
 #pragma unroll 1
   for (int q = 0; q < 3; ++q) {
     const float* Ph = Xh + q * G3;
     const float* Pl = Xl + q * G3;
     df_acc a3;
     dacc_init(a3);
+    if ((tm >> q) & 1) {
 #pragma unroll
-    for (int c = 0; c < G; ++c) {
-      df_acc a2;
-      dacc_init(a2);
-#pragma unroll
-      for (int b = 0; b < G; ++b) {
-        df_acc a1;
-        dacc_init(a1);
-#pragma unroll
-        for (int a = 0; a < G; ++a) {
-          const int i = a + G * (b + G * c);
-          dacc_fma(a1, df{__ldg(Ph + i), __ldg(Pl + i)}, l0[a]);
-        }
-        dacc_fma(a2, dacc_result(a1), l1[b]);
+      for (int c = 0; c < 8; ++c) {
+        const int i = corner_node<G>(c);
+        dacc_fma(a3, df{__ldg(Ph + i), __ldg(Pl + i)}, w8[c]);
       }
-      dacc_fma(a3, dacc_result(a2), l2[c]);
+    } else {
+#pragma unroll 1
+      for (int c = 0; c < G; ++c) {
+        df_acc a2;
+        dacc_init(a2);
+#pragma unroll
+        for (int b = 0; b < G; ++b) {
+          df_acc a1;
+          dacc_init(a1);
+#pragma unroll
+          for (int a = 0; a < G; ++a) {
+            const int i = a + G * (b + G * c);
+            dacc_fma(a1, df{__ldg(Ph + i), __ldg(Pl + i)}, l0[a]);
+          }
+          dacc_fma(a2, dacc_result(a1), l1[b]);
+        }
+        dacc_fma(a3, dacc_result(a2), l2[c]);
+      }
     }
     const df rr = df_sub(dacc_result(a3), xloc[q]);
     r[q] = __fadd_rn(rr.hi, rr.lo);
@@ -330,29 +381,29 @@ __device__ __noinline__ bool newton64_cold(const double* X64, const double* xl, 
   return newton64<G>(X64, xl, xi, k, k.max_newton, it64);
 }
 
-// Mixed-precision Newton: FP32 iterations (chi and J in FP32) until the step
-// is below 1e-5, then double-float residuals with the last FP32 inverse
-// Jacobian until the step is below newton_tol; a full FP64 Newton is the
-// fallback.
+// Mixed-precision Newton on a double-float local position xd (relative to the
+// element centre): FP32 iterations (chi and J in FP32) until the step is below
+// 1e-5, then double-float residuals with the last FP32 inverse Jacobian until
+// the step is below newton_tol.  Returns the double-float xi in zd; a full
+// FP64 Newton is the (out-of-line) fallback.
 template <int G>
-__device__ __forceinline__ bool newton_mixed(const DevMesh& m, const DevConsts& k, int e,
-                                             const double* xl, const float* guess, double* xi,
-                                             int& it32, int& it64) {
+__device__ __forceinline__ bool newton_df(const DevMesh& m, const DevConsts& k, int e,
+                                          const df* xd, const float* guess, df* zd, int& it32,
+                                          int& it64) {
   constexpr int G3 = G * G * G;
   const float* X32 = m.xg32 + (size_t)e * 3 * G3;
   const float* X32l = m.xg32lo + (size_t)e * 3 * G3;
-  const double* X64 = m.xg64 + (size_t)e * 3 * G3;
-  float xf[3] = {(float)xl[0], (float)xl[1], (float)xl[2]};
+  const int tm = __ldg(m.tmask + e);
   float z[3] = {guess[0], guess[1], guess[2]};
   float Ji[9];
   bool have = false;
   for (int it = 0; it < 8; ++it) {
     float chi[3], J[9], r[3], d[3];
-    map_j32<G>(X32, z, k, chi, J);
+    map_j32<G>(X32, z, tm, k, chi, J);
     if (!inv3(J, Ji)) break;
     have = true;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) r[q] = chi[q] - xf[q];
+    for (int q = 0; q < 3; ++q) r[q] = chi[q] - xd[q].hi;
     matvec3(Ji, r, d);
 #pragma unroll
     for (int q = 0; q < 3; ++q) z[q] -= d[q];
@@ -364,35 +415,45 @@ __device__ __forceinline__ bool newton_mixed(const DevMesh& m, const DevConsts& 
     if (tmax3(d[0], d[1], d[2]) < 1e-5f) break;
   }
   if (have) {
-    df xd[3], zd[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      xd[q] = df{xf[q], (float)(xl[q] - (double)xf[q])};
-      zd[q] = df_from(z[q]);
-    }
+    for (int q = 0; q < 3; ++q) zd[q] = df_from(z[q]);
     const float tol = (float)k.newton_tol;
     for (int it = 0; it < 6; ++it) {
       float r[3], d[3];
-      resid_df<G>(X32, X32l, zd, xd, k, r);
+      resid_df<G>(X32, X32l, zd, tm, xd, k, r);
       matvec3(Ji, r, d);
 #pragma unroll
       for (int q = 0; q < 3; ++q) zd[q] = df_sub(zd[q], df_from(d[q]));
       ++it64;
-      if (tmax3(d[0], d[1], d[2]) < tol) {
-#pragma unroll
-        for (int q = 0; q < 3; ++q) xi[q] = df_to_double(zd[q]);
-        return true;
-      }
+      if (tmax3(d[0], d[1], d[2]) < tol) return true;
     }
+  }
+  // fallback: full FP64 Newton
+  double xl[3], xi[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) xi[q] = df_to_double(zd[q]);
-  } else {
-    xi[0] = guess[0];
-    xi[1] = guess[1];
-    xi[2] = guess[2];
+  for (int q = 0; q < 3; ++q) {
+    xl[q] = df_to_double(xd[q]);
+    xi[q] = have ? df_to_double(zd[q]) : (double)guess[q];
   }
   if (!(tmax3(xi[0], xi[1], xi[2]) <= 4.0)) xi[0] = xi[1] = xi[2] = 0.0;
-  return newton64_cold<G>(X64, xl, xi, k, it64);
+  const bool ok = newton64_cold<G>(m.xg64 + (size_t)e * 3 * G3, xl, xi, k, it64);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) zd[q] = df_from_double(xi[q]);
+  return ok;
+}
+
+// As newton_df for a local position in FP64 (xl) and a FP64 result.
+template <int G>
+__device__ __forceinline__ bool newton_mixed(const DevMesh& m, const DevConsts& k, int e,
+                                             const double* xl, const float* guess, double* xi,
+                                             int& it32, int& it64) {
+  df xd[3], zd[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) xd[q] = df_from_double(xl[q]);
+  const bool ok = newton_df<G>(m, k, e, xd, guess, zd, it32, it64);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) xi[q] = df_to_double(zd[q]);
+  return ok;
 }
 
 // ---------------------------------------------------------------------------
@@ -407,7 +468,7 @@ __device__ __forceinline__ void interp4(const T* __restrict__ Ue, const T* l1, c
   for (int v = 0; v < 4; ++v) {
     const T* Uv = Ue + v * N3;
     T acc = T(0);
-#pragma unroll
+#pragma unroll 1
     for (int kk = 0; kk < NP; ++kk) {
       T t2 = T(0);
 #pragma unroll
@@ -583,21 +644,16 @@ struct TrackCounters {
   int cross, hits, slow;
 };
 
-// Conservative FP32 test: can the segment x -> xe (extended by the band) touch
-// any face of element e?  Slab of face f: lo <= n.(P - ce) <= hi for every
-// point of the face, margins included.
-__device__ __forceinline__ bool touches_any_slab(const DevMesh& m, int e, const double* x,
-                                                 const double* xe) {
-  const double* ce = m.ce + 3 * (size_t)e;
-  float a[3], b[3];
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    double c = __ldg(ce + r);
-    a[r] = (float)(x[r] - c);
-    b[r] = (float)(xe[r] - c);
-  }
+// Conservative FP32 test: can the segment a -> b (element-local coordinates,
+// extended by the band) touch any face of element e?  Slab of face f:
+// lo <= n.(P - ce) <= hi for every point of the face, margins (band plus
+// 4e-6 of the element radius, which covers the FP32 rounding of a and b while
+// they stay within 8 radii) included; longer segments take the exact path.
+__device__ __forceinline__ bool touches_any_slab(const DevMesh& m, int e, const float* a,
+                                                 const float* b) {
   const float4* S = reinterpret_cast<const float4*>(m.slab + 48 * (size_t)e);
-  bool hit = false;
+  const float rlim = 8.f * __ldg(m.slab + 48 * (size_t)e + 5);
+  bool hit = !(fmaxf(fmaxf(fabsf(b[0]), fabsf(b[1])), fabsf(b[2])) <= rlim);
 #pragma unroll
   for (int f = 0; f < 6; ++f) {
     float4 s0 = __ldg(S + 2 * f), s1 = __ldg(S + 2 * f + 1);
@@ -620,11 +676,12 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
                                         double* xe, R* v, R* kx, R* kv, int& hits, unsigned& st,
                                         TrackCounters& tc);
 
+// a, b: segment ends relative to the element centre in FP32 (for the test only)
 template <int G, typename R>
 __device__ __forceinline__ void track(const DevMesh& m, const DevConsts& k, int& e, double* x,
-                                      double* xe, R* v, R* kx, R* kv, int& hits, unsigned& st,
-                                      TrackCounters& tc) {
-  if (!touches_any_slab(m, e, x, xe)) {
+                                      double* xe, const float* a, const float* b, R* v, R* kx,
+                                      R* kv, int& hits, unsigned& st, TrackCounters& tc) {
+  if (!touches_any_slab(m, e, a, b)) {
 #pragma unroll
     for (int r = 0; r < 3; ++r) x[r] = xe[r];
     return;
@@ -647,6 +704,8 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
   }
 #pragma unroll
   for (int r = 0; r < 3; ++r) td[r] /= L;
+  float tdf[3] = {(float)td[0], (float)td[1], (float)td[2]};
+  float Lf = (float)L;
   double n1[3], n2[3];
   {
     double ax[3] = {0, 0, 0};
@@ -667,16 +726,17 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
     const double* ce = m.ce + 3 * (size_t)e;
     double xl[3] = {xs[0] - __ldg(ce), xs[1] - __ldg(ce + 1), xs[2] - __ldg(ce + 2)};
     const double* X64 = m.xg64 + (size_t)e * 3 * G * G * G;
+    const float xlf[3] = {(float)xl[0], (float)xl[1], (float)xl[2]};
     double best = 1e300, bs = 0.0, bt = 0.0;
     int bf = -1;
     for (int f = 0; f < 6; ++f) {
       if (f == fin) continue;
-      // slab prefilter (double)
+      // slab prefilter (FP32, conservative: the margins cover its rounding)
       const float* sl = m.slab + 48 * (size_t)e + 8 * f;
-      double nrm[3] = {__ldg(sl), __ldg(sl + 1), __ldg(sl + 2)};
-      double pa = dot3d(nrm, xl);
-      double pb = pa + L * dot3d(nrm, td);
-      if (fmax(pa, pb) < (double)__ldg(sl + 3) || fmin(pa, pb) > (double)__ldg(sl + 4)) continue;
+      const float cosf_ = __ldg(sl) * tdf[0] + __ldg(sl + 1) * tdf[1] + __ldg(sl + 2) * tdf[2];
+      const float pa = __ldg(sl) * xlf[0] + __ldg(sl + 1) * xlf[1] + __ldg(sl + 2) * xlf[2];
+      const float pb = pa + Lf * cosf_;
+      if (fmaxf(pa, pb) < __ldg(sl + 3) || fminf(pa, pb) > __ldg(sl + 4)) continue;
       const int info = __ldg(m.finfo + 6 * (size_t)e + f);
       const int kind = (info >> 2) & 3;
       const double* Bf = m.bil + 72 * (size_t)e + 12 * f;
@@ -686,10 +746,15 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
       double rs[2], rt[2], ra[2];
       int nr = bilinear_roots(Bl, xl, td, n1, n2, rs, rt, ra);
       if (kind == PT_FACE_CURVED) {
+        // the curved face lies within dev of its bilinear patch: a bilinear
+        // crossing far beyond the segment cannot refine into one inside it
+        const double dev = (double)__ldg(sl + 6);
+        const double reach = 4.0 * dev / fmax((double)fabsf(cosf_), 0.05) + 2.0 * k.band_x;
         int kk = 0;
         for (int i = 0; i < nr; ++i) {
           double s = rs[i], t = rt[i], al = ra[i];
           if (!(fabs(s) < 2.0 && fabs(t) < 2.0)) continue;
+          if (al > L + reach || al < a0 - reach) continue;
           if (curved_refine<G>(X64, f, xl, td, k, s, t, al, L)) {
             bool dup = false;
             for (int j = 0; j < kk; ++j)

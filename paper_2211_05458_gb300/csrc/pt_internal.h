@@ -36,6 +36,7 @@ struct DevMesh {
   const float* xg32lo;    // [E][3][g^3]   (nodes - ce) - xg32: low parts of a double-float copy
   const double* ce;       // [E][3]
   const float* tri;       // [E][12]       trilinear centre (3) and inverse Jacobian (9)
+  const int* tmask;       // [E]           bit q: coordinate q is trilinear in xi (8-corner form)
   const int* fnbr;        // [E][6]        neighbour element
   const int* finfo;       // [E][6]        bc | kind << 2 | nbr_face << 4
   const float* slab;      // [E][6][8]     unit normal (3), lo, hi, -, -, - (local coords)
@@ -68,18 +69,17 @@ struct DevParticles {
   unsigned* status;
 };
 
-// BF16 network for the learned guess: layers 2 and 3 as bf16 [out][in],
-// first-layer xi columns and the output layer in FP32, plus normalisation.
+// BF16 network for the learned guess: layers 2 and 3 as bf16 [out][in] in
+// global memory (staged to shared memory per block); the small FP32 parts
+// travel by value in the kernel parameters (constant bank).
 struct DevMLP {
   const uint16_t* w2;     // [64][64] bf16
   const uint16_t* w3;     // [64][64] bf16
-  const float* w1x;       // [64][3]  first-layer columns of the xi_tri inputs / in_std
-  const float* b2;        // [64]
-  const float* b3;        // [64]
-  const float* w4;        // [3][64]
-  const float* b4;        // [3]
-  float xmean[3];         // input mean of the xi_tri features
-  float oscale[3];        // output scale
+  float w1x[64 * 3];      // first-layer columns of the xi_tri inputs / in_std
+  float b2[64];
+  float b3[64];
+  float w4[3 * 64];       // output layer scaled by the output scale
+  float b4[4];
 };
 
 struct PushArgs {

@@ -6,10 +6,10 @@
 #include "pt_mlp_infer.cuh"
 
 // minimum resident blocks of 128 threads per SM for the push kernel (sets the
-// register budget: 4 -> 128 registers per thread, 2 -> 255); the FP64 mode
+// register budget: 3 -> 168 registers per thread, 2 -> 255); the FP64 mode
 // keeps the larger budget
 #ifndef PT_PUSH_MINB
-#define PT_PUSH_MINB 4
+#define PT_PUSH_MINB 3
 #endif
 #define PT_PUSH_MINB_F64 2
 
@@ -49,31 +49,52 @@ __device__ __forceinline__ bool locate_one(const DevMesh& m, const DevConsts& k,
   return newton_mixed<G>(m, k, e, xl, guess, xi, it32, it64);
 }
 
+// As locate_one, with x already relative to the element centre.
+template <int G, bool F64>
+__device__ __forceinline__ bool locate_local(const DevMesh& m, const DevConsts& k, int e,
+                                             const double* xl, const float* guess, double* xi,
+                                             int& it32, int& it64) {
+  if (F64) {
+    xi[0] = guess[0];
+    xi[1] = guess[1];
+    xi[2] = guess[2];
+    return newton64<G>(m.xg64 + (size_t)e * 3 * G * G * G, xl, xi, k, k.max_newton, it64);
+  }
+  return newton_mixed<G>(m, k, e, xl, guess, xi, it32, it64);
+}
+
 // Start guess: trilinear, optionally corrected by the learned network (warp-
 // collective: every lane of the warp must call it).
-template <int G>
+template <int G, bool MLP>
 __device__ __forceinline__ void start_guess(const DevMesh& m, const DevConsts& k, MlpSmem* sm,
-                                            int e, const double* x, bool live, float* guess) {
+                                            const DevMLP* mlpp, int e, const double* x, bool live,
+                                            float* guess) {
   const double* ce = m.ce + 3 * (size_t)e;
   float xf[3] = {(float)(x[0] - __ldg(ce)), (float)(x[1] - __ldg(ce + 1)),
                  (float)(x[2] - __ldg(ce + 2))};
   trilinear_guess(m, e, xf, guess);
-  if constexpr (G == 4) {
-    if (k.guess == PT_GUESS_MLP) mlp_correct_smem(*sm, m, e, live, guess);
-  }
+  if constexpr (MLP) mlp_correct_smem(*sm, *mlpp, m, e, live, guess);
+}
+
+// As start_guess, with x already relative to the element centre (FP32).
+template <int G, bool MLP>
+__device__ __forceinline__ void start_guess_local(const DevMesh& m, const DevConsts& k,
+                                                  MlpSmem* sm, const DevMLP* mlpp, int e,
+                                                  const float* xf, bool live,
+                                                  float* guess) {
+  trilinear_guess(m, e, xf, guess);
+  if constexpr (MLP) mlp_correct_smem(*sm, *mlpp, m, e, live, guess);
 }
 
 // The block's copy of the network weights (NGeo = 3 kernels only); must be
 // reached by every thread of the block.
-#define PT_MLP_PROLOGUE(G, K, MLP)                    \
+#define PT_MLP_PROLOGUE(USE, P)                       \
   MlpSmem* sm = nullptr;                              \
-  if constexpr (G == 4) {                             \
+  if constexpr (USE) {                                \
     __shared__ MlpSmem s_mlp;                         \
     sm = &s_mlp;                                      \
-    if ((K).guess == PT_GUESS_MLP) {                  \
-      mlp_load(s_mlp, MLP);                           \
-      __syncthreads();                                \
-    }                                                 \
+    mlp_load(s_mlp, P);                               \
+    __syncthreads();                                  \
   }
 
 struct PushCounters {
@@ -87,8 +108,9 @@ struct PushCounters {
 // the whole call (the fluid state is constant during it).  Every lane of a
 // warp must call it (the learned start is warp-collective); lanes without a
 // particle pass inrange = false.
-template <int G, int NP, bool F64>
+template <int G, int NP, bool F64, bool MLP>
 __device__ __forceinline__ void push_particle(const DevMesh& m, const DevConsts& k, MlpSmem* sm,
+                                              const DevMLP* mlpp,
                                               const typename RealOf<F64>::type* __restrict__ U,
                                               const DevParticles& p, int64_t ip, bool inrange,
                                               int nsteps, double dtd, PushCounters& c) {
@@ -125,12 +147,16 @@ __device__ __forceinline__ void push_particle(const DevMesh& m, const DevConsts&
     for (int s = 0; s < 5; ++s) {
       const R As = F64 ? (R)k.A[s] : (R)k.A32[s];
       const R Bs = F64 ? (R)k.B[s] : (R)k.B32[s];
+      const int eg = live ? e : 0;
+      const double* ce = m.ce + 3 * (size_t)eg;
+      const double xl[3] = {x[0] - __ldg(ce), x[1] - __ldg(ce + 1), x[2] - __ldg(ce + 2)};
+      const float xf[3] = {(float)xl[0], (float)xl[1], (float)xl[2]};
       float guess[3];
-      start_guess<G>(m, k, sm, live ? e : 0, x, live, guess);
+      start_guess_local<G, MLP>(m, k, sm, mlpp, eg, xf, live, guess);
       if (!live) continue;
       double xi[3];
       int i32 = 0, i64 = 0;
-      bool ok = locate_one<G, F64>(m, k, e, x, guess, xi, i32, i64);
+      bool ok = locate_local<G, F64>(m, k, e, xl, guess, xi, i32, i64);
       c.it32 += i32;
       c.it64 += i64;
       if (!ok) {
@@ -163,15 +189,18 @@ __device__ __forceinline__ void push_particle(const DevMesh& m, const DevConsts&
       }
       const R coef = fD / tau;
       double xe[3];
+      float bf[3];
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         R acc = (R)k.mask[r] * coef * rel[r] + (R)k.g[r];
         kx[r] = As * kx[r] + dt * v[r];
         kv[r] = As * kv[r] + dt * acc;
-        xe[r] = x[r] + (double)(Bs * kx[r]);
+        const R dx = Bs * kx[r];
+        xe[r] = x[r] + (double)dx;
+        bf[r] = F64 ? (float)(xl[r] + (double)dx) : xf[r] + (float)dx;
         v[r] = v[r] + Bs * kv[r];
       }
-      track<G, R>(m, k, e, x, xe, v, kx, kv, hits, st, c.tc);
+      track<G, R>(m, k, e, x, xe, xf, bf, v, kx, kv, hits, st, c.tc);
       if (st & PT_ST_FROZEN) live = false;
     }
     if (live) ++c.steps;
@@ -189,12 +218,166 @@ __device__ __forceinline__ void push_particle(const DevMesh& m, const DevConsts&
   }
 }
 
+// FP32 mode: as push_particle, with the position held during the call as a
+// double-float offset from the owning element's centre, so that a stage issues
+// no FP64 instruction except in the exact face-intersection path (the FP64
+// position is formed again at the end and around that path).
+template <int G, int NP, bool MLP>
+__device__ __forceinline__ void push_particle_f32(const DevMesh& m, const DevConsts& k,
+                                                  MlpSmem* sm, const DevMLP* mlpp,
+                                                  const float* __restrict__ U,
+                                                  const DevParticles& p, int64_t ip, bool inrange,
+                                                  int nsteps, double dtd, PushCounters& c) {
+  constexpr int N3 = NP * NP * NP;
+  const int64_t n = p.n;
+  const float dt = (float)dtd;
+  const float mu = (float)k.mu;
+  float* vg = reinterpret_cast<float*>(p.v);
+  const float* dg = reinterpret_cast<const float*>(p.d);
+  unsigned st = inrange ? p.status[ip] : PT_ST_FROZEN;
+  bool live = !(st & PT_ST_FROZEN);
+  double x[3] = {0, 0, 0};
+  float v[3] = {0, 0, 0}, d = 1.f;
+  int e = 0, hits = 0;
+  if (inrange) {
+    x[0] = p.x[ip];
+    x[1] = p.x[n + ip];
+    x[2] = p.x[2 * n + ip];
+    v[0] = vg[ip];
+    v[1] = vg[n + ip];
+    v[2] = vg[2 * n + ip];
+    d = dg[ip];
+    e = p.elem[ip];
+    hits = p.hits[ip];
+  }
+  if (e < 0 || e >= m.nelem) {
+    if (live) st |= PT_ST_LOST;
+    live = false;
+  }
+  // local double-float position
+  df xd[3];
+  {
+    const double* ce = m.ce + 3 * (size_t)(live ? e : 0);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) xd[r] = df_from_double(x[r] - __ldg(ce + r));
+  }
+  bool moved = false;
+  const float tau = (float)k.rho_p * d * d / (18.f * mu);
+  for (int step = 0; step < nsteps; ++step) {
+    float kx[3] = {0, 0, 0}, kv[3] = {0, 0, 0};
+    for (int s = 0; s < 5; ++s) {
+      const float As = k.A32[s];
+      const float Bs = k.B32[s];
+      const int eg = live ? e : 0;
+      const float xf[3] = {xd[0].hi, xd[1].hi, xd[2].hi};
+      float guess[3];
+      start_guess_local<G, MLP>(m, k, sm, mlpp, eg, xf, live, guess);
+      if (!live) continue;
+      df zd[3];
+      int i32 = 0, i64 = 0;
+      bool ok = newton_df<G>(m, k, e, xd, guess, zd, i32, i64);
+      c.it32 += i32;
+      c.it64 += i64;
+      if (!ok) {
+        st |= PT_ST_NEWTON_FAIL;
+        live = false;
+        continue;
+      }
+      const float xi[3] = {zd[0].hi + zd[0].lo, zd[1].hi + zd[1].lo, zd[2].hi + zd[2].lo};
+      const float mx = tmax3(xi[0], xi[1], xi[2]);
+      if (mx > 1.f - 1e-5f) {  // decide the bands exactly (rare)
+        double md = fmax(fmax(fabs(df_to_double(zd[0])), fabs(df_to_double(zd[1]))),
+                         fabs(df_to_double(zd[2])));
+        if (md > 1.0 + k.lost_tol) {
+          st |= PT_ST_LOST;
+          live = false;
+          continue;
+        }
+        if (md > 1.0 - k.band_ref) st |= PT_ST_NEAR_FACE;
+      }
+      // interpolation of rho, rho u at xi
+      float l1[NP], l2[NP], l3[NP], Uv[4];
+      lagr<NP, float>(xi[0], k.sn32, k.sw32, l1);
+      lagr<NP, float>(xi[1], k.sn32, k.sw32, l2);
+      lagr<NP, float>(xi[2], k.sn32, k.sw32, l3);
+      interp4<NP, float>(U + (size_t)e * 5 * N3, l1, l2, l3, Uv);
+      // drag + gravity
+      float irho = 1.f / Uv[0], rel[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) rel[r] = Uv[1 + r] * irho - v[r];
+      float fD = 1.f;
+      if (k.drag_law) {
+        float re = Uv[0] * sqrtf(rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2]) * d / mu;
+        if (re >= 800.f) st |= PT_ST_REP800;
+        fD = drag_factor<float>(1, re);
+      }
+      const float coef = fD / tau;
+      df xe[3];
+      float bf[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        float acc = (float)k.mask[r] * coef * rel[r] + (float)k.g[r];
+        kx[r] = As * kx[r] + dt * v[r];
+        kv[r] = As * kv[r] + dt * acc;
+        xe[r] = df_add(xd[r], df_from(Bs * kx[r]));
+        bf[r] = xe[r].hi;
+        v[r] = v[r] + Bs * kv[r];
+      }
+      if (!touches_any_slab(m, e, xf, bf)) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) xd[r] = xe[r];
+      } else {
+        // exact tracking in FP64 on global positions, then back to local
+        const double* ce = m.ce + 3 * (size_t)e;
+        double xs[3], xg[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const double cr = __ldg(ce + r);
+          xs[r] = cr + df_to_double(xd[r]);
+          xg[r] = cr + df_to_double(xe[r]);
+        }
+        track_slow<G, float>(m, k, e, xs, xg, v, kx, kv, hits, st, c.tc);
+        if (st & PT_ST_FROZEN) {
+          live = false;
+#pragma unroll
+          for (int r = 0; r < 3; ++r) x[r] = xs[r];
+          moved = true;
+          continue;
+        }
+        const double* cn = m.ce + 3 * (size_t)e;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) xd[r] = df_from_double(xs[r] - __ldg(cn + r));
+      }
+    }
+    if (live) ++c.steps;
+  }
+  if (inrange && !(p.status[ip] & PT_ST_FROZEN)) {
+    if (live || !moved) {
+      const double* ce = m.ce + 3 * (size_t)(e >= 0 && e < m.nelem ? e : 0);
+      if (e >= 0 && e < m.nelem) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) x[r] = __ldg(ce + r) + df_to_double(xd[r]);
+      }
+    }
+    p.x[ip] = x[0];
+    p.x[n + ip] = x[1];
+    p.x[2 * n + ip] = x[2];
+    vg[ip] = v[0];
+    vg[n + ip] = v[1];
+    vg[2 * n + ip] = v[2];
+    p.elem[ip] = e;
+    p.hits[ip] = hits;
+    p.status[ip] = st;
+  }
+}
+
 // One thread per particle, visiting particles in element-sorted order (perm)
 // so that a warp shares its element's data through L1.  Persistent grid.
-template <int G, int NP, bool F64>
-__global__ void __launch_bounds__(128, F64 ? PT_PUSH_MINB_F64 : PT_PUSH_MINB) k_push(const PushArgs a) {
+template <int G, int NP, bool F64, bool MLP>
+__global__ void __launch_bounds__(128, F64 ? PT_PUSH_MINB_F64 : PT_PUSH_MINB)
+    k_push(const __grid_constant__ PushArgs a) {
   using R = typename RealOf<F64>::type;
-  PT_MLP_PROLOGUE(G, a.k, a.mlp);
+  PT_MLP_PROLOGUE(MLP, a.mlp);
   const R* __restrict__ U = reinterpret_cast<const R*>(a.U);
   PushCounters c = {0, 0, 0, {0, 0, 0}};
   const int64_t n = a.p.n;
@@ -203,7 +386,12 @@ __global__ void __launch_bounds__(128, F64 ? PT_PUSH_MINB_F64 : PT_PUSH_MINB) k_
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nround; t += stride) {
     const bool inrange = t < n;
     const int64_t ip = inrange ? (a.perm ? (int64_t)a.perm[t] : t) : 0;
-    push_particle<G, NP, F64>(a.m, a.k, sm, U, a.p, ip, inrange, a.nsteps, a.dt, c);
+    if constexpr (F64)
+      push_particle<G, NP, true, false>(a.m, a.k, sm, &a.mlp, U, a.p, ip, inrange, a.nsteps, a.dt,
+                                        c);
+    else
+      push_particle_f32<G, NP, MLP>(a.m, a.k, sm, &a.mlp, (const float*)U, a.p, ip, inrange, a.nsteps,
+                               a.dt, c);
   }
   count_add(a.stats, PT_C_STEPS, c.steps);
   count_add(a.stats, PT_C_IT32, c.it32);
@@ -213,9 +401,9 @@ __global__ void __launch_bounds__(128, F64 ? PT_PUSH_MINB_F64 : PT_PUSH_MINB) k_
   count_add(a.stats, PT_C_SLOW, (unsigned long long)c.tc.slow);
 }
 
-template <int G, bool F64>
-__global__ void __launch_bounds__(256) k_locate(const LocateArgs a) {
-  PT_MLP_PROLOGUE(G, a.k, a.mlp);
+template <int G, bool F64, bool MLP>
+__global__ void __launch_bounds__(256) k_locate(const __grid_constant__ LocateArgs a) {
+  PT_MLP_PROLOGUE(MLP, a.mlp);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t nround = (a.n + stride - 1) / stride * stride;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nround; i += stride) {
@@ -231,7 +419,7 @@ __global__ void __launch_bounds__(256) k_locate(const LocateArgs a) {
     bool live = inrange && e >= 0 && e < a.m.nelem;
     if (!live) e = 0;
     float guess[3];
-    start_guess<G>(a.m, a.k, sm, e, x, live, guess);
+    start_guess<G, MLP>(a.m, a.k, sm, &a.mlp, e, x, live, guess);
     if (!inrange) continue;
     double xi[3] = {0, 0, 0};
     int i32 = 0, i64 = 0;
@@ -345,16 +533,18 @@ __global__ void __launch_bounds__(256) k_deposit_segmented(const DepositArgs a) 
     float acc[NO];
 #pragma unroll
     for (int r = 0; r < NO; ++r) acc[r] = 0.f;
-    for (int c0 = beg; c0 < end; c0 += SEG_TILE) {
-      const int cnt = min(SEG_TILE, end - c0);
+    const int total = end - beg;
+    for (int base = 0; base < total; base += SEG_TILE) {
+      const int cnt = min(SEG_TILE, total - base);
       __syncthreads();
-      // rank-sort this chunk's particle indices (the segment order from the
-      // atomic scatter is arbitrary; index order makes the sum reproducible)
-      if (threadIdx.x < cnt) {
-        const int my = a.perm[c0 + threadIdx.x];
+      // the segment's particles in index order, SEG_TILE at a time (the order
+      // left by the atomic scatter is arbitrary; index order makes the sum
+      // reproducible): the particle of rank r goes to idx[r - base]
+      for (int j = threadIdx.x; j < total; j += blockDim.x) {
+        const int my = a.perm[beg + j];
         int rank = 0;
-        for (int j = 0; j < cnt; ++j) rank += a.perm[c0 + j] < my;
-        idx[rank] = my;
+        for (int q = 0; q < total; ++q) rank += a.perm[beg + q] < my;
+        if (rank >= base && rank < base + SEG_TILE) idx[rank - base] = my;
       }
       __syncthreads();
       if (threadIdx.x < cnt) {
@@ -397,9 +587,14 @@ __global__ void __launch_bounds__(256) k_deposit_segmented(const DepositArgs a) 
 // launch helpers for one (G, mode) family
 template <int G, bool F64>
 struct Family {
+  // the learned start exists only for NGeo = 3 in FP32 mode
+  static constexpr bool kMlp = (G == 4) && !F64;
   template <int NP>
   static int push(const PushArgs& a, int grid, int block, cudaStream_t s) {
-    k_push<G, NP, F64><<<grid, block, 0, s>>>(a);
+    if (kMlp && a.k.guess == PT_GUESS_MLP)
+      k_push<G, NP, F64, kMlp><<<grid, block, 0, s>>>(a);
+    else
+      k_push<G, NP, F64, false><<<grid, block, 0, s>>>(a);
     return (int)cudaGetLastError();
   }
   template <int NP>
@@ -413,7 +608,7 @@ struct Family {
   template <int NP>
   static int occ(int block) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<G, NP, F64>, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<G, NP, F64, false>, block, 0);
     return nb;
   }
   static int push_np(int np, const PushArgs& a, int grid, int block, cudaStream_t s) {
@@ -453,7 +648,10 @@ struct Family {
     return 0;
   }
   static int locate(const LocateArgs& a, int grid, int block, cudaStream_t s) {
-    k_locate<G, F64><<<grid, block, 0, s>>>(a);
+    if (kMlp && a.k.guess == PT_GUESS_MLP)
+      k_locate<G, F64, kMlp><<<grid, block, 0, s>>>(a);
+    else
+      k_locate<G, F64, false><<<grid, block, 0, s>>>(a);
     return (int)cudaGetLastError();
   }
 };

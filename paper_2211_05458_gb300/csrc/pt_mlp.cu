@@ -50,6 +50,7 @@ struct pt_mlp_state {
   float* w4s = nullptr;     // [3][64] scaled by out_scale
   float* b4s = nullptr;     // [3]
   double* dacc = nullptr;   // reductions scratch [64]
+  float h_w1x[192], h_b2[64], h_b3[64], h_w4s[192], h_b4s[4];  // host copies for kernel params
   float hnorm[NNORM];
   bool have_theta = false;
 };
@@ -383,14 +384,14 @@ __global__ void k_mlp_pre(const float* th, const float* norm, const float* feat4
 DevMLP pt_dev_mlp(const pt_ctx* c) {
   DevMLP m;
   std::memset(&m, 0, sizeof m);
-  if (!c->mlp) return m;
+  if (!c->mlp || !c->mlp_ready) return m;
   m.w2 = c->mlp->w2b;
   m.w3 = c->mlp->w3b;
-  m.w1x = c->mlp->w1x;
-  m.b2 = c->mlp->b2;
-  m.b3 = c->mlp->b3;
-  m.w4 = c->mlp->w4s;
-  m.b4 = c->mlp->b4s;
+  std::memcpy(m.w1x, c->mlp->h_w1x, sizeof m.w1x);
+  std::memcpy(m.b2, c->mlp->h_b2, sizeof m.b2);
+  std::memcpy(m.b3, c->mlp->h_b3, sizeof m.b3);
+  std::memcpy(m.w4, c->mlp->h_w4s, sizeof m.w4);
+  std::memcpy(m.b4, c->mlp->h_b4s, sizeof m.b4);
   return m;
 }
 
@@ -467,6 +468,11 @@ static pt_status export_bf16(pt_ctx* c) {
   MCK(cudaMemcpy(s->b3, th.data() + OFF_B3, 64 * 4, cudaMemcpyHostToDevice));
   MCK(cudaMemcpy(s->w4s, w4s.data(), 192 * 4, cudaMemcpyHostToDevice));
   MCK(cudaMemcpy(s->b4s, b4s.data(), 4 * 4, cudaMemcpyHostToDevice));
+  std::memcpy(s->h_w1x, w1x.data(), sizeof s->h_w1x);
+  std::memcpy(s->h_b2, th.data() + OFF_B2, sizeof s->h_b2);
+  std::memcpy(s->h_b3, th.data() + OFF_B3, sizeof s->h_b3);
+  std::memcpy(s->h_w4s, w4s.data(), sizeof s->h_w4s);
+  std::memcpy(s->h_b4s, b4s.data(), sizeof s->h_b4s);
   const int64_t tot = (int64_t)c->nelem * 64;
   k_mlp_pre<<<(int)((tot + 255) / 256), 256, 0, c->stream>>>(s->theta, s->norm, s->feat48,
                                                               c->nelem, c->d_mlp_pre);

@@ -18,12 +18,17 @@ constexpr int MLP_LD = 72;  // padded row length (bf16) of activations and weigh
 struct MlpSmem {
   __nv_bfloat16 w2[64 * MLP_LD];
   __nv_bfloat16 w3[64 * MLP_LD];
-  float b2[64], b3[64], w4[3 * 64], b4[4], w1x[64 * 3];
   __nv_bfloat16 act[4][32 * MLP_LD];  // one [32][72] tile per warp (blocks <= 128 threads)
 };
 
+// GELU for inference in its tanh form, 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)))
+// (Hendrycks & Gimpel 2016), with the hardware tanh approximation: within about
+// 1e-3 of the erf form the network was trained with, below the BF16 rounding of
+// weights and activations.
 __device__ __forceinline__ float gelu_f(float z) {
-  return 0.5f * z * (1.f + erff(z * 0.70710678118654752f));
+  float u = 0.7978845608028654f * fmaf(0.044715f * z, z * z, z), t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
+  return 0.5f * z * (1.f + t);
 }
 
 // Fills the block's weight copy (call by every thread, followed by __syncthreads).
@@ -33,15 +38,6 @@ __device__ __forceinline__ void mlp_load(MlpSmem& s, const DevMLP& p) {
     s.w2[o * MLP_LD + c] = __ushort_as_bfloat16(p.w2[i]);
     s.w3[o * MLP_LD + c] = __ushort_as_bfloat16(p.w3[i]);
   }
-  for (int i = threadIdx.x; i < 64; i += blockDim.x) {
-    s.b2[i] = p.b2[i];
-    s.b3[i] = p.b3[i];
-  }
-  for (int i = threadIdx.x; i < 3 * 64; i += blockDim.x) {
-    s.w4[i] = p.w4[i];
-    s.w1x[i] = p.w1x[i];
-  }
-  if (threadIdx.x < 3) s.b4[threadIdx.x] = p.b4[threadIdx.x];
 }
 
 __device__ __forceinline__ void mma_bf16_16816(float* c, const uint32_t* a, const uint32_t* b) {
@@ -52,39 +48,58 @@ __device__ __forceinline__ void mma_bf16_16816(float* c, const uint32_t* a, cons
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// act <- GELU(act W^T + b) for the warp's [32][64] tile (in place)
+// act <- GELU(act W^T + b) for the warp's [32][64] tile (in place).  The 64
+// output columns are produced in two halves so that only 32 accumulators are
+// live; all results stay in registers until both halves are done.
 __device__ __forceinline__ void mlp_layer(__nv_bfloat16* act, const __nv_bfloat16* W,
                                           const float* bias) {
   const int lane = threadIdx.x & 31;
   const int r = lane >> 2, cq = (lane & 3) * 2;
-  float acc[2][8][4];
+  uint32_t outp[2][8][2];  // packed bf16 results: [m-tile][n-tile][row, row+8]
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
+  for (int half = 0; half < 2; ++half) {
+    float acc[2][4][4];
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
+    for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.f;
+      for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
-  for (int ks = 0; ks < 4; ++ks) {
-    const int k0 = ks * 16;
-    uint32_t a[2][4];
+        for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.f;
 #pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      const __nv_bfloat16* A = act + (mt * 16 + r) * MLP_LD + k0 + cq;
-      a[mt][0] = *reinterpret_cast<const uint32_t*>(A);
-      a[mt][1] = *reinterpret_cast<const uint32_t*>(A + 8 * MLP_LD);
-      a[mt][2] = *reinterpret_cast<const uint32_t*>(A + 8);
-      a[mt][3] = *reinterpret_cast<const uint32_t*>(A + 8 * MLP_LD + 8);
+    for (int ks = 0; ks < 4; ++ks) {
+      const int k0 = ks * 16;
+      uint32_t a[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const __nv_bfloat16* A = act + (mt * 16 + r) * MLP_LD + k0 + cq;
+        a[mt][0] = *reinterpret_cast<const uint32_t*>(A);
+        a[mt][1] = *reinterpret_cast<const uint32_t*>(A + 8 * MLP_LD);
+        a[mt][2] = *reinterpret_cast<const uint32_t*>(A + 8);
+        a[mt][3] = *reinterpret_cast<const uint32_t*>(A + 8 * MLP_LD + 8);
+      }
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const __nv_bfloat16* B = W + ((half * 4 + nt) * 8 + r) * MLP_LD + k0 + cq;
+        uint32_t b[2];
+        b[0] = *reinterpret_cast<const uint32_t*>(B);
+        b[1] = *reinterpret_cast<const uint32_t*>(B + 8);
+        mma_bf16_16816(acc[0][nt], a[0], b);
+        mma_bf16_16816(acc[1][nt], a[1], b);
+      }
     }
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      const __nv_bfloat16* B = W + (nt * 8 + r) * MLP_LD + k0 + cq;
-      uint32_t b[2];
-      b[0] = *reinterpret_cast<const uint32_t*>(B);
-      b[1] = *reinterpret_cast<const uint32_t*>(B + 8);
-      mma_bf16_16816(acc[0][nt], a[0], b);
-      mma_bf16_16816(acc[1][nt], a[1], b);
-    }
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int col = (half * 4 + nt) * 8 + cq;
+        const float b0 = bias[col], b1 = bias[col + 1];
+        __nv_bfloat162 lo = __floats2bfloat162_rn(gelu_f(acc[mt][nt][0] + b0),
+                                                  gelu_f(acc[mt][nt][1] + b1));
+        __nv_bfloat162 hi = __floats2bfloat162_rn(gelu_f(acc[mt][nt][2] + b0),
+                                                  gelu_f(acc[mt][nt][3] + b1));
+        outp[mt][half * 4 + nt][0] = *reinterpret_cast<uint32_t*>(&lo);
+        outp[mt][half * 4 + nt][1] = *reinterpret_cast<uint32_t*>(&hi);
+      }
   }
   __syncwarp();
 #pragma unroll
@@ -92,13 +107,8 @@ __device__ __forceinline__ void mlp_layer(__nv_bfloat16* act, const __nv_bfloat1
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
       const int col = nt * 8 + cq;
-      const float b0 = bias[col], b1 = bias[col + 1];
-      __nv_bfloat162 lo = __floats2bfloat162_rn(gelu_f(acc[mt][nt][0] + b0),
-                                                gelu_f(acc[mt][nt][1] + b1));
-      __nv_bfloat162 hi = __floats2bfloat162_rn(gelu_f(acc[mt][nt][2] + b0),
-                                                gelu_f(acc[mt][nt][3] + b1));
-      *reinterpret_cast<__nv_bfloat162*>(act + (mt * 16 + r) * MLP_LD + col) = lo;
-      *reinterpret_cast<__nv_bfloat162*>(act + (mt * 16 + r + 8) * MLP_LD + col) = hi;
+      *reinterpret_cast<uint32_t*>(act + (mt * 16 + r) * MLP_LD + col) = outp[mt][nt][0];
+      *reinterpret_cast<uint32_t*>(act + (mt * 16 + r + 8) * MLP_LD + col) = outp[mt][nt][1];
     }
   __syncwarp();
 }
@@ -106,8 +116,8 @@ __device__ __forceinline__ void mlp_layer(__nv_bfloat16* act, const __nv_bfloat1
 // Corrects guess[3] (the trilinear start) of this lane's particle.  Warp-
 // collective: all 32 lanes call it together; a lane with live == false uses
 // its own inputs and keeps its guess.
-__device__ __forceinline__ void mlp_correct_smem(MlpSmem& s, const DevMesh& m, int e, bool live,
-                                                 float* guess) {
+__device__ __forceinline__ void mlp_correct_smem(MlpSmem& s, const DevMLP& p, const DevMesh& m,
+                                                 int e, bool live, float* guess) {
   __syncwarp();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   __nv_bfloat16* act = s.act[w];
@@ -115,23 +125,23 @@ __device__ __forceinline__ void mlp_correct_smem(MlpSmem& s, const DevMesh& m, i
   // layer 1: element part + xi_tri columns, GELU, into this lane's row
 #pragma unroll 8
   for (int o = 0; o < 64; o += 2) {
-    float z0 = __ldg(pre + o) + s.w1x[3 * o] * guess[0] + s.w1x[3 * o + 1] * guess[1] +
-               s.w1x[3 * o + 2] * guess[2];
-    float z1 = __ldg(pre + o + 1) + s.w1x[3 * o + 3] * guess[0] + s.w1x[3 * o + 4] * guess[1] +
-               s.w1x[3 * o + 5] * guess[2];
+    float z0 = __ldg(pre + o) + p.w1x[3 * o] * guess[0] + p.w1x[3 * o + 1] * guess[1] +
+               p.w1x[3 * o + 2] * guess[2];
+    float z1 = __ldg(pre + o + 1) + p.w1x[3 * o + 3] * guess[0] + p.w1x[3 * o + 4] * guess[1] +
+               p.w1x[3 * o + 5] * guess[2];
     *reinterpret_cast<__nv_bfloat162*>(act + lane * MLP_LD + o) =
         __floats2bfloat162_rn(gelu_f(z0), gelu_f(z1));
   }
   __syncwarp();
-  mlp_layer(act, s.w2, s.b2);
-  mlp_layer(act, s.w3, s.b3);
+  mlp_layer(act, s.w2, p.b2);
+  mlp_layer(act, s.w3, p.b3);
   // output layer (FP32) on this lane's row
-  float y[3] = {s.b4[0], s.b4[1], s.b4[2]};
+  float y[3] = {p.b4[0], p.b4[1], p.b4[2]};
 #pragma unroll 8
   for (int i = 0; i < 64; i += 2) {
     float2 h = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(act + lane * MLP_LD + i));
 #pragma unroll
-    for (int q = 0; q < 3; ++q) y[q] += s.w4[64 * q + i] * h.x + s.w4[64 * q + i + 1] * h.y;
+    for (int q = 0; q < 3; ++q) y[q] += p.w4[64 * q + i] * h.x + p.w4[64 * q + i + 1] * h.y;
   }
   __syncwarp();
   if (live) {
