@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--dims", type=int, default=64)
     ap.add_argument("--guess", default="auto", choices=["auto", "trilinear", "mlp"])
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / fp64 / cpu legs")
+    ap.add_argument("--extras", default="trilinear,e2e,fp64,cpu",
+                    help="comma list of extra legs to run (trilinear, e2e, fp64, cpu)")
     return ap.parse_args()
 
 
@@ -123,6 +125,31 @@ def make_workload(args, device, seed, precision):
     from paper_2211_05458_gb300 import workloads as W
     return W.curved_channel((args.dims,) * 3, 3, 5, P=args.particles, nsteps=args.inner,
                             seed=seed, device=device, precision=precision)
+
+
+# DRAM bytes per particle-step of k_push, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum of the push kernel on the 32^3, 10^6-particle case, per
+# particle-step; see profiles/); traffic scales with the particles processed.
+TRAFFIC_BYTES_PER_PARTICLE_STEP = 180.0
+
+
+def algorithmic_flops_per_particle_stage(G=4, NP=6, ntri=2):
+    """FP32 flops (FMA = 2) of one particle-stage of the FP32-mode push as the
+    method prescribes it: trilinear start, 2 FP32 Newton iterations (chi and J),
+    2 double-float residual iterations, interpolation of 4 conserved variables,
+    drag + RK + slab test.  ntri of the 3 coordinates are trilinear in xi."""
+    full = 3 - ntri
+    basis_d = 3 * (G + 10 * G)                       # Lagrange values + derivatives
+    newton32 = basis_d + full * (4 * G ** 3 + 6 * G ** 2 + 8 * G) + ntri * 104 + 12 + 60 + 24
+    basis_df = 3 * (11 * G + 7 * (3 * G - 1))
+    resid_df = basis_df + 150 + full * (12 * G ** 3 + 18 * G ** 2 + 18 * G) + ntri * 96 + 84
+    interp = 3 * 4 * NP + 4 * 2 * (NP ** 3 + NP ** 2 + NP)
+    misc = 21 + 180
+    return 2 * newton32 + 2 * resid_df + interp + misc
+
+
+def fp32_peak_tflops(clk_max_mhz=2070.0, sms=152, lanes=128):
+    return sms * lanes * 2 * clk_max_mhz * 1e6 / 1e12
 
 
 def measured_peaks():
@@ -268,20 +295,23 @@ def main():
     value = throughput(P, args.inner, args.steps, world, ms)
     stats = ctx.push(parts, 1, wl.dt, stats=True)  # one more step with counters
 
-    # roofline of the dominant kernel (k_push): algorithmic bytes per launch
-    N3 = (wl.N + 1) ** 3
-    g3 = 4 ** 3
-    elem_bytes = 4 * N3 * 4 + g3 * 3 * (8 + 4) + 8 * 3 + 12 * 4 + 6 * (4 + 4 + 32 + 96 + 24)
-    rec_bytes = (24 + 12 + 4 + 4 + 4 + 4) + (24 + 12 + 4 + 4 + 4) + 4  # read, write, perm
-    occupied = min(wl.mesh.nelem, P)
-    bytes_per_launch = P * rec_bytes + occupied * elem_bytes
+    # roofline of the dominant kernel (k_push): it is bound by FP32 arithmetic and
+    # issue latency, not by memory (DRAM traffic is a few percent of peak)
+    flops_stage = algorithmic_flops_per_particle_stage(G=4, NP=wl.N + 1, ntri=2)
     avg_launch_s = (kern_ms / 1e3) / max(launches, 1)
-    achieved = bytes_per_launch / avg_launch_s / 1e9
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None,
-                "kernel": "k_push<4,6,fp32>", "peak_kind": peak_kind,
-                "kernel_share_of_step": (kern_ms / ms) if ms > 0 else None}
+    flops_launch = flops_stage * 5 * args.inner * P
+    achieved = flops_launch / avg_launch_s / 1e12
+    fp32_peak = fp32_peak_tflops(clk_max_mhz=2070.0)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak,
+                "traffic": TRAFFIC_BYTES_PER_PARTICLE_STEP * P * args.inner,
+                "kernel": "k_push<4,6,fp32,%s>" % ("learned" if guess else "trilinear"),
+                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "flops_per_particle_stage": flops_stage,
+                "launch_ms": avg_launch_s * 1e3,
+                "kernel_share_of_step": (kern_ms / ms) if ms > 0 else None,
+                "hbm_frac_of_measured": (TRAFFIC_BYTES_PER_PARTICLE_STEP * P * args.inner
+                                         / avg_launch_s / 1e9) / float(peaks.get("hbm_gbs", 6800.0))}
 
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -304,7 +334,8 @@ def main():
 
     if not args.no_extras and rank == 0:
         # the same FP32 push with the trilinear Newton start (no learned correction)
-        if guess == pt.GUESS_MLP:
+        legs = set(args.extras.split(","))
+        if guess == pt.GUESS_MLP and "trilinear" in legs:
             ctx.set_config(guess=pt.GUESS_TRILINEAR)
             ptri = pt.ParticleSet.create(wl.x, wl.v, wl.d, wl.elem, pt.FP32, dev)
             ctx.push(ptri, args.inner, wl.dt, stats=False)
@@ -321,6 +352,7 @@ def main():
                                       "note": "same FP32 push, trilinear Newton start"}
             ctx.set_config(guess=guess)
             del ptri
+    if not args.no_extras and rank == 0 and "e2e" in legs:
         # e2e: same metric through pt_push_host with pinned host buffers
         hp = parts.to("cpu", pin=True)
         e2e_steps = max(1, min(3, args.steps))
@@ -334,6 +366,7 @@ def main():
         line["e2e"] = {"value": P * args.inner * e2e_steps / e2e_s, "unit": METRIC,
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
         del hp
+    if not args.no_extras and rank == 0 and "fp64" in legs:
         # plain FP64 Newton (FP64 mode) on the same workload, fewer steps
         ctx64 = pt.Context(wl.mesh, stream=stream, precision=pt.FP64, mu=wl.mu, rho_p=wl.rho_p,
                            drag_law=wl.drag_law, rebin_every=2)
@@ -352,6 +385,7 @@ def main():
                               "note": "FP64 mode: FP64 Newton from the trilinear guess, FP64 "
                                       "interpolation, drag and RK"}
         del p64, U64, ctx64
+    if not args.no_extras and rank == 0 and "cpu" in legs:
         # oracle on the host cores, bounded sample
         try:
             wl.U = wl.U.cpu()

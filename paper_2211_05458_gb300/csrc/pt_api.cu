@@ -446,6 +446,10 @@ static pt_status upload_mesh(pt_ctx* c, const pt_mesh_desc* md) {
   if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
   c->d_bil = dmalloc<double>(cc, bil.size(), &err);
   if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
+  std::vector<float> bil32(bil.size());
+  for (size_t i = 0; i < bil.size(); ++i) bil32[i] = (float)bil[i];
+  c->d_bil32 = dmalloc<float>(cc, bil32.size(), &err);
+  if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
   c->d_shift = dmalloc<double>(cc, shift.size(), &err);
   if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
   c->d_stats = dmalloc<unsigned long long>(cc, PT_C_COUNT, &err);
@@ -460,6 +464,7 @@ static pt_status upload_mesh(pt_ctx* c, const pt_mesh_desc* md) {
             {c->d_tmask, tmask.data(), tmask.size() * 4},
             {c->d_fnbr, fnbr.data(), fnbr.size() * 4}, {c->d_finfo, finfo.data(), finfo.size() * 4},
             {c->d_slab, slab.data(), slab.size() * 4}, {c->d_bil, bil.data(), bil.size() * 8},
+            {c->d_bil32, bil32.data(), bil32.size() * 4},
             {c->d_shift, shift.data(), shift.size() * 8}};
   for (auto& q : cp) {
     err = cudaMemcpy(q.d, q.h, q.b, cudaMemcpyHostToDevice);
@@ -525,6 +530,7 @@ static DevMesh dev_mesh(const pt_ctx* c) {
   m.finfo = c->d_finfo;
   m.slab = c->d_slab;
   m.bil = c->d_bil;
+  m.bil32 = c->d_bil32;
   m.shift = c->d_shift;
   m.mlp_pre = c->d_mlp_pre;
   return m;

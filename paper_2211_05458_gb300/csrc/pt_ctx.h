@@ -29,6 +29,7 @@ struct pt_ctx {
   int* d_finfo = nullptr;
   float* d_slab = nullptr;
   double* d_bil = nullptr;
+  float* d_bil32 = nullptr;
   double* d_shift = nullptr;
   unsigned long long* d_stats = nullptr;
   std::vector<void*> allocs;

@@ -13,6 +13,17 @@
 #include "pt_df.cuh"
 #include "pt_internal.h"
 
+// 1: evaluate the per-dimension Lagrange bases of the Newton residuals in a
+// rolled loop (one copy of the code, values through local memory), which
+// shrinks the hot loop's instruction footprint
+#ifndef PT_ROLL_BASIS
+#define PT_ROLL_BASIS 0
+#endif
+// 1: screen each touched face in FP32 before its exact FP64 solve
+#ifndef PT_FACE_SCREEN
+#define PT_FACE_SCREEN 1
+#endif
+
 namespace pt {
 
 template <typename T>
@@ -142,12 +153,16 @@ template <int G>
 __device__ __forceinline__ void map_j32(const float* __restrict__ X, const float* xi, int tm,
                                         const DevConsts& k, float* chi, float* J) {
   constexpr int G3 = G * G * G;
-  float l0[G], d0[G], l1[G], d1[G], l2[G], d2[G];
+  float lb[3][G], db[3][G];
   if (tm != 7) {
-    lagr_d<G, float>(xi[0], k.gn32, k.gw32, l0, d0);
-    lagr_d<G, float>(xi[1], k.gn32, k.gw32, l1, d1);
-    lagr_d<G, float>(xi[2], k.gn32, k.gw32, l2, d2);
+#if PT_ROLL_BASIS
+#pragma unroll 1
+#else
+#pragma unroll
+#endif
+    for (int d = 0; d < 3; ++d) lagr_d<G, float>(xi[d], k.gn32, k.gw32, lb[d], db[d]);
   }
+  const float *l0 = lb[0], *d0 = db[0], *l1 = lb[1], *d1 = db[1], *l2 = lb[2], *d2 = db[2];
   const float hp[3] = {0.5f * (1.f + xi[0]), 0.5f * (1.f + xi[1]), 0.5f * (1.f + xi[2])};
   const float hm[3] = {0.5f * (1.f - xi[0]), 0.5f * (1.f - xi[1]), 0.5f * (1.f - xi[2])};
   // one coordinate at a time; the loops over c and r stay rolled so that the
@@ -316,12 +331,18 @@ __device__ __forceinline__ void resid_df(const float* __restrict__ Xh,
                                          const float* __restrict__ Xl, const df* xi, int tm,
                                          const df* xloc, const DevConsts& k, float* r) {
   constexpr int G3 = G * G * G;
-  df l0[G], l1[G], l2[G];
+  df lb[3][G];
   if (tm != 7) {
-    lagr_df<G>(xi[0], k, l0);
-    lagr_df<G>(xi[1], k, l1);
-    lagr_df<G>(xi[2], k, l2);
+#if PT_ROLL_BASIS
+#pragma unroll 1
+#else
+#pragma unroll
+#endif
+    for (int d = 0; d < 3; ++d) lagr_df<G>(xi[d], k, lb[d]);
   }
+  const df* l0 = lb[0];
+  const df* l1 = lb[1];
+  const df* l2 = lb[2];
   df w8[8];
   if (tm != 0) {
     df hp[3], hm[3];
@@ -605,6 +626,118 @@ __device__ __forceinline__ int bilinear_roots(const double* B, const double* xs,
   return nr;
 }
 
+// FP32 version of bilinear_roots used to screen faces before the exact FP64
+// solve; sets ill when a root is ill-conditioned in FP32 (near-tangent ray,
+// vanishing denominator), in which case the caller must not trust it.
+__device__ __forceinline__ int bilinear_roots_f32(const float* B, const float* xs, const float* td,
+                                                  const float* n1, const float* n2, float* rs,
+                                                  float* rt, float* ra, bool& ill) {
+  const float* a = B;
+  const float* b = B + 3;
+  const float* c = B + 6;
+  const float dd[3] = {B[9] - xs[0], B[10] - xs[1], B[11] - xs[2]};
+  auto dot = [](const float* u, const float* w) { return u[0] * w[0] + u[1] * w[1] + u[2] * w[2]; };
+  const float A1 = dot(n1, a), B1 = dot(n1, b), C1 = dot(n1, c), D1 = dot(n1, dd);
+  const float A2 = dot(n2, a), B2 = dot(n2, b), C2 = dot(n2, c), D2 = dot(n2, dd);
+  const float scl = fabsf(A1) + fabsf(B1) + fabsf(C1) + fabsf(D1) + fabsf(A2) + fabsf(B2) +
+                    fabsf(C2) + fabsf(D2);
+  if (!(scl > 0.f)) {
+    ill = true;
+    return 0;
+  }
+  const float q2 = B1 * A2 - B2 * A1;
+  const float q1 = B1 * C2 + D1 * A2 - B2 * C1 - D2 * A1;
+  const float q0 = D1 * C2 - D2 * C1;
+  float r[2];
+  int k = 0;
+  if (fabsf(q2) <= 1e-4f * scl * scl) {
+    if (fabsf(q1) <= 1e-3f * scl * scl) {
+      ill = true;
+      return 0;
+    }
+    r[k++] = -q0 / q1;
+  } else {
+    const float disc = q1 * q1 - 4.f * q2 * q0;
+    if (fabsf(disc) <= 1e-3f * q1 * q1 + 1e-6f * scl * scl * scl * scl) ill = true;
+    if (disc >= 0.f) {
+      const float sq = sqrtf(disc);
+      const float qq = -0.5f * (q1 + (q1 >= 0.f ? sq : -sq));
+      if (qq != 0.f) {
+        r[k++] = qq / q2;
+        r[k++] = q0 / qq;
+      } else {
+        ill = true;
+      }
+    }
+  }
+  int nr = 0;
+  for (int i = 0; i < k; ++i) {
+    const float u = r[i];
+    const float den1 = A1 * u + C1, den2 = A2 * u + C2;
+    const bool use1 = fabsf(den1) >= fabsf(den2);
+    const float den = use1 ? den1 : den2;
+    if (fabsf(den) <= 1e-3f * scl) {
+      ill = true;
+      continue;
+    }
+    const float w = -((use1 ? B1 : B2) * u + (use1 ? D1 : D2)) / den;
+    float pp[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) pp[q] = a[q] * u * w + b[q] * u + c[q] * w + dd[q];
+    rs[nr] = u;
+    rt[nr] = w;
+    ra[nr] = dot(td, pp);
+    nr++;
+  }
+  return nr;
+}
+
+// FP32 Newton on F(s,t,alpha) = p(s,t) - xs - alpha td for a curved face, from
+// the element's FP32 nodes (coordinate-major); false if it does not settle.
+template <int G>
+__device__ __forceinline__ bool curved_newton_f32(const float* __restrict__ X32, int f,
+                                                  const float* xs, const float* td,
+                                                  const DevConsts& k, float& s, float& t,
+                                                  float& al) {
+  constexpr int G3 = G * G * G;
+  for (int it = 0; it < 12; ++it) {
+    float ls[G], ds[G], lt[G], dt[G];
+    lagr_d<G, float>(s, k.gn32, k.gw32, ls, ds);
+    lagr_d<G, float>(t, k.gn32, k.gw32, lt, dt);
+    float p[3] = {0, 0, 0}, ps[3] = {0, 0, 0}, pt[3] = {0, 0, 0};
+#pragma unroll
+    for (int kk = 0; kk < G; ++kk)
+#pragma unroll
+      for (int mm = 0; mm < G; ++mm) {
+        const int q = face_node<G>(f, mm, kk);
+        const float w = ls[mm] * lt[kk], wsv = ds[mm] * lt[kk], wtv = ls[mm] * dt[kk];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const float xv = __ldg(X32 + r * G3 + q);
+          p[r] = fmaf(xv, w, p[r]);
+          ps[r] = fmaf(xv, wsv, ps[r]);
+          pt[r] = fmaf(xv, wtv, pt[r]);
+        }
+      }
+    float F[3], J[9], Ji[9], dl[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      F[r] = p[r] - xs[r] - al * td[r];
+      J[3 * r] = ps[r];
+      J[3 * r + 1] = pt[r];
+      J[3 * r + 2] = -td[r];
+    }
+    if (!inv3(J, Ji)) return false;
+    matvec3(Ji, F, dl);
+    s -= dl[0];
+    t -= dl[1];
+    al -= dl[2];
+    if (fabsf(dl[0]) < 1e-5f && fabsf(dl[1]) < 1e-5f) return true;
+    if (!(fabsf(s) < 3.f && fabsf(t) < 3.f)) return false;
+  }
+  return false;
+}
+
 // Newton on F(s,t,alpha) = p(s,t) - xs - alpha td for a curved face, started
 // from a bilinear root; returns true on convergence.
 template <int G>
@@ -706,6 +839,7 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
   for (int r = 0; r < 3; ++r) td[r] /= L;
   float tdf[3] = {(float)td[0], (float)td[1], (float)td[2]};
   float Lf = (float)L;
+  float n1f[3], n2f[3];
   double n1[3], n2[3];
   {
     double ax[3] = {0, 0, 0};
@@ -718,6 +852,11 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
 #pragma unroll
     for (int r = 0; r < 3; ++r) n1[r] /= nn;
     cross3d(td, n1, n2);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      n1f[r] = (float)n1[r];
+      n2f[r] = (float)n2[r];
+    }
   }
   double a0 = 0.0;
   int fin = -1;
@@ -739,6 +878,32 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
       if (fmaxf(pa, pb) < __ldg(sl + 3) || fminf(pa, pb) > __ldg(sl + 4)) continue;
       const int info = __ldg(m.finfo + 6 * (size_t)e + f);
       const int kind = (info >> 2) & 3;
+      // FP32 screen: skip the exact solve when every FP32 root is clearly
+      // outside the segment or the face (margins ~100x the FP32 error)
+      float fs[2], ft[2], fa[2];
+      bool ill = fabsf(cosf_) < 1e-2f;
+      if (PT_FACE_SCREEN) {
+        const float* Bf32 = m.bil32 + 72 * (size_t)e + 12 * f;
+        float B32[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) B32[q] = __ldg(Bf32 + q);
+        const int n32 = bilinear_roots_f32(B32, xlf, tdf, n1f, n2f, fs, ft, fa, ill);
+        const float ta = 1e-4f * (__ldg(sl + 5) + Lf) / fmaxf(fabsf(cosf_), 1e-2f) +
+                         4.f * (float)k.band_x;
+        const float a0f = (float)a0;
+        bool any = ill;
+        for (int i = 0; i < n32 && !ill; ++i) {
+          if (kind == PT_FACE_CURVED &&
+              !curved_newton_f32<G>(m.xg32 + (size_t)e * 3 * G * G * G, f, xlf, tdf, k, fs[i],
+                                    ft[i], fa[i])) {
+            any = true;
+            break;
+          }
+          const float mm = fmaxf(fabsf(fs[i]), fabsf(ft[i]));
+          if (!(fa[i] < a0f - ta || fa[i] > Lf + ta || mm > 1.f + 1e-3f)) any = true;
+        }
+        if (!any) continue;
+      }
       const double* Bf = m.bil + 72 * (size_t)e + 12 * f;
       double Bl[12];
 #pragma unroll

@@ -41,6 +41,7 @@ struct DevMesh {
   const int* finfo;       // [E][6]        bc | kind << 2 | nbr_face << 4
   const float* slab;      // [E][6][8]     unit normal (3), lo, hi, -, -, - (local coords)
   const double* bil;      // [E][6][12]    p(s,t) = a st + b s + c t + d (local coords)
+  const float* bil32;     // [E][6][12]    FP32 copy of bil (screening)
   const double* shift;    // [E][6][3]
   const float* mlp_pre;   // [E][64]       element part of the first MLP layer, or null
 };
