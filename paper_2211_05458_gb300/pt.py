@@ -165,8 +165,8 @@ class ParticleSet:
         rd = torch.float64 if precision == FP64 else torch.float32
 
         def T(a, dt):
-            t = torch.as_tensor(a).to(dtype=dt)
-            t = t.to(device).contiguous()
+            # always a private copy: the push updates these arrays in place
+            t = torch.as_tensor(a).to(device=device, dtype=dt, copy=True).contiguous()
             return t.pin_memory() if pin and t.device.type == "cpu" else t
         x = T(torch.as_tensor(x).T.contiguous(), torch.float64)
         v = T(torch.as_tensor(v).T.contiguous(), rd)

@@ -107,3 +107,15 @@ def test_weak_scaling_aggregation_two_ranks_gloo():
     for rank, ms, v in out:
         assert ms == 150.0  # max over ranks
         assert abs(v - 1000 * 10 * 5 * 2 / 0.15) < 1e-6 * v
+
+
+def test_particle_set_never_aliases_its_inputs():
+    from paper_2211_05458_gb300 import pt
+    x = torch.rand(5, 3, dtype=torch.float64)
+    v = torch.rand(5, 3, dtype=torch.float32)
+    d = torch.rand(5, dtype=torch.float32)
+    el = torch.arange(5, dtype=torch.int32)
+    ps = pt.ParticleSet.create(x, v, d, el, pt.FP32, "cpu")
+    ps.elem[0] = 99
+    ps.d[0] = -1.0
+    assert int(el[0]) == 0 and float(d[0]) >= 0.0
