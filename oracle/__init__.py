@@ -106,6 +106,11 @@ def lib():
             L.or_deposit.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_int64, _D, _D, _D, _I,
                                      _U, _D]
             L.or_lserk_coeffs.argtypes = [_D, _D, _D]
+            L.or_quad_weights.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
+            L.or_deposit_nearest.argtypes = L.or_deposit.argtypes
+            L.or_dt_violations.restype = ctypes.c_int64
+            L.or_dt_violations.argtypes = [ctypes.POINTER(Params), ctypes.c_int64, _D,
+                                           ctypes.c_double]
             L.or_mlp_features.argtypes = [vp, ctypes.c_int, _D, _D]
             L.or_mlp_forward.argtypes = [_D, ctypes.c_int, _D, _D]
             L.or_mlp_loss_grad.restype = ctypes.c_double
@@ -151,6 +156,18 @@ def lagrange(xn, i, x) -> float:
 def lagrange_deriv(xn, i, x) -> float:
     xn = _f64(xn)
     return lib().or_lagrange_deriv(len(xn), _dp(xn), i, float(x))
+
+
+def quad_weights(kind: int, n: int) -> np.ndarray:
+    x = nodes(kind, n)
+    w = np.zeros(n)
+    lib().or_quad_weights(kind, n, _dp(x), _dp(w))
+    return w
+
+
+def dt_violations(params: Params, d, dt: float) -> int:
+    d = _f64(d)
+    return int(lib().or_dt_violations(ctypes.byref(params), len(d), _dp(d), float(dt)))
 
 
 def lserk_coeffs():
@@ -257,6 +274,16 @@ class Oracle:
         S = np.zeros(self.nelem * 4 * nn)
         lib().or_deposit(self.h, ctypes.byref(params), n, _dp(_f64(x)), _dp(_f64(v)),
                          _dp(_f64(d)), _ip(_i32(elem)), _up(status), _dp(S))
+        return S.reshape(self.nelem, 4, nn)
+
+    def deposit_nearest(self, params: Params, x, v, d, elem, status=None):
+        n = len(d)
+        status = np.zeros(n, np.uint32) if status is None else np.ascontiguousarray(
+            status, dtype=np.uint32)
+        nn = (self.N + 1) ** 3
+        S = np.zeros(self.nelem * 4 * nn)
+        lib().or_deposit_nearest(self.h, ctypes.byref(params), n, _dp(_f64(x)), _dp(_f64(v)),
+                                 _dp(_f64(d)), _ip(_i32(elem)), _up(status), _dp(S))
         return S.reshape(self.nelem, 4, nn)
 
     def mlp_features(self, e, x):

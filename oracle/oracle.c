@@ -821,6 +821,82 @@ void or_deposit(const or_ctx* c, const or_params* p, int64_t np, const double* x
   }
 }
 
+/* Quadrature weights of the solution nodes (kind 0 Gauss, 1 GLL):
+ * Gauss w_i = 2 / ((1 - x_i^2) P_n'(x_i)^2); GLL w_i = 2 / (N (N+1) P_N(x_i)^2). */
+void or_quad_weights(int kind, int n, const double* x, double* w) {
+  if (n == 1) {
+    w[0] = 2.0;
+    return;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (kind == 0) {
+      double dp;
+      legendre(n, x[i], &dp);
+      w[i] = 2.0 / ((1.0 - x[i] * x[i]) * dp * dp);
+    } else {
+      int N = n - 1;
+      double p = legendre(N, x[i], NULL);
+      w[i] = 2.0 / (N * (N + 1.0) * p * p);
+    }
+  }
+}
+
+/* Nearest-DoF projection (Sec. 2.3): the whole source of a particle goes to
+ * the node nearest to it, as the density a / V_ijk, V_ijk = w_i w_j w_k |det J|
+ * at that node (the node's share of the element volume).  "Nearest" is taken
+ * per reference direction.  S[nelem][4][n^3] is accumulated into. */
+void or_deposit_nearest(const or_ctx* c, const or_params* p, int64_t np, const double* x,
+                        const double* v, const double* d, const int32_t* elem,
+                        const uint32_t* status, double* S) {
+  const double pi = 3.14159265358979323846;
+  int n = c->n, n3 = n * n * n;
+  double w[MAXN];
+  or_quad_weights(c->node_type, n, c->nodes, w);
+  for (int64_t ip = 0; ip < np; ++ip) {
+    if (status[ip] & OR_ST_FROZEN) continue;
+    int e = elem[ip], it;
+    double xi[3], U[5], rel[3], F[4];
+    if (!or_newton(c, p, e, x + 3 * ip, xi, &it)) continue;
+    or_interp(c, e, xi, U);
+    for (int r = 0; r < 3; ++r) rel[r] = U[1 + r] / U[0] - v[3 * ip + r];
+    double tau = p->rho_p * d[ip] * d[ip] / (18.0 * p->mu);
+    double mp = p->rho_p * pi * d[ip] * d[ip] * d[ip] / 6.0;
+    double fD = drag_factor(p, U[0], rel, d[ip], NULL);
+    F[3] = 0.0;
+    for (int r = 0; r < 3; ++r) {
+      double Fr = mp * fD * rel[r] / tau;
+      F[r] = -Fr;
+      F[3] -= Fr * v[3 * ip + r];
+    }
+    int idx[3];
+    for (int dd = 0; dd < 3; ++dd) {
+      idx[dd] = 0;
+      for (int i = 1; i < n; ++i)
+        if (fabs(xi[dd] - c->nodes[i]) < fabs(xi[dd] - c->nodes[idx[dd]])) idx[dd] = i;
+    }
+    double xn[3] = {c->nodes[idx[0]], c->nodes[idx[1]], c->nodes[idx[2]]}, xx[3], J[9];
+    or_elem_map(c, e, xn, xx, J);
+    double det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+                 J[2] * (J[3] * J[7] - J[4] * J[6]);
+    double V = w[idx[0]] * w[idx[1]] * w[idx[2]] * fabs(det);
+    double* Se = S + (size_t)e * 4 * n3;
+    int node = idx[0] + n * (idx[1] + n * idx[2]);
+    for (int q = 0; q < 4; ++q) Se[(size_t)q * n3 + node] += F[q] / V;
+  }
+}
+
+/* Two-way time-step restriction (Sec. 2.3): with f_D = 1 the source term's
+ * eigenvalue is 1/tau_p; a fourth-order RK scheme allows dt <= 2.75 tau_p.
+ * Returns the number of particles that violate it. */
+int64_t or_dt_violations(const or_params* p, int64_t np, const double* d, double dt) {
+  int64_t bad = 0;
+  for (int64_t ip = 0; ip < np; ++ip) {
+    double tau = p->rho_p * d[ip] * d[ip] / (18.0 * p->mu);
+    if (dt > 2.75 * tau) ++bad;
+  }
+  return bad;
+}
+
 /* ------------------------------------------------------------------------ */
 /* brute-force point location: every element whose Newton solution lies in   */
 /* [-1-tol, 1+tol]^3 (Sec. 3.2.3, localisation in reference space)           */

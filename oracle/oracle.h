@@ -88,6 +88,11 @@ void    or_deposit(const or_ctx* c, const or_params* p, int64_t np, const double
                    const double* v, const double* d, const int32_t* elem,
                    const uint32_t* status, double* S);
 
+void    or_quad_weights(int kind, int n, const double* x, double* w);
+void    or_deposit_nearest(const or_ctx* c, const or_params* p, int64_t np, const double* x,
+                           const double* v, const double* d, const int32_t* elem,
+                           const uint32_t* status, double* S);
+int64_t or_dt_violations(const or_params* p, int64_t np, const double* d, double dt);
 void    or_lserk_coeffs(double* A, double* B, double* C);
 void    or_mlp_features(const or_ctx* c, int e, const double x[3], double feat[51]);
 void    or_mlp_forward(const double* theta, int B, const double* in, double* out);

@@ -603,3 +603,62 @@ def test_mlp_features_affine_element():
         f = orc.mlp_features(e, x)
         assert np.allclose(f[:3], xi, atol=1e-14)
         assert np.abs(f[3:]).max() < 1e-13
+
+
+@pytest.mark.parametrize("n", range(2, 9))
+def test_quadrature_weights(n):
+    # Gauss weights against numpy; GLL weights integrate polynomials of degree 2n-3
+    assert np.allclose(oracle.quad_weights(0, n), np.polynomial.legendre.leggauss(n)[1], atol=1e-14)
+    x, w = oracle.nodes(1, n), oracle.quad_weights(1, n)
+    for k in range(2 * n - 2):
+        exact = (1 - (-1) ** (k + 1)) / (k + 1)
+        assert abs(np.dot(w, x ** k) - exact) < 1e-13
+
+
+def test_nearest_dof_projection_conserves_and_picks_nearest_node():
+    """Sec. 2.3: P{a} = a / V_ijk at the nearest node; sum_ijk S_ijk V_ijk = a."""
+    mesh = W.channel_mesh((3, 3, 2), 2, amp=0.2)
+    N = 3
+    U = W.fluid_uniform(mesh, N, (0.3, 0.0, 0.1))
+    orc = oracle.Oracle(mesh.as_dict())
+    orc.set_fluid(N, 0, _np(U))
+    p = oracle.make_params(drag_law=1)
+    rng = np.random.default_rng(21)
+    P = 40
+    x, el = W.seed_particles(mesh, P, seed=21)
+    vel = rng.normal(size=(P, 3))
+    d = rng.uniform(1e-4, 1e-3, P)
+    S = orc.deposit_nearest(p, _np(x), vel, d, _np(el))
+    Sl = orc.deposit(p, _np(x), vel, d, _np(el))  # Lagrange form: nodal amounts
+    n = N + 1
+    xn, wq = oracle.nodes(0, n), oracle.quad_weights(0, n)
+    # node volumes from the element map
+    tot = np.zeros(4)
+    for e in range(mesh.nelem):
+        for k in range(n):
+            for j in range(n):
+                for i in range(n):
+                    s_ = S[e, :, i + n * (j + n * k)]
+                    if not np.any(s_):
+                        continue
+                    _, J = orc.elem_map(e, np.array([xn[i], xn[j], xn[k]]))
+                    tot += s_ * wq[i] * wq[j] * wq[k] * abs(np.linalg.det(J))
+    assert np.allclose(tot, Sl.sum(axis=(0, 2)), rtol=1e-12)
+    # one particle: exactly one non-zero node, the nearest in reference space
+    ok, xi, _ = orc.newton(int(el[0]), _np(x[0]))
+    S1 = orc.deposit_nearest(p, _np(x[:1]), vel[:1], d[:1], _np(el[:1]))
+    nzn = np.flatnonzero(np.abs(S1[int(el[0])]).max(axis=0))
+    idx = [int(np.argmin(np.abs(xn - xi[q]))) for q in range(3)]
+    assert list(nzn) == [idx[0] + n * (idx[1] + n * idx[2])]
+
+
+def test_dt_violations_threshold():
+    """Sec. 2.3: dt <= 2.75 tau_p, tau_p = rho_p d^2 / (18 mu): a particle just
+    inside the limit passes, one just outside fails."""
+    p = oracle.make_params(mu=1e-5, rho_p=1000.0)
+    d = np.array([1e-4, 2e-4, 5e-5])
+    taus = 1000.0 * d ** 2 / 18e-5
+    dt = 2.75 * taus[0]
+    assert oracle.dt_violations(p, d, dt * (1 - 1e-12)) == 1  # only the 5e-5 particle
+    assert oracle.dt_violations(p, d, dt * (1 + 1e-12)) == 2
+    assert oracle.dt_violations(p, d, 0.0) == 0
