@@ -57,7 +57,11 @@ enum { PT_BC_INTERNAL = 0, PT_BC_WALL = 1, PT_BC_PERIODIC = 2, PT_BC_OPEN = 3 };
 typedef enum { PT_FP64 = 0, PT_FP32 = 1 } pt_precision;
 typedef enum { PT_DRAG_STOKES = 0, PT_DRAG_SCHILLER_NAUMANN = 1 } pt_drag_law;
 typedef enum { PT_GUESS_TRILINEAR = 0, PT_GUESS_MLP = 1 } pt_guess;
-typedef enum { PT_DEPOSIT_ATOMIC = 0, PT_DEPOSIT_SEGMENTED = 1 } pt_deposit_mode;
+typedef enum {
+  PT_DEPOSIT_ATOMIC = 0,     /* FP32 atomics                                   */
+  PT_DEPOSIT_SEGMENTED = 1,  /* element-sorted, fixed summation order          */
+  PT_DEPOSIT_NEAREST = 2     /* flag: nearest-node projection (Sec. 2.3)       */
+} pt_deposit_mode;
 
 /* Mesh of curved hexahedra (Sec. 3.1, Eq. dgsem_curvedfaces).  All arrays are
  * host memory, read during pt_init_mesh and copied; the caller keeps ownership.
@@ -159,7 +163,8 @@ pt_status pt_set_config(pt_ctx* ctx, const pt_config* cfg);
  * node_type 0 = Legendre-Gauss, 1 = Legendre-Gauss-Lobatto,
  * U_dev [nelem][5][(N+1)^3] device array of (rho, rho u1, rho u2, rho u3,
  * rho e) with node (i,j,k) at i + n*(j + n*k); double in PT_FP64 mode, float
- * in PT_FP32 mode.  Caller-owned; read by every later push / deposit. */
+ * in PT_FP32 mode, 16-byte aligned (PT_ERR_ARG otherwise).  Caller-owned;
+ * read by every later push / deposit. */
 pt_status pt_set_fluid(pt_ctx* ctx, int32_t N, int32_t node_type, const void* U_dev);
 
 /* Advances every live particle by nsteps steps of the 5-stage, 4th-order
@@ -184,13 +189,18 @@ pt_status pt_push(pt_ctx* ctx, const pt_particles* p, int32_t nsteps, double dt,
 pt_status pt_push_host(pt_ctx* ctx, const pt_particles* p_host, int32_t nsteps, double dt,
                        pt_stats* out);
 
-/* Two-way coupling source (Sec. 2.3, Eq. theory:source) with Lagrange-basis
- * weights: each live particle's drag F = m_p f_D (u - v) / tau_p contributes
- * momentum -F and energy -F.v_p, spread over the nodes of its element with
- * weights l_i(xi1) l_j(xi2) l_k(xi3).  S_dev [nelem][4][(N+1)^3] float, device,
- * caller-owned, overwritten.  mode PT_DEPOSIT_ATOMIC adds with FP32 atomics
- * (order-dependent rounding); PT_DEPOSIT_SEGMENTED sums each element's
- * particles in index order (bitwise reproducible). */
+/* Two-way coupling source (Sec. 2.3, Eq. theory:source): each live particle's
+ * drag F = m_p f_D (u - v) / tau_p contributes momentum -F and energy -F.v_p.
+ * S_dev [nelem][4][(N+1)^3] float, device, caller-owned, overwritten.
+ * Projection: by default the amounts are spread over the nodes of the
+ * particle's element with weights l_i(xi1) l_j(xi2) l_k(xi3) (nodal amounts);
+ * with the PT_DEPOSIT_NEAREST flag the whole source goes to the node nearest
+ * to xi (per reference direction, the lower node on a tie) as the density
+ * a / V_ijk, V_ijk = w_i w_j w_k |det J(xi_ijk)| the node's quadrature share
+ * of the element volume (the paper's projection operator).  Summation:
+ * PT_DEPOSIT_ATOMIC adds with FP32 atomics (order-dependent rounding);
+ * PT_DEPOSIT_SEGMENTED sums each element's particles in index order (bitwise
+ * reproducible).  Other mode bits: PT_ERR_ARG. */
 pt_status pt_deposit(pt_ctx* ctx, const pt_particles* p, int32_t mode, float* S_dev);
 
 /* pt_deposit without any device allocation (the paper has no counterpart).

@@ -162,6 +162,33 @@ static void bary(int n, const double* x, double* w) {
   }
 }
 
+// Quadrature weights of a node set: the w with sum_i w_i P_k(x_i) = int P_k =
+// 2 delta_k0 for k < n (exact for every polynomial of degree < n, hence
+// w_i = int l_i), solved by Gaussian elimination with partial pivoting.
+static void quad_weights(int n, const double* x, double* w) {
+  double M[PT_MAXN][PT_MAXN + 1];
+  for (int k = 0; k < n; ++k) {
+    for (int i = 0; i < n; ++i) {
+      double p, dp;
+      legendre_pd(k, x[i], &p, &dp);
+      M[k][i] = p;
+    }
+    M[k][n] = k == 0 ? 2.0 : 0.0;
+  }
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(M[r][col]) > std::fabs(M[piv][col])) piv = r;
+    for (int q = 0; q <= n; ++q) std::swap(M[col][q], M[piv][q]);
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      const double f = M[r][col] / M[col][col];
+      for (int q = col; q <= n; ++q) M[r][q] -= f * M[col][q];
+    }
+  }
+  for (int i = 0; i < n; ++i) w[i] = M[i][n] / M[i][i];
+}
+
 // 5-stage 4th-order 2N-storage Runge-Kutta (Carpenter & Kennedy, NASA TM-109112)
 static const double kRK_A[5] = {0.0, -567301805773.0 / 1357537059087.0,
                                 -2404267990393.0 / 2016746695238.0,
@@ -493,6 +520,7 @@ static void fill_consts(const pt_ctx* c, DevConsts& k) {
     k.sw[i] = c->sw[i];
     k.sn32[i] = (float)c->sn[i];
     k.sw32[i] = (float)c->sw[i];
+    k.sq[i] = c->sq[i];
   }
   for (int i = 0; i < 5; ++i) {
     k.A[i] = kRK_A[i];
@@ -619,11 +647,14 @@ pt_status pt_set_fluid(pt_ctx* c, int32_t N, int32_t node_type, const void* U) {
   if (N < 1 || N > 7) return fail(c, PT_ERR_ARG, "N must be 1..7");
   if (node_type != 0 && node_type != 1) return fail(c, PT_ERR_ARG, "node_type must be 0 or 1");
   if (!U) return fail(c, PT_ERR_ARG, "U is NULL");
+  if (reinterpret_cast<uintptr_t>(U) % 16 != 0)
+    return fail(c, PT_ERR_ARG, "U must be 16-byte aligned (vector loads)");
   c->N = N;
   c->node_type = node_type;
   c->U = U;
   solution_nodes(node_type, N + 1, c->sn);
   bary(N + 1, c->sn, c->sw);
+  quad_weights(N + 1, c->sn, c->sq);
   return PT_OK;
 }
 
@@ -883,8 +914,10 @@ pt_status pt_deposit(pt_ctx* c, const pt_particles* p, int32_t mode, float* S) {
   if (c->N < 0 || !c->U) return fail(c, PT_ERR_STATE, "pt_set_fluid was not called");
   pt_status s = validate_particles(c, p);
   if (s) return s;
-  if (mode != PT_DEPOSIT_ATOMIC && mode != PT_DEPOSIT_SEGMENTED)
-    return fail(c, PT_ERR_ARG, "mode must be PT_DEPOSIT_ATOMIC or PT_DEPOSIT_SEGMENTED");
+  if (mode & ~(PT_DEPOSIT_SEGMENTED | PT_DEPOSIT_NEAREST))
+    return fail(c, PT_ERR_ARG,
+                "mode must be PT_DEPOSIT_ATOMIC or PT_DEPOSIT_SEGMENTED, optionally | "
+                "PT_DEPOSIT_NEAREST");
   if (!S) return fail(c, PT_ERR_ARG, "S is NULL");
   const int np = c->N + 1;
   const size_t n3 = (size_t)np * np * np;
@@ -903,14 +936,14 @@ pt_status pt_deposit(pt_ctx* c, const pt_particles* p, int32_t mode, float* S) {
   a.offs = offs;
   a.S = S;
   const bool f64 = c->cfg.precision == PT_FP64;
-  if (mode == PT_DEPOSIT_ATOMIC) {
+  if (!(mode & PT_DEPOSIT_SEGMENTED)) {
     CK(cudaMemsetAsync(S, 0, sizeof(float) * 4 * n3 * c->nelem, c->stream));
     if (n == 0) return PT_OK;
     int grid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)c->nsm * 16);
-    rc = launch_deposit(c->g, f64, np, 0, a, grid, 128, c->stream);
+    rc = launch_deposit(c->g, f64, np, mode, a, grid, 128, c->stream);
   } else {
     int grid = std::min(c->nelem, c->nsm * 32);
-    rc = launch_deposit(c->g, f64, np, 1, a, grid, 256, c->stream);
+    rc = launch_deposit(c->g, f64, np, mode, a, grid, 256, c->stream);
   }
   if (rc) return fail(c, PT_ERR_CUDA, "deposit launch: %s", cudaGetErrorString((cudaError_t)rc));
   return PT_OK;

@@ -36,7 +36,7 @@ struct pt_ctx {
   // fluid
   int N = -1, node_type = 0;
   const void* U = nullptr;
-  double sn[PT_MAXN] = {0}, sw[PT_MAXN] = {0};
+  double sn[PT_MAXN] = {0}, sw[PT_MAXN] = {0}, sq[PT_MAXN] = {0};
   // scratch (binning), permutation, host-call staging
   int* d_scratch = nullptr;
   size_t scratch_ints = 0;

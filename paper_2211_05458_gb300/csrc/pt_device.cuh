@@ -111,6 +111,30 @@ __device__ __forceinline__ void lagr_d(T x, const T* nodes, const T* w, T* l, T*
   }
 }
 
+// G consecutive floats starting at p (p is 16-byte aligned when G == 4 and
+// 8-byte aligned when G is even: row starts are multiples of G in arrays whose
+// per-element blocks are multiples of 16 bytes)
+template <int G>
+__device__ __forceinline__ void load_row(const float* __restrict__ p, float* v) {
+  if constexpr (G == 4) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+  } else if constexpr (G % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < G; i += 2) {
+      const float2 q = __ldg(reinterpret_cast<const float2*>(p + i));
+      v[i] = q.x;
+      v[i + 1] = q.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < G; ++i) v[i] = __ldg(p + i);
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ bool inv3(const T* J, T* Ji) {
   T c00 = J[4] * J[8] - J[5] * J[7];
@@ -190,12 +214,12 @@ __device__ __forceinline__ void map_j32(const float* __restrict__ X, const float
         float T0 = 0.f, T1 = 0.f, T2 = 0.f;
 #pragma unroll
         for (int b = 0; b < G; ++b) {
-          float sv = 0.f, s1 = 0.f;
+          float sv = 0.f, s1 = 0.f, row[G];
+          load_row<G>(Xr + G * (b + G * c), row);
 #pragma unroll
           for (int a = 0; a < G; ++a) {
-            const float xv = __ldg(Xr + a + G * (b + G * c));
-            sv = fmaf(xv, l0[a], sv);
-            s1 = fmaf(xv, d0[a], s1);
+            sv = fmaf(row[a], l0[a], sv);
+            s1 = fmaf(row[a], d0[a], s1);
           }
           T0 = fmaf(sv, l1[b], T0);
           T1 = fmaf(s1, l1[b], T1);
@@ -234,10 +258,10 @@ __device__ __forceinline__ void map64(const double* __restrict__ X, const double
     chi[r] = 0.0;
     if (WJ) J[3 * r] = J[3 * r + 1] = J[3 * r + 2] = 0.0;
   }
-#pragma unroll
+#pragma unroll 1
   for (int c = 0; c < G; ++c) {
     double T0[3] = {0, 0, 0}, T1[3] = {0, 0, 0}, T2[3] = {0, 0, 0};
-#pragma unroll
+#pragma unroll 1
     for (int b = 0; b < G; ++b) {
       double s[3] = {0, 0, 0}, s1[3] = {0, 0, 0};
 #pragma unroll
@@ -285,6 +309,7 @@ __device__ __forceinline__ void trilinear_guess(const DevMesh& m, int e, const f
 template <int G>
 __device__ __forceinline__ bool newton64(const double* X64, const double* xl, double* xi,
                                          const DevConsts& k, int maxit, int& it64) {
+  #pragma unroll 1
   for (int it = 0; it < maxit; ++it) {
     double chi[3], J[9], Ji[9], r[3], d[3];
     map64<G, true>(X64, xi, k, chi, J);
@@ -381,11 +406,11 @@ __device__ __forceinline__ void resid_df(const float* __restrict__ Xh,
         for (int b = 0; b < G; ++b) {
           df_acc a1;
           dacc_init(a1);
+          float rh[G], rl[G];
+          load_row<G>(Ph + G * (b + G * c), rh);
+          load_row<G>(Pl + G * (b + G * c), rl);
 #pragma unroll
-          for (int a = 0; a < G; ++a) {
-            const int i = a + G * (b + G * c);
-            dacc_fma(a1, df{__ldg(Ph + i), __ldg(Pl + i)}, l0[a]);
-          }
+          for (int a = 0; a < G; ++a) dacc_fma(a1, df{rh[a], rl[a]}, l0[a]);
           dacc_fma(a2, dacc_result(a1), l1[b]);
         }
         dacc_fma(a3, dacc_result(a2), l2[c]);
@@ -418,6 +443,7 @@ __device__ __forceinline__ bool newton_df(const DevMesh& m, const DevConsts& k, 
   float z[3] = {guess[0], guess[1], guess[2]};
   float Ji[9];
   bool have = false;
+  #pragma unroll 1
   for (int it = 0; it < 8; ++it) {
     float chi[3], J[9], r[3], d[3];
     map_j32<G>(X32, z, tm, k, chi, J);
@@ -439,6 +465,7 @@ __device__ __forceinline__ bool newton_df(const DevMesh& m, const DevConsts& k, 
 #pragma unroll
     for (int q = 0; q < 3; ++q) zd[q] = df_from(z[q]);
     const float tol = (float)k.newton_tol;
+    #pragma unroll 1
     for (int it = 0; it < 6; ++it) {
       float r[3], d[3];
       resid_df<G>(X32, X32l, zd, tm, xd, k, r);
@@ -496,8 +523,15 @@ __device__ __forceinline__ void interp4(const T* __restrict__ Ue, const T* l1, c
       for (int j = 0; j < NP; ++j) {
         const T* row = Uv + NP * (j + NP * kk);
         T t1 = T(0);
+        if constexpr (std::is_same<T, float>::value && NP % 2 == 0) {
+          float rv[NP];
+          load_row<NP>(reinterpret_cast<const float*>(row), rv);
 #pragma unroll
-        for (int i = 0; i < NP; ++i) t1 = tfma(__ldg(row + i), l1[i], t1);
+          for (int i = 0; i < NP; ++i) t1 = tfma((T)rv[i], l1[i], t1);
+        } else {
+#pragma unroll
+          for (int i = 0; i < NP; ++i) t1 = tfma(__ldg(row + i), l1[i], t1);
+        }
         t2 = tfma(t1, l2[j], t2);
       }
       acc = tfma(t2, l3[kk], acc);
@@ -518,14 +552,15 @@ __device__ __forceinline__ T drag_factor(int law, T re) {
 // tracking (Secs. 3.2.3-3.2.4, 2.4)
 // ---------------------------------------------------------------------------
 
+// Node (mm, kk) of local face f is base + mm sm + kk sk (mm along the face's
+// first in-plane direction, kk along its second).
 template <int G>
-__device__ __forceinline__ int face_node(int f, int mm, int kk) {
+__device__ __forceinline__ void face_strides(int f, int& base, int& sm, int& sk) {
   const int fixed = (f & 1) ? G - 1 : 0;
-  switch (f >> 1) {
-    case 0: return fixed + G * (mm + G * kk);
-    case 1: return mm + G * (fixed + G * kk);
-    default: return mm + G * (kk + G * fixed);
-  }
+  const int dir = f >> 1;
+  base = fixed * (dir == 0 ? 1 : dir == 1 ? G : G * G);
+  sm = dir == 0 ? G : 1;
+  sk = dir == 2 ? G : G * G;
 }
 
 // curved face p(s,t) and its tangents from the element's Lagrange nodes
@@ -538,11 +573,13 @@ __device__ __forceinline__ void face_eval(const double* X64, int f, double s, do
   lagr_d<G, double>(t, k.gn, k.gw, lt, dt);
 #pragma unroll
   for (int r = 0; r < 3; ++r) p[r] = ps[r] = pt[r] = 0.0;
+  int base, sm, sk;
+  face_strides<G>(f, base, sm, sk);
 #pragma unroll
   for (int kk = 0; kk < G; ++kk)
 #pragma unroll
     for (int mm = 0; mm < G; ++mm) {
-      const double* P = X64 + 3 * face_node<G>(f, mm, kk);
+      const double* P = X64 + 3 * (base + mm * sm + kk * sk);
       double w = ls[mm] * lt[kk], wsv = ds[mm] * lt[kk], wtv = ls[mm] * dt[kk];
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
@@ -580,6 +617,7 @@ __device__ __forceinline__ int bilinear_roots(const double* B, const double* xs,
                fabs(D2);
   if (!(scl > 0.0)) return 0;
   int nr = 0;
+  #pragma unroll 1
   for (int pass = 0; pass < 2 && nr == 0; ++pass) {
     // pass 0 eliminates t (quadratic in s), pass 1 eliminates s (quadratic in t)
     double P1 = pass ? C1 : B1, Q1 = pass ? B1 : C1, P2 = pass ? C2 : B2, Q2 = pass ? B2 : C2;
@@ -603,6 +641,7 @@ __device__ __forceinline__ int bilinear_roots(const double* B, const double* xs,
         }
       }
     }
+    #pragma unroll 1
     for (int i = 0; i < k; ++i) {
       double u = r[i];
       double den1 = A1 * u + Q1, den2 = A2 * u + Q2, w;
@@ -700,16 +739,19 @@ __device__ __forceinline__ bool curved_newton_f32(const float* __restrict__ X32,
                                                   const DevConsts& k, float& s, float& t,
                                                   float& al) {
   constexpr int G3 = G * G * G;
+  #pragma unroll 1
   for (int it = 0; it < 12; ++it) {
     float ls[G], ds[G], lt[G], dt[G];
     lagr_d<G, float>(s, k.gn32, k.gw32, ls, ds);
     lagr_d<G, float>(t, k.gn32, k.gw32, lt, dt);
     float p[3] = {0, 0, 0}, ps[3] = {0, 0, 0}, pt[3] = {0, 0, 0};
+    int base, sm, sk;
+    face_strides<G>(f, base, sm, sk);
 #pragma unroll
     for (int kk = 0; kk < G; ++kk)
 #pragma unroll
       for (int mm = 0; mm < G; ++mm) {
-        const int q = face_node<G>(f, mm, kk);
+        const int q = base + mm * sm + kk * sk;
         const float w = ls[mm] * lt[kk], wsv = ds[mm] * lt[kk], wtv = ls[mm] * dt[kk];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
@@ -744,6 +786,7 @@ template <int G>
 __device__ __forceinline__ bool curved_refine(const double* X64, int f, const double* xs,
                                               const double* td, const DevConsts& k, double& s,
                                               double& t, double& al, double L) {
+  #pragma unroll 1
   for (int it = 0; it < 20; ++it) {
     double p[3], ps[3], pt[3], F[3], J[9], Ji[9], dl[3];
     face_eval<G>(X64, f, s, t, k, p, ps, pt);
@@ -868,6 +911,7 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
     const float xlf[3] = {(float)xl[0], (float)xl[1], (float)xl[2]};
     double best = 1e300, bs = 0.0, bt = 0.0;
     int bf = -1;
+#pragma unroll 1
     for (int f = 0; f < 6; ++f) {
       if (f == fin) continue;
       // slab prefilter (FP32, conservative: the margins cover its rounding)
@@ -892,6 +936,7 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
                          4.f * (float)k.band_x;
         const float a0f = (float)a0;
         bool any = ill;
+        #pragma unroll 1
         for (int i = 0; i < n32 && !ill; ++i) {
           if (kind == PT_FACE_CURVED &&
               !curved_newton_f32<G>(m.xg32 + (size_t)e * 3 * G * G * G, f, xlf, tdf, k, fs[i],
@@ -916,6 +961,7 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
         const double dev = (double)__ldg(sl + 6);
         const double reach = 4.0 * dev / fmax((double)fabsf(cosf_), 0.05) + 2.0 * k.band_x;
         int kk = 0;
+        #pragma unroll 1
         for (int i = 0; i < nr; ++i) {
           double s = rs[i], t = rt[i], al = ra[i];
           if (!(fabs(s) < 2.0 && fabs(t) < 2.0)) continue;
@@ -934,6 +980,7 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
         }
         nr = kk;
       }
+      #pragma unroll 1
       for (int i = 0; i < nr; ++i) {
         double al = ra[i], s = rs[i], t = rt[i];
         double mm = fmax(fabs(s), fabs(t));

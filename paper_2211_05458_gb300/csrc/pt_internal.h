@@ -53,6 +53,7 @@ struct DevConsts {
   float gn_hi[PT_MAXG], gn_lo[PT_MAXG], gw_hi[PT_MAXG], gw_lo[PT_MAXG];  // double-float copies
   double sn[PT_MAXN], sw[PT_MAXN];   // solution nodes / barycentric weights
   float sn32[PT_MAXN], sw32[PT_MAXN];
+  double sq[PT_MAXN];                // quadrature weights of the solution nodes
   double A[5], B[5];
   float A32[5], B32[5];
   double mu, rho_p, g[3], mask[3];

@@ -102,6 +102,96 @@ struct PushCounters {
   TrackCounters tc;
 };
 
+// Missed-crossing repair.  Curved faces are intersected by Newton from the
+// roots of their bilinear patch, which can miss a near-tangential crossing
+// (the ray leaves through the curved face where the patch has no nearby
+// root).  Such a particle is found outside its element by the next inverse map
+// (max |xi| > 1 + lost_tol).  It is then moved across the face of its largest
+// |xi_d| -- translated on a periodic face -- and mapped again, until it lands
+// inside, across at most 4 faces; a wall or open face ends the walk and the
+// particle is lost as before.  Only a stage that took the exact tracking path
+// can leave a particle outside, so the push checks the final position of such
+// a stage as well.  Returns 0 (inside), 1 (inverse map failed) or 2 (lost).
+// Out of line: it is rare.
+__device__ __forceinline__ int settle_face(const double* z) {
+  const double a0 = fabs(z[0]), a1 = fabs(z[1]), a2 = fabs(z[2]);
+  const int d = (a0 >= a1 && a0 >= a2) ? 0 : (a1 >= a2 ? 1 : 2);
+  return 2 * d + (z[d] > 0.0 ? 1 : 0);
+}
+
+// FP64 mode: x global, xi valid on entry if have.
+template <int G>
+__device__ __noinline__ int settle64(const DevMesh& m, const DevConsts& k, int& e, double* x,
+                                     double* xi, bool have, int& it64, int& cross) {
+#pragma unroll 1
+  for (int w = 0; w <= 4; ++w) {
+    if (!have) {
+      const double* ce = m.ce + 3 * (size_t)e;
+      const double xl[3] = {x[0] - __ldg(ce), x[1] - __ldg(ce + 1), x[2] - __ldg(ce + 2)};
+      const float xf[3] = {(float)xl[0], (float)xl[1], (float)xl[2]};
+      float g[3];
+      trilinear_guess(m, e, xf, g);
+      xi[0] = g[0];
+      xi[1] = g[1];
+      xi[2] = g[2];
+      if (!newton64<G>(m.xg64 + (size_t)e * 3 * G * G * G, xl, xi, k, k.max_newton, it64))
+        return 1;
+    }
+    have = false;
+    if (tmax3(xi[0], xi[1], xi[2]) <= 1.0 + k.lost_tol) return 0;
+    if (w == 4) break;
+    const int f = settle_face(xi);
+    const int bc = __ldg(m.finfo + 6 * (size_t)e + f) & 3;
+    if (bc != PT_BC_INTERNAL && bc != PT_BC_PERIODIC) break;
+    if (bc == PT_BC_PERIODIC) {
+      const double* sh = m.shift + 18 * (size_t)e + 3 * f;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) x[r] += __ldg(sh + r);
+    }
+    e = __ldg(m.fnbr + 6 * (size_t)e + f);
+    ++cross;
+  }
+  return 2;
+}
+
+// FP32 mode: xd local double-float position in element e, zd its xi (valid
+// on entry if have).
+template <int G>
+__device__ __noinline__ int settle_f32(const DevMesh& m, const DevConsts& k, int& e, df* xd,
+                                       df* zd, bool have, int& it32, int& it64, int& cross) {
+#pragma unroll 1
+  for (int w = 0; w <= 4; ++w) {
+    if (!have) {
+      const float xf[3] = {xd[0].hi, xd[1].hi, xd[2].hi};
+      float g[3];
+      trilinear_guess(m, e, xf, g);
+      if (!newton_df<G>(m, k, e, xd, g, zd, it32, it64)) return 1;
+    }
+    have = false;
+    const double z[3] = {df_to_double(zd[0]), df_to_double(zd[1]), df_to_double(zd[2])};
+    if (tmax3(z[0], z[1], z[2]) <= 1.0 + k.lost_tol) return 0;
+    if (w == 4) break;
+    const int f = settle_face(z);
+    const int bc = __ldg(m.finfo + 6 * (size_t)e + f) & 3;
+    if (bc != PT_BC_INTERNAL && bc != PT_BC_PERIODIC) break;
+    const double* ce = m.ce + 3 * (size_t)e;
+    double xg[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) xg[r] = __ldg(ce + r) + df_to_double(xd[r]);
+    if (bc == PT_BC_PERIODIC) {
+      const double* sh = m.shift + 18 * (size_t)e + 3 * f;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) xg[r] += __ldg(sh + r);
+    }
+    e = __ldg(m.fnbr + 6 * (size_t)e + f);
+    const double* cn = m.ce + 3 * (size_t)e;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) xd[r] = df_from_double(xg[r] - __ldg(cn + r));
+    ++cross;
+  }
+  return 2;
+}
+
 // Advances particle ip of p by nsteps RK steps: per stage the inverse map,
 // interpolation of rho and rho u, drag + gravity, the low-storage RK update of
 // x and v, and tracking of the stage segment.  State lives in registers for
@@ -142,6 +232,7 @@ __device__ __forceinline__ void push_particle(const DevMesh& m, const DevConsts&
     live = false;
   }
   const R tau = (R)k.rho_p * d * d / (R(18) * mu);
+  bool pending = false;  // the last stage took the exact tracking path
   for (int step = 0; step < nsteps; ++step) {
     R kx[3] = {0, 0, 0}, kv[3] = {0, 0, 0};
     for (int s = 0; s < 5; ++s) {
@@ -164,12 +255,20 @@ __device__ __forceinline__ void push_particle(const DevMesh& m, const DevConsts&
         live = false;
         continue;
       }
-      const double mx = tmax3(xi[0], xi[1], xi[2]);
+      double mx = tmax3(xi[0], xi[1], xi[2]);
       if (mx > 1.0 + k.lost_tol) {
-        st |= PT_ST_LOST;
-        live = false;
-        continue;
+        int cr = 0, j64 = 0;
+        const int rc = settle64<G>(m, k, e, x, xi, true, j64, cr);
+        c.it64 += j64;
+        c.tc.cross += cr;
+        if (rc) {
+          st |= rc == 1 ? PT_ST_NEWTON_FAIL : PT_ST_LOST;
+          live = false;
+          continue;
+        }
+        mx = tmax3(xi[0], xi[1], xi[2]);
       }
+      pending = false;
       if (mx > 1.0 - k.band_ref) st |= PT_ST_NEAR_FACE;
       // interpolation of rho, rho u at xi
       R l1[NP], l2[NP], l3[NP], Uv[4];
@@ -200,10 +299,20 @@ __device__ __forceinline__ void push_particle(const DevMesh& m, const DevConsts&
         bf[r] = F64 ? (float)(xl[r] + (double)dx) : xf[r] + (float)dx;
         v[r] = v[r] + Bs * kv[r];
       }
+      const int slow0 = c.tc.slow;
       track<G, R>(m, k, e, x, xe, xf, bf, v, kx, kv, hits, st, c.tc);
+      pending = c.tc.slow != slow0;
       if (st & PT_ST_FROZEN) live = false;
     }
     if (live) ++c.steps;
+  }
+  if (live && pending) {
+    double xi[3];
+    int cr = 0, j64 = 0;
+    const int rc = settle64<G>(m, k, e, x, xi, false, j64, cr);
+    c.it64 += j64;
+    c.tc.cross += cr;
+    if (rc) st |= rc == 1 ? PT_ST_NEWTON_FAIL : PT_ST_LOST;
   }
   if (inrange && !(p.status[ip] & PT_ST_FROZEN)) {
     p.x[ip] = x[0];
@@ -262,6 +371,7 @@ __device__ __forceinline__ void push_particle_f32(const DevMesh& m, const DevCon
     for (int r = 0; r < 3; ++r) xd[r] = df_from_double(x[r] - __ldg(ce + r));
   }
   bool moved = false;
+  bool pending = false;  // the last stage took the exact tracking path
   const float tau = (float)k.rho_p * d * d / (18.f * mu);
   for (int step = 0; step < nsteps; ++step) {
     float kx[3] = {0, 0, 0}, kv[3] = {0, 0, 0};
@@ -283,18 +393,30 @@ __device__ __forceinline__ void push_particle_f32(const DevMesh& m, const DevCon
         live = false;
         continue;
       }
-      const float xi[3] = {zd[0].hi + zd[0].lo, zd[1].hi + zd[1].lo, zd[2].hi + zd[2].lo};
+      float xi[3] = {zd[0].hi + zd[0].lo, zd[1].hi + zd[1].lo, zd[2].hi + zd[2].lo};
       const float mx = tmax3(xi[0], xi[1], xi[2]);
       if (mx > 1.f - 1e-5f) {  // decide the bands exactly (rare)
         double md = fmax(fmax(fabs(df_to_double(zd[0])), fabs(df_to_double(zd[1]))),
                          fabs(df_to_double(zd[2])));
         if (md > 1.0 + k.lost_tol) {
-          st |= PT_ST_LOST;
-          live = false;
-          continue;
+          int cr = 0, j32 = 0, j64 = 0;
+          const int rc = settle_f32<G>(m, k, e, xd, zd, true, j32, j64, cr);
+          c.it32 += j32;
+          c.it64 += j64;
+          c.tc.cross += cr;
+          if (rc) {
+            st |= rc == 1 ? PT_ST_NEWTON_FAIL : PT_ST_LOST;
+            live = false;
+            continue;
+          }
+#pragma unroll
+          for (int q = 0; q < 3; ++q) xi[q] = zd[q].hi + zd[q].lo;
+          md = fmax(fmax(fabs(df_to_double(zd[0])), fabs(df_to_double(zd[1]))),
+                    fabs(df_to_double(zd[2])));
         }
         if (md > 1.0 - k.band_ref) st |= PT_ST_NEAR_FACE;
       }
+      pending = false;
       // interpolation of rho, rho u at xi
       float l1[NP], l2[NP], l3[NP], Uv[4];
       lagr<NP, float>(xi[0], k.sn32, k.sw32, l1);
@@ -347,9 +469,22 @@ __device__ __forceinline__ void push_particle_f32(const DevMesh& m, const DevCon
         const double* cn = m.ce + 3 * (size_t)e;
 #pragma unroll
         for (int r = 0; r < 3; ++r) xd[r] = df_from_double(xs[r] - __ldg(cn + r));
+        pending = true;
       }
     }
     if (live) ++c.steps;
+  }
+  if (live && pending) {
+    df zd[3];
+    int cr = 0, j32 = 0, j64 = 0;
+    const int rc = settle_f32<G>(m, k, e, xd, zd, false, j32, j64, cr);
+    c.it32 += j32;
+    c.it64 += j64;
+    c.tc.cross += cr;
+    if (rc) {
+      st |= rc == 1 ? PT_ST_NEWTON_FAIL : PT_ST_LOST;
+      live = false;
+    }
   }
   if (inrange && !(p.status[ip] & PT_ST_FROZEN)) {
     if (live || !moved) {
@@ -432,12 +567,17 @@ __global__ void __launch_bounds__(256) k_locate(const __grid_constant__ LocateAr
   }
 }
 
-// Per-particle source of Eq. theory:source with Lagrange weights: returns the
-// element and fills f[4] = (-F, -F.v) and the three 1-D bases; false if the
-// particle is frozen or its inverse map fails.
-template <int G, int NP, bool F64>
+// Per-particle source of Eq. theory:source: returns the element and fills
+// f[4] = (-F, -F.v) and three 1-D weight vectors whose outer product spreads f
+// over the element's nodes; false if the particle is frozen or its inverse map
+// fails.  Lagrange projection: the bases l(xi).  Nearest-node projection
+// (NEAR): one-hot vectors at the node nearest to xi per direction (lower node
+// on a tie), with f divided by that node's volume V_ijk = w_i w_j w_k |det J|;
+// node[0] receives the node's index within the element.
+template <int G, int NP, bool F64, bool NEAR>
 __device__ __forceinline__ bool particle_source(const DepositArgs& a, int64_t ip, int& e,
-                                                float* f, float* l1, float* l2, float* l3) {
+                                                float* f, float* l1, float* l2, float* l3,
+                                                int* node) {
   using R = typename RealOf<F64>::type;
   constexpr int N3 = NP * NP * NP;
   const int64_t n = a.p.n;
@@ -480,6 +620,40 @@ __device__ __forceinline__ bool particle_source(const DepositArgs& a, int64_t ip
     f[r] = (float)(-Fr);
     Fe -= Fr * v[r];
   }
+  if constexpr (NEAR) {
+    int id[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      int best = 0;
+      double bd = fabs(xi[q] - a.k.sn[0]);
+#pragma unroll
+      for (int i = 1; i < NP; ++i) {
+        const double di = fabs(xi[q] - a.k.sn[i]);
+        if (di < bd) {
+          bd = di;
+          best = i;
+        }
+      }
+      id[q] = best;
+    }
+    const double xn[3] = {a.k.sn[id[0]], a.k.sn[id[1]], a.k.sn[id[2]]};
+    double chi[3], J[9];
+    map64<G, true>(a.m.xg64 + (size_t)e * G * G * G * 3, xn, a.k, chi, J);
+    const double det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+                       J[2] * (J[3] * J[7] - J[4] * J[6]);
+    const R iv = R(1) / (R)(a.k.sq[id[0]] * a.k.sq[id[1]] * a.k.sq[id[2]] * fabs(det));
+#pragma unroll
+    for (int r = 0; r < 3; ++r) f[r] = (float)(-(c * rel[r]) * iv);
+    f[3] = (float)(Fe * iv);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      l1[i] = i == id[0] ? 1.f : 0.f;
+      l2[i] = i == id[1] ? 1.f : 0.f;
+      l3[i] = i == id[2] ? 1.f : 0.f;
+    }
+    *node = id[0] + NP * (id[1] + NP * id[2]);
+    return true;
+  }
   f[3] = (float)Fe;
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
@@ -487,30 +661,37 @@ __device__ __forceinline__ bool particle_source(const DepositArgs& a, int64_t ip
     l2[i] = (float)lr2[i];
     l3[i] = (float)lr3[i];
   }
+  *node = 0;
   return true;
 }
 
 // FP32 atomics straight into S (S cleared beforehand)
-template <int G, int NP, bool F64>
+template <int G, int NP, bool F64, bool NEAR>
 __global__ void __launch_bounds__(256) k_deposit_atomic(const DepositArgs a) {
   constexpr int N3 = NP * NP * NP;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.p.n; t += stride) {
     const int64_t ip = a.perm ? (int64_t)a.perm[t] : t;
-    int e;
+    int e, node;
     float f[4], l1[NP], l2[NP], l3[NP];
-    if (!particle_source<G, NP, F64>(a, ip, e, f, l1, l2, l3)) continue;
+    if (!particle_source<G, NP, F64, NEAR>(a, ip, e, f, l1, l2, l3, &node)) continue;
     float* Se = a.S + (size_t)e * 4 * N3;
-#pragma unroll 1
-    for (int q = 0; q < 4; ++q)
-#pragma unroll 1
-      for (int kk = 0; kk < NP; ++kk)
+    if constexpr (NEAR) {
 #pragma unroll
-        for (int j = 0; j < NP; ++j) {
-          const float w = f[q] * l3[kk] * l2[j];
+      for (int q = 0; q < 4; ++q) atomicAdd(Se + q * N3 + node, f[q]);
+    } else {
+#pragma unroll 1
+      for (int q = 0; q < 4; ++q)
+#pragma unroll 1
+        for (int kk = 0; kk < NP; ++kk)
 #pragma unroll
-          for (int i = 0; i < NP; ++i) atomicAdd(Se + q * N3 + i + NP * (j + NP * kk), w * l1[i]);
-        }
+          for (int j = 0; j < NP; ++j) {
+            const float w = f[q] * l3[kk] * l2[j];
+#pragma unroll
+            for (int i = 0; i < NP; ++i)
+              atomicAdd(Se + q * N3 + i + NP * (j + NP * kk), w * l1[i]);
+          }
+    }
   }
 }
 
@@ -519,7 +700,7 @@ __global__ void __launch_bounds__(256) k_deposit_atomic(const DepositArgs a) {
 // their sources staged in shared memory, and every output node sums them in
 // that fixed order -- S_e[q][ijk] = sum_p f_q(p) l_i(p) l_j(p) l_k(p).
 constexpr int SEG_TILE = 128;
-template <int G, int NP, bool F64>
+template <int G, int NP, bool F64, bool NEAR>
 __global__ void __launch_bounds__(256) k_deposit_segmented(const DepositArgs a) {
   constexpr int N3 = NP * NP * NP;
   __shared__ int idx[SEG_TILE];
@@ -548,9 +729,9 @@ __global__ void __launch_bounds__(256) k_deposit_segmented(const DepositArgs a) 
       }
       __syncthreads();
       if (threadIdx.x < cnt) {
-        int ee;
+        int ee, node;
         float f[4], l1[NP], l2[NP], l3[NP];
-        bool ok = particle_source<G, NP, F64>(a, idx[threadIdx.x], ee, f, l1, l2, l3);
+        bool ok = particle_source<G, NP, F64, NEAR>(a, idx[threadIdx.x], ee, f, l1, l2, l3, &node);
         sok[threadIdx.x] = ok;
 #pragma unroll
         for (int q = 0; q < 4; ++q) sf[threadIdx.x][q] = ok ? f[q] : 0.f;
@@ -597,12 +778,16 @@ struct Family {
       k_push<G, NP, F64, false><<<grid, block, 0, s>>>(a);
     return (int)cudaGetLastError();
   }
+  // mode bit 0: segmented summation, bit 1: nearest-node projection
   template <int NP>
   static int dep(int mode, const DepositArgs& a, int grid, int block, cudaStream_t s) {
-    if (mode == 0)
-      k_deposit_atomic<G, NP, F64><<<grid, block, 0, s>>>(a);
-    else
-      k_deposit_segmented<G, NP, F64><<<grid, 256, 0, s>>>(a);
+    switch (mode) {
+      case 0: k_deposit_atomic<G, NP, F64, false><<<grid, block, 0, s>>>(a); break;
+      case 1: k_deposit_segmented<G, NP, F64, false><<<grid, 256, 0, s>>>(a); break;
+      case 2: k_deposit_atomic<G, NP, F64, true><<<grid, block, 0, s>>>(a); break;
+      case 3: k_deposit_segmented<G, NP, F64, true><<<grid, 256, 0, s>>>(a); break;
+      default: return (int)cudaErrorInvalidValue;
+    }
     return (int)cudaGetLastError();
   }
   template <int NP>

@@ -61,8 +61,9 @@ extern "C" pt_status pt_deposit_noalloc(pt_ctx* c, const pt_particles* p, int32_
     c->err = "pt_deposit_noalloc: bad particle arrays";
     return PT_ERR_ARG;
   }
-  if (mode != PT_DEPOSIT_ATOMIC && mode != PT_DEPOSIT_SEGMENTED) {
-    c->err = "pt_deposit_noalloc: mode must be PT_DEPOSIT_ATOMIC or PT_DEPOSIT_SEGMENTED";
+  if (mode & ~(PT_DEPOSIT_SEGMENTED | PT_DEPOSIT_NEAREST)) {
+    c->err = "pt_deposit_noalloc: mode must be PT_DEPOSIT_ATOMIC or PT_DEPOSIT_SEGMENTED, "
+             "optionally | PT_DEPOSIT_NEAREST";
     return PT_ERR_ARG;
   }
   if (!S) {
@@ -103,7 +104,7 @@ extern "C" pt_status pt_deposit_noalloc(pt_ctx* c, const pt_particles* p, int32_
   a.offs = offs;
   a.S = S;
   const bool f64 = c->cfg.precision == PT_FP64;
-  if (mode == PT_DEPOSIT_ATOMIC) {
+  if (!(mode & PT_DEPOSIT_SEGMENTED)) {
     e = cudaMemsetAsync(S, 0, sizeof(float) * 4 * n3 * c->nelem, c->stream);
     if (e != cudaSuccess) {
       c->err = std::string("pt_deposit_noalloc: ") + cudaGetErrorString(e);
@@ -111,10 +112,10 @@ extern "C" pt_status pt_deposit_noalloc(pt_ctx* c, const pt_particles* p, int32_
     }
     if (n == 0) return PT_OK;
     const int grid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)c->nsm * 16);
-    rc = pt::launch_deposit(c->g, f64, np, 0, a, grid, 128, c->stream);
+    rc = pt::launch_deposit(c->g, f64, np, mode, a, grid, 128, c->stream);
   } else {
     const int grid = std::min(c->nelem, c->nsm * 32);
-    rc = pt::launch_deposit(c->g, f64, np, 1, a, grid, 256, c->stream);
+    rc = pt::launch_deposit(c->g, f64, np, mode, a, grid, 256, c->stream);
   }
   if (rc) {
     c->err = std::string("pt_deposit_noalloc: launch: ") + cudaGetErrorString((cudaError_t)rc);

@@ -21,7 +21,7 @@ ST_FROZEN = ST_NEWTON_FAIL | ST_LOST | ST_CROSS_CAP | ST_OPEN
 FP64, FP32 = 0, 1
 STOKES, SCHILLER_NAUMANN = 0, 1
 GUESS_TRILINEAR, GUESS_MLP = 0, 1
-DEPOSIT_ATOMIC, DEPOSIT_SEGMENTED = 0, 1
+DEPOSIT_ATOMIC, DEPOSIT_SEGMENTED, DEPOSIT_NEAREST = 0, 1, 2
 
 _vp = ctypes.c_void_p
 

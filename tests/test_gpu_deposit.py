@@ -10,6 +10,7 @@ import torch
 
 from paper_2211_05458_gb300 import pt
 from paper_2211_05458_gb300 import workloads as W
+import oracle
 from tests import helpers as H
 
 pytestmark = pytest.mark.gpu
@@ -63,3 +64,66 @@ def test_empty_elements_are_zero_and_frozen_particles_skipped():
     assert float(S.abs().max()) == 0.0
     S = ctx.deposit(parts, pt.DEPOSIT_ATOMIC)
     assert float(S.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("summation", [pt.DEPOSIT_ATOMIC, pt.DEPOSIT_SEGMENTED])
+def test_nearest_node_projection_matches_oracle(precision, summation):
+    """Sec. 2.3 projection P{a} = a / V_ijk at the nearest node.  Particles whose
+    xi lies within 1e-8 of a midpoint between two nodes (where either node is
+    a correct choice) are frozen on both sides."""
+    wl = _state(dims=(5, 4, 4), ngeo=2, N=5, P=4000, seed=3)
+    orc = H.make_oracle(wl)
+    x, el = H.np64(wl.x), H.np64(wl.elem).astype(np.int32)
+    xn = oracle.nodes(wl.node_type, wl.N + 1)
+    mids = 0.5 * (xn[1:] + xn[:-1])
+    status = np.zeros(len(el), np.uint32)
+    for i in range(len(el)):
+        ok, xi, _ = orc.newton(int(el[i]), x[i])
+        if ok and np.min(np.abs(xi[:, None] - mids[None, :])) < 1e-8:
+            status[i] = oracle.ST_LOST
+    p = H.oracle_params(wl)
+    So = orc.deposit_nearest(p, x, H.np64(wl.v), H.np64(wl.d), el, status)
+    ctx = H.gpu_context(wl, precision)
+    parts = H.gpu_particles(wl, ctx)
+    parts.status.copy_(torch.as_tensor(status.astype(np.int32)))
+    S = ctx.deposit(parts, summation | pt.DEPOSIT_NEAREST).double().cpu().numpy()
+    # the same nodes are hit, with the same densities
+    assert np.array_equal(S != 0, So != 0)
+    assert np.max(np.abs(S - So)) <= 1e-5 * np.abs(So).max()
+    # per-element sums of each source component
+    es, eo = S.sum(axis=2), So.sum(axis=2)
+    assert np.max(np.abs(es - eo) / np.abs(eo).max(axis=0, keepdims=True)) < 1e-5
+
+
+def test_nearest_segmented_is_bitwise_reproducible():
+    wl = _state(P=20_000)
+    ctx = H.gpu_context(wl, "fp32")
+    parts = H.gpu_particles(wl, ctx)
+    mode = pt.DEPOSIT_SEGMENTED | pt.DEPOSIT_NEAREST
+    a = ctx.deposit(parts, mode).clone()
+    b = ctx.deposit(parts, mode).clone()
+    assert torch.equal(a, b)
+    c = ctx.deposit(parts, pt.DEPOSIT_NEAREST)
+    assert float((a - c).abs().max()) <= 1e-5 * float(a.abs().max())
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_two_way_time_step_guard_counts_like_oracle(precision):
+    """Sec. 2.3 restriction dt <= 2.75 tau_p, reported as PT_WARN_DT with the
+    number of violating particles; the push itself still runs."""
+    wl = _state(P=2000, seed=4)
+    rng = np.random.default_rng(4)
+    wl.d = torch.as_tensor(10 ** rng.uniform(-5.2, -4.9, 2000))  # dt / tau_p in [1, 5]
+    ctx = H.gpu_context(wl, precision)
+    parts = H.gpu_particles(wl, ctx)
+    d_used = parts.d.double().cpu().numpy()  # as the kernel reads them (FP32 rounded in FP32 mode)
+    dt = 1e-3
+    tau = wl.rho_p * d_used ** 2 / (18 * wl.mu)
+    assert np.min(np.abs(dt / (2.75 * tau) - 1)) > 1e-6  # no particle at the threshold
+    expect = oracle.dt_violations(H.oracle_params(wl), d_used, dt)
+    assert 0 < expect < 2000
+    st = ctx.push(parts, 1, dt)
+    assert st["dt_warn"] == expect
+    errors = st["newton_fail"] + st["lost"] + st["cross_cap"]
+    assert st["status_code"] == pt.PT_WARN_DT or errors > 0
