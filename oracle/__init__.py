@@ -57,13 +57,15 @@ class Params(ctypes.Structure):
         ("max_cross", ctypes.c_int), ("pad", ctypes.c_int),
         ("newton_tol", ctypes.c_double), ("band_ref", ctypes.c_double),
         ("band_x", ctypes.c_double), ("lost_tol", ctypes.c_double),
+        ("lift", ctypes.c_int), ("pad2", ctypes.c_int), ("sphericity", ctypes.c_double),
     ]
 
 
 def make_params(mu=1e-5, rho_p=1000.0, drag_law=0, g=(0.0, 0.0, 0.0), mask=(1.0, 1.0, 1.0),
                 max_newton=50, max_cross=64, newton_tol=1e-12, band_ref=1e-10, band_x=1e-10,
-                lost_tol=1e-6) -> Params:
+                lost_tol=1e-6, lift=0, sphericity=1.0) -> Params:
     p = Params()
+    p.lift, p.sphericity = lift, sphericity
     p.mu, p.rho_p, p.drag_law, p.max_newton = mu, rho_p, drag_law, max_newton
     p.g[:] = list(g)
     p.mask[:] = list(mask)
@@ -96,6 +98,12 @@ def lib():
             L.or_newton.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_int, _D, _D,
                                     ctypes.POINTER(ctypes.c_int)]
             L.or_interp.argtypes = [vp, ctypes.c_int, _D, _D]
+            L.or_interp_grad.argtypes = [vp, ctypes.c_int, _D, _D, _D]
+            L.or_velocity_gradient.argtypes = [vp, ctypes.c_int, _D, _D]
+            L.or_drag_factor.restype = ctypes.c_double
+            L.or_drag_factor.argtypes = [ctypes.POINTER(Params), ctypes.c_double]
+            L.or_saffman_force.argtypes = [ctypes.POINTER(Params), ctypes.c_double, _D, _D,
+                                           ctypes.c_double, _D]
             L.or_face_hits.argtypes = [vp, ctypes.c_int, ctypes.c_int, _D, _D, ctypes.c_double,
                                        _D, ctypes.c_int]
             L.or_face_ctrl.argtypes = [vp, ctypes.c_int, ctypes.c_int, _D]
@@ -170,6 +178,17 @@ def dt_violations(params: Params, d, dt: float) -> int:
     return int(lib().or_dt_violations(ctypes.byref(params), len(d), _dp(d), float(dt)))
 
 
+def drag_factor(params: Params, re: float) -> float:
+    return float(lib().or_drag_factor(ctypes.byref(params), float(re)))
+
+
+def saffman_force(params: Params, rho, rel, omega, d):
+    F = np.zeros(3)
+    lib().or_saffman_force(ctypes.byref(params), float(rho), _dp(_f64(rel)), _dp(_f64(omega)),
+                           float(d), _dp(F))
+    return F
+
+
 def lserk_coeffs():
     A, B, C = np.zeros(5), np.zeros(5), np.zeros(5)
     lib().or_lserk_coeffs(_dp(A), _dp(B), _dp(C))
@@ -231,6 +250,17 @@ class Oracle:
         U = np.zeros(5)
         lib().or_interp(self.h, int(e), _dp(xi), _dp(U))
         return U
+
+    def interp_grad(self, e, xi):
+        xi = _f64(xi)
+        U, dU = np.zeros(5), np.zeros(15)
+        lib().or_interp_grad(self.h, int(e), _dp(xi), _dp(U), _dp(dU))
+        return U, dU.reshape(5, 3)
+
+    def velocity_gradient(self, e, xi):
+        G = np.zeros(9)
+        lib().or_velocity_gradient(self.h, int(e), _dp(_f64(xi)), _dp(G))
+        return G.reshape(3, 3)
 
     def face_hits(self, e, f, x0, x1, band=0.0):
         out = np.zeros(3 * 16)

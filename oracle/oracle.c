@@ -269,6 +269,58 @@ void or_interp(const or_ctx* c, int e, const double xi[3], double U[5]) {
   }
 }
 
+/* U and its reference-space derivatives dU[v][q] = dU_v / dxi_q, by
+ * differentiating the same Lagrange interpolant. */
+void or_interp_grad(const or_ctx* c, int e, const double xi[3], double U[5], double dU[15]) {
+  int n = c->n;
+  double l[3][MAXN], dl[3][MAXN];
+  for (int d = 0; d < 3; ++d)
+    for (int i = 0; i < n; ++i) {
+      l[d][i] = or_lagrange(n, c->nodes, i, xi[d]);
+      dl[d][i] = or_lagrange_deriv(n, c->nodes, i, xi[d]);
+    }
+  const double* Ue = c->U + (size_t)e * 5 * n * n * n;
+  for (int v = 0; v < 5; ++v) {
+    double s = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          double u = Ue[(size_t)v * n * n * n + i + n * (j + n * k)];
+          s += u * l[0][i] * l[1][j] * l[2][k];
+          s0 += u * dl[0][i] * l[1][j] * l[2][k];
+          s1 += u * l[0][i] * dl[1][j] * l[2][k];
+          s2 += u * l[0][i] * l[1][j] * dl[2][k];
+        }
+    U[v] = s;
+    dU[3 * v] = s0;
+    dU[3 * v + 1] = s1;
+    dU[3 * v + 2] = s2;
+  }
+}
+
+/* Physical velocity gradient G[i][j] = du_i/dx_j of u = (rho u)/rho:
+ * du_i/dxi_q = (d(rho u_i)/dxi_q - u_i drho/dxi_q) / rho, and by the chain
+ * rule du_i/dx_j = sum_q du_i/dxi_q dxi_q/dx_j with dxi/dx = J^{-1}. */
+void or_velocity_gradient(const or_ctx* c, int e, const double xi[3], double G[9]) {
+  double U[5], dU[15], chi[3], J[9];
+  or_interp_grad(c, e, xi, U, dU);
+  or_elem_map(c, e, xi, chi, J);
+  double Dxi[9]; /* Dxi[i][q] = du_i/dxi_q */
+  for (int i = 0; i < 3; ++i) {
+    double ui = U[1 + i] / U[0];
+    for (int q = 0; q < 3; ++q) Dxi[3 * i + q] = (dU[3 * (1 + i) + q] - ui * dU[q]) / U[0];
+  }
+  /* row i of G solves G_i J = Dxi_i, i.e. J^T G_i^T = Dxi_i^T */
+  double JT[9];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) JT[3 * a + b] = J[3 * b + a];
+  for (int i = 0; i < 3; ++i) {
+    double row[3];
+    gauss_solve(3, JT, Dxi + 3 * i, row);
+    for (int j = 0; j < 3; ++j) G[3 * i + j] = row[j];
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* face representation: Bezier control points (Sec. 3.2.4)                   */
 /* ------------------------------------------------------------------------ */
@@ -725,13 +777,85 @@ void or_lserk_coeffs(double* A, double* B, double* C) {
 
 /* tau_p = d^2 rho_p / (18 mu) (Eq. stokesnumber); Re_p = rho |u - v| d / mu;
  * F_D = 3 pi mu d f_D (u - v) (Eq. dragforce) => dv/dt = f_D (u - v) / tau_p;
- * f_D = 1 (Stokes) or 1 + 0.15 Re_p^0.687 (Eq. dragfactor). */
+ * f_D = 1 (Stokes), 1 + 0.15 Re_p^0.687 (Schiller-Naumann, Eq. dragfactor) or
+ * the four-parameter correlation 1 + A Re^B + (Re/24) C / (1 + D/Re) of
+ * Haider & Levenspiel (1989, Powder Technol. 58), whose parameters are their
+ * published fits in the sphericity phi:
+ *   A = exp(2.3288 - 6.4581 phi + 2.4486 phi^2),  B = 0.0964 + 0.5565 phi,
+ *   C = exp(4.905 - 13.8944 phi + 18.4222 phi^2 - 10.2599 phi^3),
+ *   D = exp(1.4681 + 12.2584 phi - 20.7322 phi^2 + 15.8855 phi^3). */
+double or_drag_factor(const or_params* p, double re) {
+  if (p->drag_law == 0) return 1.0;
+  if (p->drag_law == 1) return 1.0 + 0.15 * pow(re, 0.687);
+  double f = p->sphericity;
+  double A = exp(2.3288 - 6.4581 * f + 2.4486 * f * f);
+  double B = 0.0964 + 0.5565 * f;
+  double C = exp(4.905 - 13.8944 * f + 18.4222 * f * f - 10.2599 * f * f * f);
+  double D = exp(1.4681 + 12.2584 * f - 20.7322 * f * f + 15.8855 * f * f * f);
+  if (!(re > 0.0)) return 1.0;
+  return 1.0 + A * pow(re, B) + re / 24.0 * C / (1.0 + D / re);
+}
+
 static double drag_factor(const or_params* p, double rho, const double rel[3], double d,
                           uint32_t* status) {
   if (p->drag_law == 0) return 1.0;
   double re = rho * sqrt(dot3(rel, rel)) * d / p->mu;
-  if (re >= 800.0 && status) *status |= OR_ST_REP800;
-  return 1.0 + 0.15 * pow(re, 0.687);
+  if (p->drag_law == 1 && re >= 800.0 && status) *status |= OR_ST_REP800;
+  return or_drag_factor(p, re);
+}
+
+/* Saffman lift (Sec. 2.2): F_S = 6.46/4 C_S d^2 sqrt(rho mu / |w|) (w x (v - u)),
+ * w = curl u (the relative velocity in the printed cross product is read as
+ * particle minus fluid: a particle lagging in a shear flow then drifts toward
+ * the faster fluid, as in Saffman 1965), with Mei's correction C_S = (1 - 0.3314 sqrt(th)) exp(-Re_p/10)
+ * + 0.3314 sqrt(th) for Re_p <= 40 and 0.0524 sqrt(th Re_p) above, where
+ * th = d |w| / (2 |u - v|) is held within [0.005, 0.4] (the range the paper
+ * states for it).  Zero when w or u - v vanishes. */
+void or_saffman_force(const or_params* p, double rho, const double rel[3],
+                      const double omega[3], double d, double F[3]) {
+  double wn = sqrt(dot3(omega, omega)), rn = sqrt(dot3(rel, rel));
+  F[0] = F[1] = F[2] = 0.0;
+  if (!(wn > 0.0) || !(rn > 0.0)) return;
+  double re = rho * rn * d / p->mu;
+  double th = d * wn / (2.0 * rn);
+  if (th < 0.005) th = 0.005;
+  if (th > 0.4) th = 0.4;
+  double cs = re <= 40.0 ? (1.0 - 0.3314 * sqrt(th)) * exp(-0.1 * re) + 0.3314 * sqrt(th)
+                         : 0.0524 * sqrt(th * re);
+  double k = 6.46 / 4.0 * cs * d * d * sqrt(rho * p->mu / wn);
+  double rxw[3]; /* w x (v - u) = (u - v) x w */
+  cross3(rel, omega, rxw);
+  for (int r = 0; r < 3; ++r) F[r] = k * rxw[r];
+}
+
+/* Acceleration of the particle: f_D (u - v) / tau_p (+ F_S / m_p) + g; F gets
+ * the fluid force on the particle, F_D (+ F_S). */
+static void particle_accel(const or_ctx* c, const or_params* p, int e, const double xi[3],
+                           const double vp[3], double d, uint32_t* status, double acc[3],
+                           double F[3]) {
+  const double pi = 3.14159265358979323846;
+  double U[5], rel[3];
+  or_interp(c, e, xi, U);
+  for (int r = 0; r < 3; ++r) rel[r] = U[1 + r] / U[0] - vp[r];
+  double tau = p->rho_p * d * d / (18.0 * p->mu);
+  double mp = p->rho_p * pi * d * d * d / 6.0;
+  double fD = drag_factor(p, U[0], rel, d, status);
+  for (int r = 0; r < 3; ++r) {
+    acc[r] = p->mask[r] * fD * rel[r] / tau + p->g[r];
+    F[r] = mp * fD * rel[r] / tau;
+  }
+  if (p->lift) {
+    double G[9], w[3], FS[3];
+    or_velocity_gradient(c, e, xi, G);
+    w[0] = G[7] - G[5]; /* du_z/dy - du_y/dz */
+    w[1] = G[2] - G[6]; /* du_x/dz - du_z/dx */
+    w[2] = G[3] - G[1]; /* du_y/dx - du_x/dy */
+    or_saffman_force(p, U[0], rel, w, d, FS);
+    for (int r = 0; r < 3; ++r) {
+      acc[r] += FS[r] / mp;
+      F[r] += FS[r];
+    }
+  }
 }
 
 void or_push(const or_ctx* c, const or_params* p, int64_t np, double* x, double* v,
@@ -742,11 +866,10 @@ void or_push(const or_ctx* c, const or_params* p, int64_t np, double* x, double*
   for (int64_t ip = 0; ip < np; ++ip) {
     double* xp = x + 3 * ip;
     double* vp = v + 3 * ip;
-    double tau = p->rho_p * d[ip] * d[ip] / (18.0 * p->mu);
     for (int step = 0; step < nsteps && !(status[ip] & OR_ST_FROZEN); ++step) {
       double kx[3] = {0, 0, 0}, kv[3] = {0, 0, 0};
       for (int st = 0; st < 5; ++st) {
-        double xi[3], U[5], u[3], rel[3], acc[3], xe[3];
+        double xi[3], acc[3], Ff[3], xe[3];
         int it;
         int e = elem[ip];
         if (!or_newton(c, p, e, xp, xi, &it)) {
@@ -759,13 +882,7 @@ void or_push(const or_ctx* c, const or_params* p, int64_t np, double* x, double*
           break;
         }
         if (m > 1.0 - p->band_ref) status[ip] |= OR_ST_NEAR_FACE;
-        or_interp(c, e, xi, U);
-        for (int r = 0; r < 3; ++r) {
-          u[r] = U[1 + r] / U[0];
-          rel[r] = u[r] - vp[r];
-        }
-        double fD = drag_factor(p, U[0], rel, d[ip], &status[ip]);
-        for (int r = 0; r < 3; ++r) acc[r] = p->mask[r] * fD * rel[r] / tau + p->g[r];
+        particle_accel(c, p, e, xi, vp, d[ip], &status[ip], acc, Ff);
         for (int r = 0; r < 3; ++r) {
           kx[r] = A[st] * kx[r] + dt * vp[r];
           kv[r] = A[st] * kv[r] + dt * acc[r];
@@ -783,7 +900,8 @@ void or_push(const or_ctx* c, const or_params* p, int64_t np, double* x, double*
 /* two-way coupling source (Sec. 2.3, Eq. theory:source), Lagrange weights    */
 /* ------------------------------------------------------------------------ */
 
-/* For every live particle: F = m_p f_D (u - v) / tau_p, m_p = rho_p pi d^3 / 6.
+/* For every live particle: F = m_p f_D (u - v) / tau_p, m_p = rho_p pi d^3 / 6
+ * (plus the Saffman lift when enabled).
  * Momentum source -F and energy source -F.v_p are spread over the nodes of the
  * owning element with weights l_i(xi1) l_j(xi2) l_k(xi3), so the nodal sums of
  * an element equal the particle's source (partition of unity).
@@ -791,23 +909,17 @@ void or_push(const or_ctx* c, const or_params* p, int64_t np, double* x, double*
 void or_deposit(const or_ctx* c, const or_params* p, int64_t np, const double* x,
                 const double* v, const double* d, const int32_t* elem, const uint32_t* status,
                 double* S) {
-  const double pi = 3.14159265358979323846;
   int n = c->n, n3 = n * n * n;
   for (int64_t ip = 0; ip < np; ++ip) {
     if (status[ip] & OR_ST_FROZEN) continue;
     int e = elem[ip], it;
-    double xi[3], U[5], rel[3], F[4];
+    double xi[3], acc[3], Fp[3], F[4];
     if (!or_newton(c, p, e, x + 3 * ip, xi, &it)) continue;
-    or_interp(c, e, xi, U);
-    for (int r = 0; r < 3; ++r) rel[r] = U[1 + r] / U[0] - v[3 * ip + r];
-    double tau = p->rho_p * d[ip] * d[ip] / (18.0 * p->mu);
-    double mp = p->rho_p * pi * d[ip] * d[ip] * d[ip] / 6.0;
-    double fD = drag_factor(p, U[0], rel, d[ip], NULL);
+    particle_accel(c, p, e, xi, v + 3 * ip, d[ip], NULL, acc, Fp);
     F[3] = 0.0;
     for (int r = 0; r < 3; ++r) {
-      double Fr = mp * fD * rel[r] / tau;
-      F[r] = -Fr;
-      F[3] -= Fr * v[3 * ip + r];
+      F[r] = -Fp[r];
+      F[3] -= Fp[r] * v[3 * ip + r];
     }
     double l[3][MAXN];
     for (int dd = 0; dd < 3; ++dd)
@@ -848,25 +960,19 @@ void or_quad_weights(int kind, int n, const double* x, double* w) {
 void or_deposit_nearest(const or_ctx* c, const or_params* p, int64_t np, const double* x,
                         const double* v, const double* d, const int32_t* elem,
                         const uint32_t* status, double* S) {
-  const double pi = 3.14159265358979323846;
   int n = c->n, n3 = n * n * n;
   double w[MAXN];
   or_quad_weights(c->node_type, n, c->nodes, w);
   for (int64_t ip = 0; ip < np; ++ip) {
     if (status[ip] & OR_ST_FROZEN) continue;
     int e = elem[ip], it;
-    double xi[3], U[5], rel[3], F[4];
+    double xi[3], acc[3], Fp[3], F[4];
     if (!or_newton(c, p, e, x + 3 * ip, xi, &it)) continue;
-    or_interp(c, e, xi, U);
-    for (int r = 0; r < 3; ++r) rel[r] = U[1 + r] / U[0] - v[3 * ip + r];
-    double tau = p->rho_p * d[ip] * d[ip] / (18.0 * p->mu);
-    double mp = p->rho_p * pi * d[ip] * d[ip] * d[ip] / 6.0;
-    double fD = drag_factor(p, U[0], rel, d[ip], NULL);
+    particle_accel(c, p, e, xi, v + 3 * ip, d[ip], NULL, acc, Fp);
     F[3] = 0.0;
     for (int r = 0; r < 3; ++r) {
-      double Fr = mp * fD * rel[r] / tau;
-      F[r] = -Fr;
-      F[3] -= Fr * v[3 * ip + r];
+      F[r] = -Fp[r];
+      F[3] -= Fp[r] * v[3 * ip + r];
     }
     int idx[3];
     for (int dd = 0; dd < 3; ++dd) {

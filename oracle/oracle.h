@@ -43,7 +43,7 @@ enum {
 typedef struct {
   double mu;          /* dynamic viscosity                                  */
   double rho_p;       /* particle material density                          */
-  int    drag_law;    /* 0 = Stokes (f_D = 1), 1 = Schiller-Naumann         */
+  int    drag_law;    /* 0 Stokes (f_D = 1), 1 Schiller-Naumann, 2 Haider-Levenspiel */
   int    max_newton;  /* Newton iteration cap                               */
   double g[3];        /* gravitational acceleration                         */
   double mask[3];     /* per-axis multiplier on the drag term (1,1,1)       */
@@ -53,6 +53,9 @@ typedef struct {
   double band_ref;    /* near-face band in reference units                  */
   double band_x;      /* near-face band in physical length                  */
   double lost_tol;    /* xi outside [-1-lost_tol, 1+lost_tol] => lost       */
+  int    lift;        /* 1: Saffman lift with Mei's correction (Sec. 2.2)   */
+  int    pad2;
+  double sphericity;  /* drag_law 2 (Haider-Levenspiel): particle sphericity */
 } or_params;
 
 typedef struct or_ctx or_ctx;
@@ -75,6 +78,11 @@ void    or_elem_map(const or_ctx* c, int e, const double xi[3], double x[3], dou
 int     or_newton(const or_ctx* c, const or_params* p, int e, const double x[3],
                   double xi[3], int* iters);
 void    or_interp(const or_ctx* c, int e, const double xi[3], double U[5]);
+void    or_interp_grad(const or_ctx* c, int e, const double xi[3], double U[5], double dU[15]);
+void    or_velocity_gradient(const or_ctx* c, int e, const double xi[3], double G[9]);
+double  or_drag_factor(const or_params* p, double re);
+void    or_saffman_force(const or_params* p, double rho, const double rel[3],
+                         const double omega[3], double d, double F[3]);
 int     or_face_hits(const or_ctx* c, int e, int f, const double x0[3], const double x1[3],
                      double band, double* out, int maxout);
 void    or_face_ctrl(const or_ctx* c, int e, int f, double* out);

@@ -214,6 +214,17 @@ def fluid_linear_shear(mesh: Mesh, N: int, y0: float, node_type: int = 0, device
     return _conservative(one, Y / y0, zero, zero, one)
 
 
+def fluid_linear(mesh: Mesh, N: int, A, u0, rho_slope, node_type: int = 0, device="cpu"):
+    """rho = 1.2 + rho_slope . x, u = u0 + A x, p = 1 at the DG nodes: a flow
+    with a constant velocity gradient A (vorticity and shear for the lift)."""
+    X, Y, Z = node_positions(mesh, N, node_type, device)
+    A = torch.as_tensor(np.asarray(A), dtype=torch.float64, device=device)
+    u0 = [float(c) for c in u0]
+    rho = 1.2 + rho_slope[0] * X + rho_slope[1] * Y + rho_slope[2] * Z
+    u = [u0[i] + A[i, 0] * X + A[i, 1] * Y + A[i, 2] * Z for i in range(3)]
+    return _conservative(rho, u[0], u[1], u[2], torch.ones_like(X))
+
+
 def fluid_polynomial(mesh: Mesh, N: int, coeffs: np.ndarray, node_type: int = 0, device="cpu"):
     """U_v(x) = sum_{abc} coeffs[v,a,b,c] X^a Y^b Z^c with X,Y,Z the physical
     node coordinates (straight meshes: degree <= N per axis in xi too)."""

@@ -662,3 +662,109 @@ def test_dt_violations_threshold():
     assert oracle.dt_violations(p, d, dt * (1 - 1e-12)) == 1  # only the 5e-5 particle
     assert oracle.dt_violations(p, d, dt * (1 + 1e-12)) == 2
     assert oracle.dt_violations(p, d, 0.0) == 0
+
+
+# ---------------------------------------------------------------------------
+# extra force models (Sec. 2.2): velocity gradient, Saffman lift, Haider-Levenspiel
+# ---------------------------------------------------------------------------
+
+def test_velocity_gradient_exact_for_linear_velocity_on_curved_mesh():
+    """u = u0 + A x with a linearly varying density on a mesh warped by a
+    polynomial of degree 2 per axis (NGeo = 2 reproduces it): rho u has degree
+    <= 4 per reference direction <= N, so the interpolant is exact and du/dx = A
+    (the quotient-rule term u_i drho/dxi is needed for that)."""
+    mesh = W.box_mesh((3, 3, 2), (0, 0, 0), (1, 1, 1), 2, periodic=(False, False, False),
+                      warp="poly", amp=0.1)
+    N = 5
+    rng = np.random.default_rng(8)
+    A = rng.normal(size=(3, 3))
+    U = W.fluid_linear(mesh, N, A, (0.3, -0.2, 0.1), (0.05, -0.03, 0.02))
+    orc = oracle.Oracle(mesh.as_dict())
+    orc.set_fluid(N, 0, _np(U))
+    for e in rng.choice(mesh.nelem, 6, replace=False):
+        xi = rng.uniform(-1, 1, 3)
+        G = orc.velocity_gradient(int(e), xi)
+        assert np.allclose(G, A, atol=1e-10), (G, A)
+
+
+def test_saffman_lift_direction_and_low_reynolds_limit():
+    """Shear u = (g y, 0, 0), particle at rest above the axis: the lift points to
+    the faster fluid (+y); for Re_p -> 0, C_S -> 1 and the force is Saffman's
+    6.46 mu a^2 |u - v| sqrt(|w| / nu), a = d/2."""
+    mu, rho, g, d = 1e-5, 1.0, 3.0, 1e-6
+    p = oracle.make_params(mu=mu, lift=1)
+    rel = np.array([g * 3e-4, 0.0, 0.0])         # u - v at y = 3e-4
+    w = np.array([0.0, 0.0, -g])                  # curl of (g y, 0, 0)
+    F = oracle.saffman_force(p, rho, rel, w, d)
+    assert F[1] > 0 and abs(F[0]) < 1e-30 and abs(F[2]) < 1e-30
+    a, nu = d / 2, mu / rho
+    classic = 6.46 * mu * a ** 2 * np.linalg.norm(rel) * np.sqrt(abs(g) / nu)
+    re = rho * np.linalg.norm(rel) * d / mu
+    assert re < 1e-3
+    assert abs(F[1] - classic) <= 1e-3 * classic
+    # no shear or no slip: no lift
+    assert np.all(oracle.saffman_force(p, rho, rel, np.zeros(3), d) == 0)
+    assert np.all(oracle.saffman_force(p, rho, np.zeros(3), w, d) == 0)
+
+
+def test_saffman_mei_branches_meet_at_re_40():
+    """0.0524 sqrt(40) = 0.3314: above Re_p = 40 the correction is
+    0.3314 sqrt(th) at the branch point (th = d |w| / (2 |u - v|))."""
+    mu, rho = 1e-5, 1.0
+    p = oracle.make_params(mu=mu, lift=1)
+    d = 1e-3
+    rn = 40.0001 * mu / (rho * d)
+    rel = np.array([0.0, rn, 0.0])
+    w = np.array([0.0, 0.0, 2 * rn * 0.1 / d])   # th = 0.1
+    F = np.linalg.norm(oracle.saffman_force(p, rho, rel, w, d))
+    k = 6.46 / 4 * d * d * np.sqrt(rho * mu / np.linalg.norm(w)) * np.linalg.norm(w) * rn
+    assert abs(F / k - 0.3314 * np.sqrt(0.1)) < 2e-4
+
+
+def test_haider_levenspiel_sphere_limits():
+    """phi = 1: Stokes limit f_D -> 1, within 10% of Schiller-Naumann (an
+    independent sphere correlation) over 0.1 <= Re <= 800, and the Newton
+    regime C_D = 24 f_D / Re ~ 0.44 at Re = 1e4."""
+    hl = oracle.make_params(drag_law=2, sphericity=1.0)
+    sn = oracle.make_params(drag_law=1)
+    assert abs(oracle.drag_factor(hl, 1e-8) - 1.0) < 1e-4
+    for re in np.geomspace(0.1, 800, 25):
+        a, b = oracle.drag_factor(hl, re), oracle.drag_factor(sn, re)
+        assert abs(a / b - 1) < 0.10, (re, a, b)
+    cd = 24 * oracle.drag_factor(hl, 1e4) / 1e4
+    assert 0.40 < cd < 0.48
+    # less spherical particles drag more at the same Re
+    lo = oracle.make_params(drag_law=2, sphericity=0.6)
+    assert oracle.drag_factor(lo, 100.0) > oracle.drag_factor(hl, 100.0)
+
+
+def test_push_with_lift_drifts_toward_faster_fluid_and_deposits_it():
+    """Shear u = (g (y - 0.5), 0, 0) in a periodic box, particle released at
+    rest at y > 0.5 (it lags the fluid): without lift its y stays fixed; with
+    lift it drifts to larger y, toward the faster fluid.  The y-momentum source
+    of the deposit is then minus the lift force."""
+    mesh = W.box_mesh((4, 4, 4), (0, 0, 0), (1, 1, 1), 1)
+    N = 3
+    g = 2.0
+    A = np.zeros((3, 3))
+    A[0, 1] = g
+    U = W.fluid_linear(mesh, N, A, (-0.5 * g, 0.0, 0.0), (0.0, 0.0, 0.0))
+    orc = oracle.Oracle(mesh.as_dict())
+    orc.set_fluid(N, 0, _np(U))
+    x = np.array([[0.4, 0.8, 0.5]])
+    el = np.array([int(0.4 * 4) + 4 * (int(0.8 * 4) + 4 * int(0.5 * 4))], np.int32)
+    v = np.zeros((1, 3))
+    d = np.array([2e-4])
+    common = dict(mu=1e-5, rho_p=1000.0, drag_law=1)
+    r0 = orc.push(oracle.make_params(**common), x, v, d, el, nsteps=20, dt=1e-3)
+    r1 = orc.push(oracle.make_params(lift=1, **common), x, v, d, el, nsteps=20, dt=1e-3)
+    assert r0["x"][0, 1] == x[0, 1]
+    assert r1["x"][0, 1] > x[0, 1] and r1["v"][0, 1] > 0
+    # deposit: with lift the y source is -F_S,y (drag has no y component here)
+    S0 = orc.deposit(oracle.make_params(**common), x, v, d, el)
+    S1 = orc.deposit(oracle.make_params(lift=1, **common), x, v, d, el)
+    assert abs(S0[:, 1].sum()) < 1e-30
+    rel = np.array([g * (0.8 - 0.5), 0.0, 0.0])
+    FS = oracle.saffman_force(oracle.make_params(lift=1, **common), 1.2, rel,
+                              np.array([0.0, 0.0, -g]), d[0])
+    assert abs(S1[:, 1].sum() + FS[1]) <= 1e-9 * abs(FS[1])
