@@ -42,8 +42,8 @@ def parse():
     ap.add_argument("--dims", type=int, default=64)
     ap.add_argument("--guess", default="auto", choices=["auto", "trilinear", "mlp"])
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / fp64 / cpu legs")
-    ap.add_argument("--extras", default="trilinear,e2e,fp64,cpu",
-                    help="comma list of extra legs to run (trilinear, e2e, fp64, cpu)")
+    ap.add_argument("--extras", default="trilinear,reference,e2e,fp64,cpu",
+                    help="comma list of extra legs to run (trilinear, reference, e2e, fp64, cpu)")
     return ap.parse_args()
 
 
@@ -119,6 +119,14 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def inputs_vs_l2(P, wl):
+    """The particle record and the fluid field against the 129 MB L2."""
+    part_b = P * (3 * 8 + 3 * 4 + 4 + 3 * 4)
+    field_b = wl.mesh.nelem * 5 * (wl.N + 1) ** 3 * 4
+    rel = "larger" if part_b + field_b > 129e6 else "SMALLER"
+    return f"inputs {rel} than L2 (particles {part_b / 1e9:.2f} GB, field {field_b / 1e9:.2f} GB)"
 
 
 def make_workload(args, device, seed, precision):
@@ -312,6 +320,15 @@ def main():
                 "kernel_share_of_step": (kern_ms / ms) if ms > 0 else None,
                 "hbm_frac_of_measured": (TRAFFIC_BYTES_PER_PARTICLE_STEP * P * args.inner
                                          / avg_launch_s / 1e9) / float(peaks.get("hbm_gbs", 6800.0))}
+    if guess:
+        # the learned start's own products run on the tensor cores (BF16, FP32
+        # accumulate): 3x64 + 2 x 64x64 + 64x3 multiply-adds per particle-stage
+        mlp_flops = 2 * (3 * 64 + 2 * 64 * 64 + 64 * 3)
+        t_ach = mlp_flops * 5 * args.inner * P / avg_launch_s / 1e12
+        roofline["mlp_tensor"] = {"flops_per_particle_stage": mlp_flops, "achieved": t_ach,
+                                  "peak": float(peaks.get("bf16_tflops", 1900.0)),
+                                  "unit": "TFLOP/s",
+                                  "frac": t_ach / float(peaks.get("bf16_tflops", 1900.0))}
 
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -320,7 +337,7 @@ def main():
             "config": {"workload": f"curved channel {args.dims}^3 NGeo=3 N=5 Gauss, "
                        f"{P} particles/GPU, Schiller-Naumann, dt=1e-3, FP32 + FP64 final Newton",
                        "inner_steps_per_call": args.inner, "guess": "mlp" if guess else "trilinear",
-                       "inputs_vs_l2": "inputs larger than L2 (particles 0.5 GB, field 1.1 GB)",
+                       "inputs_vs_l2": inputs_vs_l2(P, wl),
                        "parallelism": f"weak, {world} independent GPU(s)"},
             "gpu_launches": None, "clocks": clk.summary(), "roofline": roofline,
             "stats_one_step": {k: stats[k] for k in ("particle_steps", "crossings", "wall_hits",
@@ -352,6 +369,30 @@ def main():
                                       "note": "same FP32 push, trilinear Newton start"}
             ctx.set_config(guess=guess)
             del ptri
+        if "reference" in legs:
+            # reference-space localisation (Sec. 3.2.3): only walls intersected;
+            # same start guess as the headline; owners compared with the
+            # physical tracking of the same particles after the same steps
+            pref = pt.ParticleSet.create(wl.x, wl.v, wl.d, wl.elem, pt.FP32, dev)
+            pphy = pt.ParticleSet.create(wl.x, wl.v, wl.d, wl.elem, pt.FP32, dev)
+            ctx.push(pphy, args.inner, wl.dt, stats=False)
+            ctx.set_config(track=pt.TRACK_REFERENCE)
+            ctx.push(pref, args.inner, wl.dt, stats=False)
+            torch.cuda.synchronize()
+            same = float((pref.elem == pphy.elem).float().mean())
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                ctx.push(pref, args.inner, wl.dt, stats=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            line["fp32_reference_tracking"] = {
+                "value": P * args.inner * 3 / (e0.elapsed_time(e1) / 1e3), "unit": METRIC,
+                "same_owner_as_physical": same,
+                "note": "same FP32 push, owners found by inverse map + face walk (walls traced)"}
+            ctx.set_config(track=pt.TRACK_PHYSICAL)
+            del pref, pphy
     if not args.no_extras and rank == 0 and "e2e" in legs:
         # e2e: same metric through pt_push_host with pinned host buffers
         hp = parts.to("cpu", pin=True)

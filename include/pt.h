@@ -55,8 +55,20 @@ enum {
 enum { PT_BC_INTERNAL = 0, PT_BC_WALL = 1, PT_BC_PERIODIC = 2, PT_BC_OPEN = 3 };
 
 typedef enum { PT_FP64 = 0, PT_FP32 = 1 } pt_precision;
-typedef enum { PT_DRAG_STOKES = 0, PT_DRAG_SCHILLER_NAUMANN = 1 } pt_drag_law;
+typedef enum {
+  PT_DRAG_STOKES = 0,            /* f_D = 1                                  */
+  PT_DRAG_SCHILLER_NAUMANN = 1,  /* f_D = 1 + 0.15 Re^0.687 (Sec. 2.2)       */
+  PT_DRAG_HAIDER_LEVENSPIEL = 2  /* four-parameter law in the sphericity     */
+} pt_drag_law;
 typedef enum { PT_GUESS_TRILINEAR = 0, PT_GUESS_MLP = 1 } pt_guess;
+/* How a stage segment finds its new element (Sec. 3.2.3).  PHYSICAL: every
+ * face the segment may cross is intersected (Eq. parttrajectory).  REFERENCE:
+ * only wall and open faces are intersected; otherwise the end point is
+ * located by the inverse map in the current element and, when it lies
+ * outside, by walking across the face of the largest |xi_d| (translated on a
+ * periodic face) and mapping again (the paper's "localisation in reference
+ * space" with face neighbours instead of a background mesh). */
+typedef enum { PT_TRACK_PHYSICAL = 0, PT_TRACK_REFERENCE = 1 } pt_track;
 typedef enum {
   PT_DEPOSIT_ATOMIC = 0,     /* FP32 atomics                                   */
   PT_DEPOSIT_SEGMENTED = 1,  /* element-sorted, fixed summation order          */
@@ -102,7 +114,14 @@ typedef struct {
   int32_t max_cross;    /* face-crossing cap per RK stage (default 64)             */
   int32_t rebin_every;  /* steps between particle re-binning; 0 = library choice   */
   int32_t block;        /* threads per block of the push kernel (32..128); 0 = 128 */
-  int32_t reserved[9];
+  int32_t lift;         /* 1: add the Saffman lift with Mei's correction (Sec. 2.2),
+                           F_S = 6.46/4 C_S d^2 sqrt(rho mu/|w|) (u - v) x w, w = curl u;
+                           also deposited by pt_deposit (default 0)                */
+  double sphericity;    /* PT_DRAG_HAIDER_LEVENSPIEL: particle sphericity in (0, 1]
+                           (default 1): f_D = 1 + A Re^B + (Re/24) C / (1 + D/Re)
+                           with A..D the Haider & Levenspiel (1989) fits          */
+  int32_t track;        /* pt_track (default PT_TRACK_PHYSICAL)                    */
+  int32_t reserved[5];
 } pt_config;
 
 /* Particles, structure of arrays, all device memory, caller-owned, updated in

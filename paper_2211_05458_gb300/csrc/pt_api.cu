@@ -448,6 +448,8 @@ static pt_status upload_mesh(pt_ctx* c, const pt_mesh_desc* md) {
       S[4] = (float)(hi + margin);
       S[5] = (float)Rmax;
       S[6] = (float)(devmax * (1.0 + 1e-6) + 1e-12 * Rmax);
+      // faces that reference-space localisation must still track physically
+      S[7] = (bc == PT_BC_WALL || bc == PT_BC_OPEN) ? 1.f : 0.f;
     }
   }
   c->ncurved = ncurved;
@@ -539,6 +541,16 @@ static void fill_consts(const pt_ctx* c, DevConsts& k) {
   k.band_x = c->cfg.band_x;
   k.lost_tol = c->cfg.lost_tol;
   k.drag_law = c->cfg.drag_law;
+  k.lift = c->cfg.lift;
+  k.track = c->cfg.track;
+  {
+    // Haider & Levenspiel (1989) fits in the sphericity
+    const double f = c->cfg.sphericity;
+    k.hl[0] = std::exp(2.3288 - 6.4581 * f + 2.4486 * f * f);
+    k.hl[1] = 0.0964 + 0.5565 * f;
+    k.hl[2] = std::exp(4.905 - 13.8944 * f + 18.4222 * f * f - 10.2599 * f * f * f);
+    k.hl[3] = std::exp(1.4681 + 12.2584 * f - 20.7322 * f * f + 15.8855 * f * f * f);
+  }
   k.max_newton = c->cfg.max_newton;
   k.max_cross = c->cfg.max_cross;
   k.guess = c->cfg.guess;
@@ -572,7 +584,13 @@ static pt_status check_config(const pt_config* cfg) {
   if (!cfg) return fail(nullptr, PT_ERR_ARG, "config is NULL");
   if (cfg->precision != PT_FP64 && cfg->precision != PT_FP32)
     return fail(nullptr, PT_ERR_ARG, "precision must be PT_FP64 or PT_FP32");
-  if (cfg->drag_law != 0 && cfg->drag_law != 1) return fail(nullptr, PT_ERR_ARG, "bad drag_law");
+  if (cfg->drag_law < 0 || cfg->drag_law > 2) return fail(nullptr, PT_ERR_ARG, "bad drag_law");
+  if (cfg->drag_law == PT_DRAG_HAIDER_LEVENSPIEL &&
+      !(cfg->sphericity > 0.0 && cfg->sphericity <= 1.0))
+    return fail(nullptr, PT_ERR_ARG, "sphericity must be in (0, 1]");
+  if (cfg->lift != 0 && cfg->lift != 1) return fail(nullptr, PT_ERR_ARG, "lift must be 0 or 1");
+  if (cfg->track != PT_TRACK_PHYSICAL && cfg->track != PT_TRACK_REFERENCE)
+    return fail(nullptr, PT_ERR_ARG, "track must be PT_TRACK_PHYSICAL or PT_TRACK_REFERENCE");
   if (cfg->guess != 0 && cfg->guess != 1) return fail(nullptr, PT_ERR_ARG, "bad guess");
   if (!(cfg->mu > 0) || !(cfg->rho_p > 0)) return fail(nullptr, PT_ERR_ARG, "mu, rho_p must be > 0");
   if (cfg->max_newton < 1 || cfg->max_cross < 1) return fail(nullptr, PT_ERR_ARG, "caps must be >= 1");
@@ -603,6 +621,8 @@ void pt_config_default(pt_config* cfg) {
   cfg->max_cross = 64;
   cfg->rebin_every = 0;
   cfg->block = 0;
+  cfg->lift = 0;
+  cfg->sphericity = 1.0;
 }
 
 pt_status pt_init_mesh(pt_ctx** out, const pt_mesh_desc* md, const pt_config* cfg, void* stream) {

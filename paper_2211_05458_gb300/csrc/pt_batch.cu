@@ -147,12 +147,18 @@ struct pt_batch_plan {
   int block = 0;
   std::vector<int> tried;
   std::vector<float> tried_ms;
+  int occ[3] = {0, 0, 0};  // resident blocks per SM of k_push_batch per candidate block size
+  // private stream the graph is captured on (the caller's stream may be the
+  // legacy default stream, which cannot be captured); the graph runs on the
+  // caller's stream
+  cudaStream_t cap = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_nsteps = -1;
   double graph_dt = 0.0;
   int graph_block = 0;
   ~pt_batch_plan() {
     if (graph) cudaGraphExecDestroy(graph);
+    if (cap) cudaStreamDestroy(cap);
     cudaFree(d_boxes);
     cudaFree(d_poffs);
     cudaFree(d_scratch);
@@ -177,10 +183,13 @@ static void enqueue_chunk(pt_batch_plan* P, const BatchArgs& a, int block, cudaS
   k_hist_batch<<<std::max(g, 1), 256, 0, s>>>(a, L.counts);
   bin_scan(L, s);
   k_scatter_batch<<<std::max(g, 1), 256, 0, s>>>(a, L.cursor, P->d_perm);
-  int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_push_batch<2>, block, 0);
+  // occupancy was queried when the plan was made: no API call but stream work
+  // may run here while the stream is being captured
+  int occ = 1;
+  for (int i = 0; i < 3; ++i)
+    if (kBlocks[i] == block) occ = std::max(P->occ[i], 1);
   const int64_t want = (P->ptot + block - 1) / block;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)P->nsm * std::max(occ, 1)));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)P->nsm * occ));
   k_push_batch<2><<<grid, block, 0, s>>>(a);
 }
 
@@ -267,6 +276,12 @@ extern "C" pt_status pt_push_batch(pt_ctx* const* ctxs, const pt_particles* part
     }
     cudaMemcpy(P->d_boxes, hb.data(), sizeof(DevBox) * nbox, cudaMemcpyHostToDevice);
     cudaMemcpy(P->d_poffs, poffs.data(), sizeof(int64_t) * (nbox + 1), cudaMemcpyHostToDevice);
+    for (int i = 0; i < 3; ++i)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P->occ[i], k_push_batch<2>, kBlocks[i], 0);
+    if (cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking) != cudaSuccess) {
+      c0->err = "pt_push_batch: stream creation failed";
+      return PT_ERR_CUDA;
+    }
   }
   BatchArgs a;
   a.boxes = P->d_boxes;
@@ -313,18 +328,20 @@ extern "C" pt_status pt_push_batch(pt_ctx* const* ctxs, const pt_particles* part
         if (P->graph) cudaGraphExecDestroy(P->graph);
         P->graph = nullptr;
         cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        // capturing only records the work: nothing runs on P->cap
+        cudaError_t e = cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-          cudaMemsetAsync(P->d_stats, 0, sizeof(unsigned long long) * PT_C_COUNT * nbox, s);
+          cudaMemsetAsync(P->d_stats, 0, sizeof(unsigned long long) * PT_C_COUNT * nbox, P->cap);
           for (int s0 = 0; s0 < nsteps; s0 += kChunk) {
             a.nsteps = std::min(kChunk, nsteps - s0);
-            enqueue_chunk(P, a, P->block, s);
+            enqueue_chunk(P, a, P->block, P->cap);
           }
-          e = cudaStreamEndCapture(s, &g);
+          e = cudaStreamEndCapture(P->cap, &g);
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&P->graph, g, 0);
         if (g) cudaGraphDestroy(g);
         if (e != cudaSuccess) {
+          (void)cudaGetLastError();  // do not leave the failure to later calls
           c0->err = std::string("pt_push_batch: graph capture failed: ") + cudaGetErrorString(e);
           return PT_ERR_CUDA;
         }

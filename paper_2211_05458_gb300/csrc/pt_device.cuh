@@ -540,12 +540,19 @@ __device__ __forceinline__ void interp4(const T* __restrict__ Ue, const T* l1, c
   }
 }
 
-// drag factor f_D: 1 (Stokes) or 1 + 0.15 Re_p^0.687 (Schiller-Naumann)
+// power in the working precision
+__device__ __forceinline__ float tpow(float a, float b) { return powf(a, b); }
+__device__ __forceinline__ double tpow(double a, double b) { return pow(a, b); }
+
+// drag factor f_D (Sec. 2.2): 1 (Stokes), 1 + 0.15 Re_p^0.687 (Schiller-
+// Naumann) or 1 + A Re^B + (Re/24) C / (1 + D/Re) (Haider-Levenspiel, A..D in
+// k.hl); called for laws 1 and 2
 template <typename T>
-__device__ __forceinline__ T drag_factor(int law, T re) {
-  if (law == 0) return T(1);
-  if (std::is_same<T, float>::value) return T(1) + T(0.15) * (T)powf((float)re, 0.687f);
-  return T(1) + T(0.15) * (T)pow((double)re, 0.687);
+__device__ __forceinline__ T drag_factor(const DevConsts& k, T re) {
+  if (k.drag_law == 1) return T(1) + T(0.15) * tpow(re, T(0.687));
+  if (!(re > T(0))) return T(1);
+  return T(1) + (T)k.hl[0] * tpow(re, (T)k.hl[1]) +
+         re / T(24) * (T)k.hl[2] / (T(1) + (T)k.hl[3] / re);
 }
 
 // ---------------------------------------------------------------------------
@@ -780,13 +787,112 @@ __device__ __forceinline__ bool curved_newton_f32(const float* __restrict__ X32,
   return false;
 }
 
-// Newton on F(s,t,alpha) = p(s,t) - xs - alpha td for a curved face, started
-// from a bilinear root; returns true on convergence.
+// curved face point p(s,t) alone (FP64), sum-factorised
 template <int G>
-__device__ __forceinline__ bool curved_refine(const double* X64, int f, const double* xs,
-                                              const double* td, const DevConsts& k, double& s,
-                                              double& t, double& al, double L) {
-  #pragma unroll 1
+__device__ __forceinline__ void face_point(const double* X64, int f, double s, double t,
+                                           const DevConsts& k, double* p) {
+  double ls[G], lt[G];
+  lagr<G, double>(s, k.gn, k.gw, ls);
+  lagr<G, double>(t, k.gn, k.gw, lt);
+  int base, sm, sk;
+  face_strides<G>(f, base, sm, sk);
+  p[0] = p[1] = p[2] = 0.0;
+#pragma unroll
+  for (int kk = 0; kk < G; ++kk) {
+    double q[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int mm = 0; mm < G; ++mm) {
+      const double* P = X64 + 3 * (base + mm * sm + kk * sk);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) q[r] = fma(__ldg(P + r), ls[mm], q[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) p[r] = fma(q[r], lt[kk], p[r]);
+  }
+}
+
+// Newton on F(s,t,alpha) = p(s,t) - xs - alpha td for a curved face, started
+// from a bilinear root: FP32 iterations on the FP32 nodes until the step is
+// below 1e-5, then FP64 residuals with the last FP32 inverse Jacobian (each
+// such step gains about six digits) until the step is below 1e-14; a full
+// FP64 Newton if either stage does not settle.  Returns true on convergence.
+template <int G>
+__device__ __forceinline__ bool curved_refine(const double* X64, const float* __restrict__ X32,
+                                              int f, const double* xs, const double* td,
+                                              const DevConsts& k, double& s, double& t,
+                                              double& al, double L) {
+  constexpr int G3 = G * G * G;
+  {
+    float sf = (float)s, tf = (float)t, af = (float)al;
+    const float xsf[3] = {(float)xs[0], (float)xs[1], (float)xs[2]};
+    const float tdf[3] = {(float)td[0], (float)td[1], (float)td[2]};
+    const float atol = 1e-5f * ((float)L + 1.f);
+    int base, sm, sk;
+    face_strides<G>(f, base, sm, sk);
+    float Ji[9];
+    bool ok32 = false;
+#pragma unroll 1
+    for (int it = 0; it < 12; ++it) {
+      float ls[G], ds[G], lt[G], dt[G];
+      lagr_d<G, float>(sf, k.gn32, k.gw32, ls, ds);
+      lagr_d<G, float>(tf, k.gn32, k.gw32, lt, dt);
+      float p[3] = {0, 0, 0}, ps[3] = {0, 0, 0}, pt[3] = {0, 0, 0};
+#pragma unroll
+      for (int kk = 0; kk < G; ++kk)
+#pragma unroll
+        for (int mm = 0; mm < G; ++mm) {
+          const int q = base + mm * sm + kk * sk;
+          const float w = ls[mm] * lt[kk], wsv = ds[mm] * lt[kk], wtv = ls[mm] * dt[kk];
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            const float xv = __ldg(X32 + r * G3 + q);
+            p[r] = fmaf(xv, w, p[r]);
+            ps[r] = fmaf(xv, wsv, ps[r]);
+            pt[r] = fmaf(xv, wtv, pt[r]);
+          }
+        }
+      float F[3], J[9], dl[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        F[r] = p[r] - xsf[r] - af * tdf[r];
+        J[3 * r] = ps[r];
+        J[3 * r + 1] = pt[r];
+        J[3 * r + 2] = -tdf[r];
+      }
+      if (!inv3(J, Ji)) break;
+      matvec3(Ji, F, dl);
+      sf -= dl[0];
+      tf -= dl[1];
+      af -= dl[2];
+      if (fabsf(dl[0]) < 1e-5f && fabsf(dl[1]) < 1e-5f && fabsf(dl[2]) < atol) {
+        ok32 = true;
+        break;
+      }
+      if (!(fabsf(sf) < 3.f && fabsf(tf) < 3.f)) break;
+    }
+    if (ok32) {
+      double sd = sf, tq = tf, ad = af;
+#pragma unroll 1
+      for (int it = 0; it < 4; ++it) {
+        double p[3];
+        face_point<G>(X64, f, sd, tq, k, p);
+        float Fr[3], dl[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) Fr[r] = (float)(p[r] - xs[r] - ad * td[r]);
+        matvec3(Ji, Fr, dl);
+        sd -= dl[0];
+        tq -= dl[1];
+        ad -= dl[2];
+        if (fabs(dl[0]) < 1e-14 && fabs(dl[1]) < 1e-14 && fabs(dl[2]) < 1e-14 * (L + 1.0)) {
+          s = sd;
+          t = tq;
+          al = ad;
+          return true;
+        }
+      }
+    }
+  }
+#pragma unroll 1
   for (int it = 0; it < 20; ++it) {
     double p[3], ps[3], pt[3], F[3], J[9], Ji[9], dl[3];
     face_eval<G>(X64, f, s, t, k, p, ps, pt);
@@ -840,6 +946,24 @@ __device__ __forceinline__ bool touches_any_slab(const DevMesh& m, int e, const 
   return hit;
 }
 
+// As touches_any_slab, with the kind of face: bit 0 some face (or a long
+// segment), bit 1 a wall or open face (or a long segment).  Slab word 7 flags
+// the wall and open faces.
+__device__ __forceinline__ int slab_touch(const DevMesh& m, int e, const float* a,
+                                          const float* b) {
+  const float4* S = reinterpret_cast<const float4*>(m.slab + 48 * (size_t)e);
+  const float rlim = 8.f * __ldg(m.slab + 48 * (size_t)e + 5);
+  int t = (fmaxf(fmaxf(fabsf(b[0]), fabsf(b[1])), fabsf(b[2])) <= rlim) ? 0 : 3;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    float4 s0 = __ldg(S + 2 * f), s1 = __ldg(S + 2 * f + 1);
+    float pa = s0.x * a[0] + s0.y * a[1] + s0.z * a[2];
+    float pb = s0.x * b[0] + s0.y * b[1] + s0.z * b[2];
+    if ((fmaxf(pa, pb) >= s0.w) && (fminf(pa, pb) <= s1.x)) t |= s1.w != 0.f ? 3 : 1;
+  }
+  return t;
+}
+
 // Tracks the stage segment x -> xe through the mesh.  The ray
 // x(alpha) = xs + alpha td, alpha in (a0, L] (Eq. parttrajectory) is tested
 // against every face of the current element except the entry face; the
@@ -878,8 +1002,11 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
     for (int r = 0; r < 3; ++r) x[r] = xe[r];
     return;
   }
+  {
+    const double iL = 1.0 / L;
 #pragma unroll
-  for (int r = 0; r < 3; ++r) td[r] /= L;
+    for (int r = 0; r < 3; ++r) td[r] *= iL;
+  }
   float tdf[3] = {(float)td[0], (float)td[1], (float)td[2]};
   float Lf = (float)L;
   float n1f[3], n2f[3];
@@ -891,9 +1018,9 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
     if (fabs(td[2]) < fabs(td[im])) im = 2;
     ax[im] = 1.0;
     cross3d(td, ax, n1);
-    double nn = sqrt(dot3d(n1, n1));
+    const double inn = 1.0 / sqrt(dot3d(n1, n1));
 #pragma unroll
-    for (int r = 0; r < 3; ++r) n1[r] /= nn;
+    for (int r = 0; r < 3; ++r) n1[r] *= inn;
     cross3d(td, n1, n2);
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
@@ -966,7 +1093,8 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
           double s = rs[i], t = rt[i], al = ra[i];
           if (!(fabs(s) < 2.0 && fabs(t) < 2.0)) continue;
           if (al > L + reach || al < a0 - reach) continue;
-          if (curved_refine<G>(X64, f, xl, td, k, s, t, al, L)) {
+          if (curved_refine<G>(X64, m.xg32 + (size_t)e * 3 * G * G * G, f, xl, td, k, s, t,
+                               al, L)) {
             bool dup = false;
             for (int j = 0; j < kk; ++j)
               if (fabs(rs[j] - s) < 1e-10 && fabs(rt[j] - t) < 1e-10) dup = true;
@@ -1027,9 +1155,9 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
         }
       }
       cross3d(ps, pt, nrm);
-      double nn = sqrt(dot3d(nrm, nrm));
+      const double inn = 1.0 / sqrt(dot3d(nrm, nrm));
 #pragma unroll
-      for (int r = 0; r < 3; ++r) nrm[r] /= nn;
+      for (int r = 0; r < 3; ++r) nrm[r] *= inn;
       double xh[3];
 #pragma unroll
       for (int r = 0; r < 3; ++r) xh[r] = xs[r] + best * td[r];
@@ -1057,9 +1185,9 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
       if (fabs(td[2]) < fabs(td[im])) im = 2;
       ax[im] = 1.0;
       cross3d(td, ax, n1);
-      double n1n = sqrt(dot3d(n1, n1));
+      const double in1 = 1.0 / sqrt(dot3d(n1, n1));
 #pragma unroll
-      for (int r = 0; r < 3; ++r) n1[r] /= n1n;
+      for (int r = 0; r < 3; ++r) n1[r] *= in1;
       cross3d(td, n1, n2);
       if (!(L > 0.0)) break;
     } else {

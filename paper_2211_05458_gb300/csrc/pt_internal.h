@@ -58,7 +58,8 @@ struct DevConsts {
   float A32[5], B32[5];
   double mu, rho_p, g[3], mask[3];
   double newton_tol, band_ref, band_x, lost_tol;
-  int drag_law, max_newton, max_cross, guess;
+  double hl[4];                      // Haider-Levenspiel A, B, C, D
+  int drag_law, max_newton, max_cross, guess, lift, track;
 };
 
 struct DevParticles {

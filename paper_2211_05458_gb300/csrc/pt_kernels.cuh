@@ -97,6 +97,107 @@ __device__ __forceinline__ void start_guess_local(const DevMesh& m, const DevCon
     __syncthreads();                                  \
   }
 
+// Saffman lift with Mei's correction (Sec. 2.2): the force
+//   F_S = 6.46/4 C_S d^2 sqrt(rho mu / |w|) (u - v) x w,   w = curl u,
+// C_S = (1 - 0.3314 sqrt(th)) exp(-Re_p/10) + 0.3314 sqrt(th) for Re_p <= 40,
+// 0.0524 sqrt(th Re_p) above, th = d |w| / (2 |u - v|) held within
+// [0.005, 0.4]; zero when w or u - v vanishes.  The velocity gradient
+// differentiates the Lagrange interpolant of rho and rho u (sum-factorised,
+// Eq. part_interpolation): du_i/dxi_q = (d(rho u_i)/dxi_q - u_i drho/dxi_q)/rho,
+// mapped to physical space with the inverse Jacobian of the element map at xi.
+// Out of line: only runs with the lift enabled.
+template <int G, int NP, typename T>
+__device__ __noinline__ void saffman_force(const DevMesh& m, const DevConsts& k,
+                                           const T* __restrict__ Ue, int e, const double* xi,
+                                           const T* v, T d, T* F) {
+  constexpr int N3 = NP * NP * NP;
+  constexpr int G3 = G * G * G;
+  T l[3][NP], dl[3][NP];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) lagr_d<NP, T>((T)xi[q], Nodes<T>::sol(k), Nodes<T>::solw(k), l[q], dl[q]);
+  // value and d/dxi_1..3 of rho, rho u, rho v, rho w
+  T val[4], der[4][3];
+#pragma unroll 1
+  for (int w = 0; w < 4; ++w) {
+    const T* Uw = Ue + w * N3;
+    T s = 0, s1 = 0, s2 = 0, s3 = 0;
+#pragma unroll 1
+    for (int kk = 0; kk < NP; ++kk) {
+      T b0 = 0, b1 = 0, b2 = 0;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        T a0 = 0, a1 = 0;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          const T u = Uw[i + NP * (j + NP * kk)];
+          a0 = tfma(u, l[0][i], a0);
+          a1 = tfma(u, dl[0][i], a1);
+        }
+        b0 = tfma(a0, l[1][j], b0);
+        b1 = tfma(a1, l[1][j], b1);
+        b2 = tfma(a0, dl[1][j], b2);
+      }
+      T lk = T(0), dk = T(0);
+#pragma unroll
+      for (int c = 0; c < NP; ++c)
+        if (c == kk) {
+          lk = l[2][c];
+          dk = dl[2][c];
+        }
+      s = tfma(b0, lk, s);
+      s1 = tfma(b1, lk, s1);
+      s2 = tfma(b2, lk, s2);
+      s3 = tfma(b0, dk, s3);
+    }
+    val[w] = s;
+    der[w][0] = s1;
+    der[w][1] = s2;
+    der[w][2] = s3;
+  }
+  // Jacobian of the element map at xi and its inverse
+  T J[9], Ji[9];
+  if constexpr (std::is_same<T, float>::value) {
+    const float xf[3] = {(float)xi[0], (float)xi[1], (float)xi[2]};
+    float chi[3];
+    map_j32<G>(m.xg32 + (size_t)e * 3 * G3, xf, __ldg(m.tmask + e), k, chi, J);
+  } else {
+    double chi[3];
+    map64<G, true>(m.xg64 + (size_t)e * 3 * G3, xi, k, chi, J);
+  }
+  F[0] = F[1] = F[2] = T(0);
+  if (!inv3(J, Ji)) return;
+  const T rho = val[0], irho = T(1) / rho;
+  T u[3], rel[3], Gd[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    u[i] = val[1 + i] * irho;
+    rel[i] = u[i] - v[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T dxi[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) dxi[q] = (der[1 + i][q] - u[i] * der[0][q]) * irho;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Gd[3 * i + j] = dxi[0] * Ji[j] + dxi[1] * Ji[3 + j] + dxi[2] * Ji[6 + j];
+  }
+  const T w[3] = {Gd[7] - Gd[5], Gd[2] - Gd[6], Gd[3] - Gd[1]};
+  const T wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  const T rn = sqrt(rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2]);
+  if (!(wn > T(0)) || !(rn > T(0))) return;
+  const T mu = (T)k.mu;
+  const T re = rho * rn * d / mu;
+  T th = d * wn / (T(2) * rn);
+  th = th < T(0.005) ? T(0.005) : (th > T(0.4) ? T(0.4) : th);
+  const T sth = sqrt(th);
+  const T cs = re <= T(40) ? (T(1) - T(0.3314) * sth) * exp(T(-0.1) * re) + T(0.3314) * sth
+                           : T(0.0524) * sqrt(th * re);
+  const T kf = T(6.46 / 4.0) * cs * d * d * sqrt(rho * mu / wn);
+  F[0] = kf * (rel[1] * w[2] - rel[2] * w[1]);
+  F[1] = kf * (rel[2] * w[0] - rel[0] * w[2]);
+  F[2] = kf * (rel[0] * w[1] - rel[1] * w[0]);
+}
+
 struct PushCounters {
   unsigned long long steps, it32, it64;
   TrackCounters tc;
@@ -110,8 +211,9 @@ struct PushCounters {
 // |xi_d| -- translated on a periodic face -- and mapped again, until it lands
 // inside, across at most 4 faces; a wall or open face ends the walk and the
 // particle is lost as before.  Only a stage that took the exact tracking path
-// can leave a particle outside, so the push checks the final position of such
-// a stage as well.  Returns 0 (inside), 1 (inverse map failed) or 2 (lost).
+// can leave a particle outside: the walk runs only after such a stage (a
+// particle found outside otherwise, e.g. given outside its element, is lost),
+// and the push checks the final position of such a stage as well.  Returns 0 (inside), 1 (inverse map failed) or 2 (lost).
 // Out of line: it is rare.
 __device__ __forceinline__ int settle_face(const double* z) {
   const double a0 = fabs(z[0]), a1 = fabs(z[1]), a2 = fabs(z[2]);
@@ -119,10 +221,18 @@ __device__ __forceinline__ int settle_face(const double* z) {
   return 2 * d + (z[d] > 0.0 ? 1 : 0);
 }
 
+// Walk threshold: with physical tracking a position up to lost_tol outside is
+// accepted (the tracking decided the owner); with reference-space localisation
+// the owner is decided here, to the near-face band.
+__device__ __forceinline__ double settle_tol(const DevConsts& k) {
+  return k.track == PT_TRACK_REFERENCE ? fmin(k.band_ref, k.lost_tol) : k.lost_tol;
+}
+
 // FP64 mode: x global, xi valid on entry if have.
 template <int G>
 __device__ __noinline__ int settle64(const DevMesh& m, const DevConsts& k, int& e, double* x,
                                      double* xi, bool have, int& it64, int& cross) {
+  const double wtol = settle_tol(k);
 #pragma unroll 1
   for (int w = 0; w <= 4; ++w) {
     if (!have) {
@@ -138,8 +248,8 @@ __device__ __noinline__ int settle64(const DevMesh& m, const DevConsts& k, int& 
         return 1;
     }
     have = false;
-    if (tmax3(xi[0], xi[1], xi[2]) <= 1.0 + k.lost_tol) return 0;
-    if (w == 4) break;
+    if (tmax3(xi[0], xi[1], xi[2]) <= 1.0 + wtol) return 0;
+    if (w == 4) return tmax3(xi[0], xi[1], xi[2]) <= 1.0 + k.lost_tol ? 0 : 2;
     const int f = settle_face(xi);
     const int bc = __ldg(m.finfo + 6 * (size_t)e + f) & 3;
     if (bc != PT_BC_INTERNAL && bc != PT_BC_PERIODIC) break;
@@ -159,6 +269,7 @@ __device__ __noinline__ int settle64(const DevMesh& m, const DevConsts& k, int& 
 template <int G>
 __device__ __noinline__ int settle_f32(const DevMesh& m, const DevConsts& k, int& e, df* xd,
                                        df* zd, bool have, int& it32, int& it64, int& cross) {
+  const double wtol = settle_tol(k);
 #pragma unroll 1
   for (int w = 0; w <= 4; ++w) {
     if (!have) {
@@ -169,8 +280,8 @@ __device__ __noinline__ int settle_f32(const DevMesh& m, const DevConsts& k, int
     }
     have = false;
     const double z[3] = {df_to_double(zd[0]), df_to_double(zd[1]), df_to_double(zd[2])};
-    if (tmax3(z[0], z[1], z[2]) <= 1.0 + k.lost_tol) return 0;
-    if (w == 4) break;
+    if (tmax3(z[0], z[1], z[2]) <= 1.0 + wtol) return 0;
+    if (w == 4) return tmax3(z[0], z[1], z[2]) <= 1.0 + k.lost_tol ? 0 : 2;
     const int f = settle_face(z);
     const int bc = __ldg(m.finfo + 6 * (size_t)e + f) & 3;
     if (bc != PT_BC_INTERNAL && bc != PT_BC_PERIODIC) break;
@@ -256,7 +367,12 @@ __device__ __forceinline__ void push_particle(const DevMesh& m, const DevConsts&
         continue;
       }
       double mx = tmax3(xi[0], xi[1], xi[2]);
-      if (mx > 1.0 + k.lost_tol) {
+      if (mx > 1.0 + k.lost_tol && !pending) {  // outside without having moved: lost
+        st |= PT_ST_LOST;
+        live = false;
+        continue;
+      }
+      if (mx > 1.0 + settle_tol(k) && pending) {
         int cr = 0, j64 = 0;
         const int rc = settle64<G>(m, k, e, x, xi, true, j64, cr);
         c.it64 += j64;
@@ -283,15 +399,22 @@ __device__ __forceinline__ void push_particle(const DevMesh& m, const DevConsts&
       R fD = R(1);
       if (k.drag_law) {
         R re = Uv[0] * sqrt(rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2]) * d / mu;
-        if (re >= R(800)) st |= PT_ST_REP800;
-        fD = drag_factor<R>(1, re);
+        if (k.drag_law == 1 && re >= R(800)) st |= PT_ST_REP800;
+        fD = drag_factor<R>(k, re);
       }
       const R coef = fD / tau;
+      R al[3] = {R(0), R(0), R(0)};
+      if (k.lift) {
+        saffman_force<G, NP, R>(m, k, U + (size_t)e * 5 * N3, e, xi, v, d, al);
+        const R imp = R(6) / (R(3.14159265358979323846) * (R)k.rho_p * d * d * d);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) al[r] *= imp;
+      }
       double xe[3];
       float bf[3];
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        R acc = (R)k.mask[r] * coef * rel[r] + (R)k.g[r];
+        R acc = (R)k.mask[r] * coef * rel[r] + (R)k.g[r] + al[r];
         kx[r] = As * kx[r] + dt * v[r];
         kv[r] = As * kv[r] + dt * acc;
         const R dx = Bs * kx[r];
@@ -299,9 +422,17 @@ __device__ __forceinline__ void push_particle(const DevMesh& m, const DevConsts&
         bf[r] = F64 ? (float)(xl[r] + (double)dx) : xf[r] + (float)dx;
         v[r] = v[r] + Bs * kv[r];
       }
-      const int slow0 = c.tc.slow;
-      track<G, R>(m, k, e, x, xe, xf, bf, v, kx, kv, hits, st, c.tc);
-      pending = c.tc.slow != slow0;
+      const int touch = slab_touch(m, e, xf, bf);
+      if (!(touch & (k.track == PT_TRACK_REFERENCE ? 2 : 1))) {
+        // no face reachable, or (localisation) no wall or open face: the end
+        // point's owner is found by the next inverse map
+#pragma unroll
+        for (int r = 0; r < 3; ++r) x[r] = xe[r];
+        pending = touch != 0;
+      } else {
+        track_slow<G, R>(m, k, e, x, xe, v, kx, kv, hits, st, c.tc);
+        pending = true;
+      }
       if (st & PT_ST_FROZEN) live = false;
     }
     if (live) ++c.steps;
@@ -398,7 +529,12 @@ __device__ __forceinline__ void push_particle_f32(const DevMesh& m, const DevCon
       if (mx > 1.f - 1e-5f) {  // decide the bands exactly (rare)
         double md = fmax(fmax(fabs(df_to_double(zd[0])), fabs(df_to_double(zd[1]))),
                          fabs(df_to_double(zd[2])));
-        if (md > 1.0 + k.lost_tol) {
+        if (md > 1.0 + k.lost_tol && !pending) {  // outside without having moved: lost
+          st |= PT_ST_LOST;
+          live = false;
+          continue;
+        }
+        if (md > 1.0 + settle_tol(k) && pending) {
           int cr = 0, j32 = 0, j64 = 0;
           const int rc = settle_f32<G>(m, k, e, xd, zd, true, j32, j64, cr);
           c.it32 += j32;
@@ -430,24 +566,36 @@ __device__ __forceinline__ void push_particle_f32(const DevMesh& m, const DevCon
       float fD = 1.f;
       if (k.drag_law) {
         float re = Uv[0] * sqrtf(rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2]) * d / mu;
-        if (re >= 800.f) st |= PT_ST_REP800;
-        fD = drag_factor<float>(1, re);
+        if (k.drag_law == 1 && re >= 800.f) st |= PT_ST_REP800;
+        fD = drag_factor<float>(k, re);
       }
       const float coef = fD / tau;
+      float al[3] = {0.f, 0.f, 0.f};
+      if (k.lift) {
+        const double xid[3] = {df_to_double(zd[0]), df_to_double(zd[1]), df_to_double(zd[2])};
+        saffman_force<G, NP, float>(m, k, U + (size_t)e * 5 * N3, e, xid, v, d, al);
+        const float imp = 6.f / (3.14159265358979323846f * (float)k.rho_p * d * d * d);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) al[r] *= imp;
+      }
       df xe[3];
       float bf[3];
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        float acc = (float)k.mask[r] * coef * rel[r] + (float)k.g[r];
+        float acc = (float)k.mask[r] * coef * rel[r] + (float)k.g[r] + al[r];
         kx[r] = As * kx[r] + dt * v[r];
         kv[r] = As * kv[r] + dt * acc;
         xe[r] = df_add(xd[r], df_from(Bs * kx[r]));
         bf[r] = xe[r].hi;
         v[r] = v[r] + Bs * kv[r];
       }
-      if (!touches_any_slab(m, e, xf, bf)) {
+      const int touch = slab_touch(m, e, xf, bf);
+      if (!(touch & (k.track == PT_TRACK_REFERENCE ? 2 : 1))) {
+        // no face reachable, or (localisation) no wall or open face: the end
+        // point's owner is found by the next inverse map
 #pragma unroll
         for (int r = 0; r < 3; ++r) xd[r] = xe[r];
+        if (touch) pending = true;
       } else {
         // exact tracking in FP64 on global positions, then back to local
         const double* ce = m.ce + 3 * (size_t)e;
@@ -609,16 +757,20 @@ __device__ __forceinline__ bool particle_source(const DepositArgs& a, int64_t ip
   R fD = R(1);
   if (a.k.drag_law) {
     R re = Uv[0] * sqrt(rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2]) * d / mu;
-    fD = drag_factor<R>(1, re);
+    fD = drag_factor<R>(a.k, re);
   }
-  // F = m_p f_D (u - v) / tau_p with m_p / tau_p = 3 pi mu d
+  // F = m_p f_D (u - v) / tau_p with m_p / tau_p = 3 pi mu d, plus the lift
   const R c = R(3.14159265358979323846) * R(3) * mu * d * fD;
-  R Fe = R(0);
+  R FS[3] = {R(0), R(0), R(0)};
+  if (a.k.lift)
+    saffman_force<G, NP, R>(a.m, a.k, reinterpret_cast<const R*>(a.U) + (size_t)e * 5 * N3, e, xi,
+                            v, d, FS);
+  R Fv[3], Fe = R(0);
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    R Fr = c * rel[r];
-    f[r] = (float)(-Fr);
-    Fe -= Fr * v[r];
+    Fv[r] = c * rel[r] + FS[r];
+    f[r] = (float)(-Fv[r]);
+    Fe -= Fv[r] * v[r];
   }
   if constexpr (NEAR) {
     int id[3];
@@ -643,7 +795,7 @@ __device__ __forceinline__ bool particle_source(const DepositArgs& a, int64_t ip
                        J[2] * (J[3] * J[7] - J[4] * J[6]);
     const R iv = R(1) / (R)(a.k.sq[id[0]] * a.k.sq[id[1]] * a.k.sq[id[2]] * fabs(det));
 #pragma unroll
-    for (int r = 0; r < 3; ++r) f[r] = (float)(-(c * rel[r]) * iv);
+    for (int r = 0; r < 3; ++r) f[r] = (float)(-Fv[r] * iv);
     f[3] = (float)(Fe * iv);
 #pragma unroll
     for (int i = 0; i < NP; ++i) {

@@ -22,6 +22,7 @@ FP64, FP32 = 0, 1
 STOKES, SCHILLER_NAUMANN = 0, 1
 GUESS_TRILINEAR, GUESS_MLP = 0, 1
 DEPOSIT_ATOMIC, DEPOSIT_SEGMENTED, DEPOSIT_NEAREST = 0, 1, 2
+TRACK_PHYSICAL, TRACK_REFERENCE = 0, 1
 
 _vp = ctypes.c_void_p
 
@@ -34,7 +35,9 @@ class Config(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("drag_law", ctypes.c_int32),
                 ("guess", ctypes.c_int32), ("max_newton", ctypes.c_int32),
                 ("max_cross", ctypes.c_int32), ("rebin_every", ctypes.c_int32),
-                ("block", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9)]
+                ("block", ctypes.c_int32), ("lift", ctypes.c_int32),
+                ("sphericity", ctypes.c_double), ("track", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class MeshDesc(ctypes.Structure):

@@ -27,11 +27,13 @@ def _setup(nbox=6, seed=1):
 def test_batch_equals_individual_pushes_bitwise():
     boxes, ctxs, parts = _setup()
     ref = [p.clone() for p in parts]
-    for _ in range(2):  # first call tunes the block size, second replays the graph
+    # 20 steps are two chunks: calls 1 and 2 try the three block sizes, call 3
+    # captures the graph and replays it, call 4 replays it again
+    for _ in range(4):
         st = pt.push_batch(ctxs, parts, 20, 2e-3)
     for c, p in zip(ctxs, ref):
-        c.push(p, 20, 2e-3)
-        c.push(p, 20, 2e-3)
+        for _ in range(4):
+            c.push(p, 20, 2e-3)
     torch.cuda.synchronize()
     for a, b in zip(parts, ref):
         for f in ("x", "v", "elem", "hits", "status"):

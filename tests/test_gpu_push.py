@@ -8,6 +8,7 @@ import pytest
 import torch
 
 import oracle
+from paper_2211_05458_gb300 import pt
 from paper_2211_05458_gb300 import workloads as W
 from tests import helpers as H
 
@@ -148,3 +149,23 @@ def test_bad_arguments_are_rejected():
         ctx.push(parts, 1, -1.0)
     with pytest.raises(pt.PtError):
         ctx.push(parts, 1, float("nan"))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("ngeo,N", [(2, 5), (3, 5)])
+def test_reference_space_localisation_matches_physical_oracle(precision, tol, ngeo, N):
+    """Sec. 3.2.3: with PT_TRACK_REFERENCE only walls are intersected; internal
+    and periodic crossings are found by the inverse map and the face walk.  The
+    owners, wall hits and states equal the oracle's physical tracking."""
+    wl = W.curved_channel((6, 6, 6), ngeo, N, P=400, nsteps=40, dt=2e-3, st=(0.1, 100.0))
+    _speed_up(wl)
+    band = None if precision == "fp64" else (2e-4, 1e-4 * 2.0 / 6)
+    res, g, o = _push_and_compare(wl, precision, tol, band=band, track=pt.TRACK_REFERENCE,
+                                  min_checked=0.85)
+    assert res["stats"]["crossings"] > 50 and res["stats"]["wall_hits"] >= 1
+
+
+def test_reference_space_localisation_periodic_box():
+    wl = W.tgv_box(8, 3, P=2000, nsteps=100)
+    res, g, o = _push_and_compare(wl, "fp64", 1e-12, track=pt.TRACK_REFERENCE)
+    assert res["stats"]["crossings"] > 100 and res["stats"]["slow_track"] == 0
