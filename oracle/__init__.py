@@ -57,15 +57,15 @@ class Params(ctypes.Structure):
         ("max_cross", ctypes.c_int), ("pad", ctypes.c_int),
         ("newton_tol", ctypes.c_double), ("band_ref", ctypes.c_double),
         ("band_x", ctypes.c_double), ("lost_tol", ctypes.c_double),
-        ("lift", ctypes.c_int), ("pad2", ctypes.c_int), ("sphericity", ctypes.c_double),
+        ("lift", ctypes.c_int), ("buoyancy", ctypes.c_int), ("sphericity", ctypes.c_double),
     ]
 
 
 def make_params(mu=1e-5, rho_p=1000.0, drag_law=0, g=(0.0, 0.0, 0.0), mask=(1.0, 1.0, 1.0),
                 max_newton=50, max_cross=64, newton_tol=1e-12, band_ref=1e-10, band_x=1e-10,
-                lost_tol=1e-6, lift=0, sphericity=1.0) -> Params:
+                lost_tol=1e-6, lift=0, sphericity=1.0, buoyancy=0) -> Params:
     p = Params()
-    p.lift, p.sphericity = lift, sphericity
+    p.lift, p.sphericity, p.buoyancy = lift, sphericity, buoyancy
     p.mu, p.rho_p, p.drag_law, p.max_newton = mu, rho_p, drag_law, max_newton
     p.g[:] = list(g)
     p.mask[:] = list(mask)

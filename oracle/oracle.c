@@ -841,7 +841,8 @@ static void particle_accel(const or_ctx* c, const or_params* p, int e, const dou
   double mp = p->rho_p * pi * d * d * d / 6.0;
   double fD = drag_factor(p, U[0], rel, d, status);
   for (int r = 0; r < 3; ++r) {
-    acc[r] = p->mask[r] * fD * rel[r] / tau + p->g[r];
+    /* gravity on m_p - m_f with buoyancy (Eq. theory:maxey), else on m_p */
+    acc[r] = p->mask[r] * fD * rel[r] / tau + p->g[r] * (p->buoyancy ? 1.0 - U[0] / p->rho_p : 1.0);
     F[r] = mp * fD * rel[r] / tau;
   }
   if (p->lift) {

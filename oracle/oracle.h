@@ -54,7 +54,7 @@ typedef struct {
   double band_x;      /* near-face band in physical length                  */
   double lost_tol;    /* xi outside [-1-lost_tol, 1+lost_tol] => lost       */
   int    lift;        /* 1: Saffman lift with Mei's correction (Sec. 2.2)   */
-  int    pad2;
+  int    buoyancy;    /* 1: gravity acts on m_p - m_f (Eq. theory:maxey)      */
   double sphericity;  /* drag_law 2 (Haider-Levenspiel): particle sphericity */
 } or_params;
 

@@ -293,6 +293,22 @@ def test_schiller_naumann_terminal_velocity():
     assert abs(out["v"][0, 0]) < 1e-14 and abs(out["v"][0, 2]) < 1e-14
 
 
+def test_stokes_settling_with_buoyancy():
+    """Eq. theory:maxey with gravity on m_p - m_f: quiescent fluid of density
+    rho_f (fluid_uniform: rho = 1), Stokes drag; the settling speed tends to
+    Stokes' terminal velocity g tau_p (1 - rho_f/rho_p)."""
+    mesh, orc = _uniform_setup(np.zeros(3), N=1, dims=(3, 3, 3))
+    mu, rho_p, d, g = 1e-5, 2.5, 2e-5, 9.81   # light particles: buoyancy 40 %
+    tau = rho_p * d * d / (18 * mu)
+    x0 = np.array([[0.3, 0.6, 0.7]])
+    el = orc.locate_bruteforce(x0[0])
+    vt = g * tau * (1 - 1.0 / rho_p)
+    for b, want in [(1, vt), (0, g * tau)]:
+        p = oracle.make_params(mu=mu, rho_p=rho_p, g=(0, -g, 0), buoyancy=b)
+        out = orc.push(p, x0, np.zeros((1, 3)), [d], el, nsteps=200, dt=1e-5)
+        assert abs(out["v"][0, 1] + want) < 1e-9 * want, (b, out["v"][0, 1], want)
+
+
 # ---------------------------------------------------------------------------
 # tracking
 # ---------------------------------------------------------------------------
