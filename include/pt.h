@@ -121,7 +121,10 @@ typedef struct {
                            (default 1): f_D = 1 + A Re^B + (Re/24) C / (1 + D/Re)
                            with A..D the Haider & Levenspiel (1989) fits          */
   int32_t track;        /* pt_track (default PT_TRACK_PHYSICAL)                    */
-  int32_t reserved[5];
+  int32_t buoyancy;     /* 1: gravity acts on m_p - m_f, i.e. g (1 - rho/rho_p)
+                           with the interpolated fluid density (Eq. theory:maxey);
+                           0: g acts on m_p alone (default 0)                     */
+  int32_t reserved[4];
 } pt_config;
 
 /* Particles, structure of arrays, all device memory, caller-owned, updated in
@@ -237,6 +240,21 @@ pt_status pt_deposit(pt_ctx* ctx, const pt_particles* p, int32_t mode, float* S_
  * reuses the same array and clears what must start at zero; calls whose work
  * overlaps on the GPU (other streams, other contexts) race on it. */
 pt_status pt_deposit_noalloc(pt_ctx* ctx, const pt_particles* p, int32_t mode, float* S_dev);
+
+/* Point location without a known element (Sec. 3.2.3, localisation in
+ * reference space): for each x the candidates are the elements listed in x's
+ * cell of a uniform background grid (an element is listed in every cell its
+ * Bezier control box meets), tried closest element centre first with the
+ * inverse map; the first with max |xi| <= 1 + lost_tol owns x.  x_dev double
+ * [3][n] device; elem_dev int32 [n] out (-1: no element contains x);
+ * xi_dev double [3][n] out (0 where not found); status_dev uint32 [n] out or
+ * NULL (0, or PT_ST_LOST where not found).  The first call builds the grid
+ * (host work over all elements, device memory released by pt_destroy);
+ * PT_ERR_ARG if the elements are too distorted for a grid of at most 64
+ * candidates per cell.  A point on a face shared by several elements gets one
+ * of them. */
+pt_status pt_find_element(pt_ctx* ctx, int64_t n, const double* x_dev, int32_t* elem_dev,
+                          double* xi_dev, uint32_t* status_dev);
 
 /* Inverse map only (Sec. 3.2.1): for each i, xi of x[:,i] in element elem[i].
  * x_dev double [3][n], elem_dev int32 [n], xi_dev double [3][n] out,

@@ -42,6 +42,12 @@ int fam_g3_fp64_loc(const LocateArgs&, int, int, void*);
 int fam_g3_fp32_loc(const LocateArgs&, int, int, void*);
 int fam_g4_fp64_loc(const LocateArgs&, int, int, void*);
 int fam_g4_fp32_loc(const LocateArgs&, int, int, void*);
+int fam_g2_fp64_find(const FindArgs&, int, int, void*);
+int fam_g2_fp32_find(const FindArgs&, int, int, void*);
+int fam_g3_fp64_find(const FindArgs&, int, int, void*);
+int fam_g3_fp32_find(const FindArgs&, int, int, void*);
+int fam_g4_fp64_find(const FindArgs&, int, int, void*);
+int fam_g4_fp32_find(const FindArgs&, int, int, void*);
 
 #define PT_DISPATCH(g, f64, SUFFIX, ...)                                          \
   ((g) == 2 ? ((f64) ? fam_g2_fp64_##SUFFIX(__VA_ARGS__) : fam_g2_fp32_##SUFFIX(__VA_ARGS__)) \
@@ -57,6 +63,9 @@ int launch_deposit(int g, bool f64, int np, int mode, const DepositArgs& a, int 
 }
 int max_active_push(int g, bool f64, int np, int block) {
   return PT_DISPATCH(g, f64, occ, np, block);
+}
+int launch_find(int g, bool f64, const FindArgs& a, int grid, int block, void* s) {
+  return PT_DISPATCH(g, f64, find, a, grid, block, s);
 }
 int launch_locate(int g, bool f64, int np, const LocateArgs& a, int grid, int block, void* s) {
   (void)np;
@@ -543,6 +552,7 @@ static void fill_consts(const pt_ctx* c, DevConsts& k) {
   k.drag_law = c->cfg.drag_law;
   k.lift = c->cfg.lift;
   k.track = c->cfg.track;
+  k.buoyancy = c->cfg.buoyancy;
   {
     // Haider & Levenspiel (1989) fits in the sphericity
     const double f = c->cfg.sphericity;
@@ -589,6 +599,8 @@ static pt_status check_config(const pt_config* cfg) {
       !(cfg->sphericity > 0.0 && cfg->sphericity <= 1.0))
     return fail(nullptr, PT_ERR_ARG, "sphericity must be in (0, 1]");
   if (cfg->lift != 0 && cfg->lift != 1) return fail(nullptr, PT_ERR_ARG, "lift must be 0 or 1");
+  if (cfg->buoyancy != 0 && cfg->buoyancy != 1)
+    return fail(nullptr, PT_ERR_ARG, "buoyancy must be 0 or 1");
   if (cfg->track != PT_TRACK_PHYSICAL && cfg->track != PT_TRACK_REFERENCE)
     return fail(nullptr, PT_ERR_ARG, "track must be PT_TRACK_PHYSICAL or PT_TRACK_REFERENCE");
   if (cfg->guess != 0 && cfg->guess != 1) return fail(nullptr, PT_ERR_ARG, "bad guess");
@@ -966,6 +978,139 @@ pt_status pt_deposit(pt_ctx* c, const pt_particles* p, int32_t mode, float* S) {
     rc = launch_deposit(c->g, f64, np, mode, a, grid, 256, c->stream);
   }
   if (rc) return fail(c, PT_ERR_CUDA, "deposit launch: %s", cudaGetErrorString((cudaError_t)rc));
+  return PT_OK;
+}
+
+// Background grid of pt_find_element: every element is listed in the cells its
+// control box meets.  The box of an element is the box of the Bezier control
+// points of its map (the element lies in their convex hull).  The cell size
+// starts at the mean element size and shrinks until no cell lists more than
+// PT_FIND_MAXC elements.
+static pt_status build_find_grid(pt_ctx* c) {
+  const int E = c->nelem, g = c->g, g3 = g * g * g;
+  std::vector<double> xg((size_t)E * g3 * 3), ce((size_t)E * 3);
+  CK(cudaMemcpy(xg.data(), c->d_xg64, xg.size() * 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(ce.data(), c->d_ce, ce.size() * 8, cudaMemcpyDeviceToHost));
+  std::vector<double> M;
+  bezier_matrix(g, M);
+  std::vector<double> box((size_t)E * 6);
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  std::vector<double> t1(g3), t2(g3);
+  for (int e = 0; e < E; ++e) {
+    double* b = &box[6 * (size_t)e];
+    for (int r = 0; r < 3; ++r) {
+      b[r] = 1e300;
+      b[3 + r] = -1e300;
+      // control values of coordinate r: M applied along each direction
+      for (int q = 0; q < g3; ++q) t1[q] = xg[((size_t)e * g3 + q) * 3 + r];
+      for (int dir = 0; dir < 3; ++dir) {
+        const int st = dir == 0 ? 1 : dir == 1 ? g : g * g;
+        for (int q = 0; q < g3; ++q) {
+          const int i = (q / st) % g, base = q - i * st;
+          double v = 0.0;
+          for (int j = 0; j < g; ++j) v += M[i * g + j] * t1[base + j * st];
+          t2[q] = v;
+        }
+        t1.swap(t2);
+      }
+      for (int q = 0; q < g3; ++q) {
+        b[r] = std::min(b[r], t1[q] + ce[3 * e + r]);
+        b[3 + r] = std::max(b[3 + r], t1[q] + ce[3 * e + r]);
+      }
+      lo[r] = std::min(lo[r], b[r]);
+      hi[r] = std::max(hi[r], b[3 + r]);
+    }
+  }
+  double vol = 1.0, pad[3];
+  for (int r = 0; r < 3; ++r) {
+    pad[r] = 1e-9 * (hi[r] - lo[r]) + 1e-300;
+    lo[r] -= pad[r];
+    hi[r] += pad[r];
+    vol *= hi[r] - lo[r];
+  }
+  double h = std::cbrt(vol / E);
+  for (int attempt = 0; attempt < 8; ++attempt, h /= 1.5) {
+    int dims[3];
+    size_t ncell = 1;
+    for (int r = 0; r < 3; ++r) {
+      dims[r] = std::max(1, (int)std::ceil((hi[r] - lo[r]) / h));
+      ncell *= (size_t)dims[r];
+    }
+    if (ncell > (size_t)64 * E + 4096) break;
+    std::vector<int> start(ncell + 1, 0);
+    auto cells_of = [&](int e, int* c0, int* c1) {
+      for (int r = 0; r < 3; ++r) {
+        c0[r] = std::max(0, std::min(dims[r] - 1, (int)((box[6 * (size_t)e + r] - 1e-12 * h - lo[r]) / h)));
+        c1[r] = std::max(0, std::min(dims[r] - 1, (int)((box[6 * (size_t)e + 3 + r] + 1e-12 * h - lo[r]) / h)));
+      }
+    };
+    for (int e = 0; e < E; ++e) {
+      int c0[3], c1[3];
+      cells_of(e, c0, c1);
+      for (int k = c0[2]; k <= c1[2]; ++k)
+        for (int j = c0[1]; j <= c1[1]; ++j)
+          for (int i = c0[0]; i <= c1[0]; ++i) start[i + (size_t)dims[0] * (j + (size_t)dims[1] * k) + 1]++;
+    }
+    int maxc = 0;
+    for (size_t q = 0; q < ncell; ++q) maxc = std::max(maxc, start[q + 1]);
+    if (maxc > PT_FIND_MAXC) continue;
+    for (size_t q = 0; q < ncell; ++q) start[q + 1] += start[q];
+    std::vector<int> cur(start.begin(), start.end() - 1), list(start[ncell]);
+    for (int e = 0; e < E; ++e) {
+      int c0[3], c1[3];
+      cells_of(e, c0, c1);
+      for (int k = c0[2]; k <= c1[2]; ++k)
+        for (int j = c0[1]; j <= c1[1]; ++j)
+          for (int i = c0[0]; i <= c1[0]; ++i)
+            list[cur[i + (size_t)dims[0] * (j + (size_t)dims[1] * k)]++] = e;
+    }
+    cudaError_t err;
+    c->d_cell_start = dmalloc<int>(c, start.size(), &err);
+    if (err) return fail(c, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
+    c->d_cell_elem = dmalloc<int>(c, std::max<size_t>(list.size(), 1), &err);
+    if (err) return fail(c, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
+    CK(cudaMemcpy(c->d_cell_start, start.data(), start.size() * 4, cudaMemcpyHostToDevice));
+    if (!list.empty())
+      CK(cudaMemcpy(c->d_cell_elem, list.data(), list.size() * 4, cudaMemcpyHostToDevice));
+    for (int r = 0; r < 3; ++r) {
+      c->grid_lo[r] = lo[r];
+      c->grid_ih[r] = 1.0 / h;
+      c->grid_dims[r] = dims[r];
+    }
+    c->grid_ready = true;
+    return PT_OK;
+  }
+  return fail(c, PT_ERR_ARG, "pt_find_element: elements too distorted for the background grid");
+}
+
+pt_status pt_find_element(pt_ctx* c, int64_t n, const double* x, int32_t* elem, double* xi,
+                          uint32_t* status) {
+  if (!c) return fail(nullptr, PT_ERR_ARG, "ctx is NULL");
+  if (n < 0) return fail(c, PT_ERR_ARG, "n must be >= 0");
+  if (n > 0 && (!x || !elem || !xi)) return fail(c, PT_ERR_ARG, "NULL array");
+  if (!c->grid_ready) {
+    pt_status s = build_find_grid(c);
+    if (s) return s;
+  }
+  if (n == 0) return PT_OK;
+  FindArgs a;
+  a.m = dev_mesh(c);
+  fill_consts(c, a.k);
+  a.n = n;
+  a.x = x;
+  a.elem = elem;
+  a.xi = xi;
+  a.status = status;
+  for (int r = 0; r < 3; ++r) {
+    a.lo[r] = c->grid_lo[r];
+    a.ih[r] = c->grid_ih[r];
+    a.dims[r] = c->grid_dims[r];
+  }
+  a.cell_start = c->d_cell_start;
+  a.cell_elem = c->d_cell_elem;
+  int grid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)c->nsm * 16);
+  int rc = launch_find(c->g, c->cfg.precision == PT_FP64, a, grid, 128, c->stream);
+  if (rc) return fail(c, PT_ERR_CUDA, "find launch: %s", cudaGetErrorString((cudaError_t)rc));
   return PT_OK;
 }
 

@@ -48,6 +48,12 @@ struct pt_ctx {
   pt_mlp_state* mlp = nullptr;
   bool mlp_ready = false;
   float* d_mlp_pre = nullptr;
+  // background grid of pt_find_element, built on its first call
+  bool grid_ready = false;
+  int* d_cell_start = nullptr;
+  int* d_cell_elem = nullptr;
+  double grid_lo[3] = {0, 0, 0}, grid_ih[3] = {0, 0, 0};
+  int grid_dims[3] = {0, 0, 0};
   // batched push plan (pt_push_batch called with this context first)
   pt_batch_plan* batch = nullptr;
   // kernel timing (pt_profile)

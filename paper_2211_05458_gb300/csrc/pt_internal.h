@@ -59,7 +59,7 @@ struct DevConsts {
   double mu, rho_p, g[3], mask[3];
   double newton_tol, band_ref, band_x, lost_tol;
   double hl[4];                      // Haider-Levenspiel A, B, C, D
-  int drag_law, max_newton, max_cross, guess, lift, track;
+  int drag_law, max_newton, max_cross, guess, lift, track, buoyancy;
 };
 
 struct DevParticles {
@@ -109,6 +109,22 @@ struct LocateArgs {
   unsigned* status;
 };
 
+// point location without a known element: background grid of element lists
+#define PT_FIND_MAXC 64  // candidates per grid cell at most
+struct FindArgs {
+  DevMesh m;
+  DevConsts k;
+  int64_t n;
+  const double* x;        // [3][n]
+  int* elem;              // [n] out, -1 if not found
+  double* xi;             // [3][n] out
+  unsigned* status;       // [n] out, 0 or PT_ST_LOST
+  double lo[3], ih[3];    // grid origin and inverse cell size
+  int dims[3];
+  const int* cell_start;  // [ncell + 1]
+  const int* cell_elem;   // elements whose control box meets the cell
+};
+
 struct DepositArgs {
   DevMesh m;
   DevConsts k;
@@ -122,6 +138,7 @@ struct DepositArgs {
 // kernel entry points, one family per (g, mode) translation unit
 namespace pt {
 int launch_push(int g, bool fp64, int np, const PushArgs& a, int grid, int block, void* stream);
+int launch_find(int g, bool fp64, const FindArgs& a, int grid, int block, void* stream);
 int launch_locate(int g, bool fp64, int np, const LocateArgs& a, int grid, int block,
                   void* stream);
 int launch_deposit(int g, bool fp64, int np, int mode, const DepositArgs& a, int grid, int block,

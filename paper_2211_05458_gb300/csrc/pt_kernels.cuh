@@ -412,9 +412,10 @@ __device__ __forceinline__ void push_particle(const DevMesh& m, const DevConsts&
       }
       double xe[3];
       float bf[3];
+      const R gf = k.buoyancy ? R(1) - Uv[0] / (R)k.rho_p : R(1);
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        R acc = (R)k.mask[r] * coef * rel[r] + (R)k.g[r] + al[r];
+        R acc = (R)k.mask[r] * coef * rel[r] + (R)k.g[r] * gf + al[r];
         kx[r] = As * kx[r] + dt * v[r];
         kv[r] = As * kv[r] + dt * acc;
         const R dx = Bs * kx[r];
@@ -580,9 +581,10 @@ __device__ __forceinline__ void push_particle_f32(const DevMesh& m, const DevCon
       }
       df xe[3];
       float bf[3];
+      const float gf = k.buoyancy ? 1.f - Uv[0] / (float)k.rho_p : 1.f;
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        float acc = (float)k.mask[r] * coef * rel[r] + (float)k.g[r] + al[r];
+        float acc = (float)k.mask[r] * coef * rel[r] + (float)k.g[r] * gf + al[r];
         kx[r] = As * kx[r] + dt * v[r];
         kv[r] = As * kv[r] + dt * acc;
         xe[r] = df_add(xd[r], df_from(Bs * kx[r]));
@@ -712,6 +714,69 @@ __global__ void __launch_bounds__(256) k_locate(const __grid_constant__ LocateAr
     a.xi[2 * a.n + i] = xi[2];
     if (a.iters) a.iters[i] = i32 + i64;
     if (a.status) a.status[i] = ok ? 0u : (unsigned)PT_ST_NEWTON_FAIL;
+  }
+}
+
+// Point location without a known element (localisation in reference space,
+// Sec. 3.2.3): the candidates are the elements listed in x's cell of a uniform
+// background grid, tried closest centre first; the first whose inverse map
+// puts x inside (max |xi| <= 1 + lost_tol) owns it.  At most 64 candidates per
+// cell (the grid builder guarantees it).
+template <int G, bool F64>
+__global__ void __launch_bounds__(128) k_find(const __grid_constant__ FindArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const double x[3] = {a.x[i], a.x[a.n + i], a.x[2 * a.n + i]};
+    int cidx[3];
+    bool inside = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double u = (x[d] - a.lo[d]) * a.ih[d];
+      inside = inside && u >= 0.0 && u < (double)a.dims[d];
+      cidx[d] = inside ? (int)u : 0;
+    }
+    int found = -1;
+    double xi[3] = {0.0, 0.0, 0.0};
+    if (inside) {
+      const int cell = cidx[0] + a.dims[0] * (cidx[1] + a.dims[1] * cidx[2]);
+      const int beg = a.cell_start[cell];
+      const int cnt = min(a.cell_start[cell + 1] - beg, PT_FIND_MAXC);
+      unsigned long long done = 0ull;
+#pragma unroll 1
+      for (int t = 0; t < cnt && found < 0; ++t) {
+        int best = -1;
+        double bd = 1e300;
+#pragma unroll 1
+        for (int j = 0; j < cnt; ++j) {
+          if ((done >> j) & 1ull) continue;
+          const double* ce = a.m.ce + 3 * (size_t)a.cell_elem[beg + j];
+          const double dx = x[0] - ce[0], dy = x[1] - ce[1], dz = x[2] - ce[2];
+          const double d2 = dx * dx + dy * dy + dz * dz;
+          if (d2 < bd) {
+            bd = d2;
+            best = j;
+          }
+        }
+        done |= 1ull << best;
+        const int e = a.cell_elem[beg + best];
+        float guess[3];
+        start_guess<G, false>(a.m, a.k, nullptr, nullptr, e, x, true, guess);
+        double z[3];
+        int i32 = 0, i64 = 0;
+        if (locate_one<G, F64>(a.m, a.k, e, x, guess, z, i32, i64) &&
+            tmax3(z[0], z[1], z[2]) <= 1.0 + a.k.lost_tol) {
+          found = e;
+          xi[0] = z[0];
+          xi[1] = z[1];
+          xi[2] = z[2];
+        }
+      }
+    }
+    a.elem[i] = found;
+    a.xi[i] = xi[0];
+    a.xi[a.n + i] = xi[1];
+    a.xi[2 * a.n + i] = xi[2];
+    if (a.status) a.status[i] = found >= 0 ? 0u : (unsigned)PT_ST_LOST;
   }
 }
 
@@ -984,6 +1049,10 @@ struct Family {
     }
     return 0;
   }
+  static int find(const FindArgs& a, int grid, int block, cudaStream_t s) {
+    k_find<G, F64><<<grid, block, 0, s>>>(a);
+    return (int)cudaGetLastError();
+  }
   static int locate(const LocateArgs& a, int grid, int block, cudaStream_t s) {
     if (kMlp && a.k.guess == PT_GUESS_MLP)
       k_locate<G, F64, kMlp><<<grid, block, 0, s>>>(a);
@@ -1006,5 +1075,8 @@ struct Family {
   int NAME##_occ(int np, int block) { return Family<G, F64>::occ_np(np, block); }            \
   int NAME##_loc(const LocateArgs& a, int grid, int block, void* s) {                        \
     return Family<G, F64>::locate(a, grid, block, (cudaStream_t)s);                          \
+  }                                                                                          \
+  int NAME##_find(const FindArgs& a, int grid, int block, void* s) {                         \
+    return Family<G, F64>::find(a, grid, block, (cudaStream_t)s);                            \
   }                                                                                          \
   }

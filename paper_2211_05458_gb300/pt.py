@@ -37,7 +37,7 @@ class Config(ctypes.Structure):
                 ("max_cross", ctypes.c_int32), ("rebin_every", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("lift", ctypes.c_int32),
                 ("sphericity", ctypes.c_double), ("track", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("buoyancy", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class MeshDesc(ctypes.Structure):
@@ -69,7 +69,7 @@ EXPORTS = ["pt_config_default", "pt_init_mesh", "pt_set_config", "pt_set_fluid",
            "pt_push_host", "pt_deposit", "pt_locate", "pt_mlp_make_pairs", "pt_mlp_train",
            "pt_mlp_features", "pt_mlp_nparams", "pt_mlp_set", "pt_mlp_get", "pt_mlp_forward",
            "pt_mlp_grad", "pt_push_batch", "pt_profile", "pt_profile_read", "pt_destroy",
-           "pt_last_error", "pt_deposit_noalloc"]
+           "pt_last_error", "pt_deposit_noalloc", "pt_find_element"]
 
 
 def library_path() -> str:
@@ -112,6 +112,7 @@ def lib():
             L.pt_push_batch.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(CParticles),
                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                         ctypes.POINTER(Stats)]
+            L.pt_find_element.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp]
             L.pt_profile.argtypes = [_vp, ctypes.c_int32]
             L.pt_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int64)]
@@ -282,6 +283,15 @@ class Context:
         p = parts.struct()
         self._check(lib().pt_deposit(self.h, ctypes.byref(p), int(mode), _ptr(S)))
         return S
+
+    def find_element(self, x: torch.Tensor):
+        """x: [3][n] float64 cuda -> (elem [n] int32, -1 if outside; xi [3][n]; status)."""
+        n = x.shape[1]
+        elem = torch.empty(n, dtype=torch.int32, device=x.device)
+        xi = torch.empty_like(x)
+        st = torch.empty(n, dtype=torch.int32, device=x.device)
+        self._check(lib().pt_find_element(self.h, n, _ptr(x), _ptr(elem), _ptr(xi), _ptr(st)))
+        return elem, xi, st
 
     def locate(self, x: torch.Tensor, elem: torch.Tensor):
         """x: [3][n] float64 cuda, elem: [n] int32 cuda -> (xi [3][n], iters, status)."""

@@ -70,3 +70,21 @@ def test_bad_force_config_is_rejected():
     wl.drag_law = 2
     with pytest.raises(pt.PtError):
         H.gpu_context(wl, "fp32", sphericity=0.0)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_push_with_gravity_and_buoyancy_matches_oracle(precision, tol):
+    """Eq. theory:maxey: gravity on m_p - m_f (g (1 - rho/rho_p), rho interpolated);
+    light particles so that the buoyancy is 10 % of the weight."""
+    wl = W.curved_channel((6, 5, 4), 2, 5, P=400, nsteps=30, dt=2e-3, st=(0.5, 50.0), seed=9,
+                          rho_p=12.0)
+    band = (1e-10, 1e-10) if precision == "fp64" else (2e-4, 1e-4 * 2.0 / 5)
+    cfg = dict(buoyancy=1, g=(0.0, -9.81, 0.0))
+    ctx = H.gpu_context(wl, precision, band_ref=band[0], band_x=band[1], **cfg)
+    parts = H.gpu_particles(wl, ctx)
+    ctx.push(parts, wl.nsteps, wl.dt)
+    o = H.run_oracle(wl, band_ref=band[0], band_x=band[1], **cfg)
+    res = H.compare(H.gpu_result(parts), o, tol)
+    assert res["checked"] >= 350
+    o0 = H.run_oracle(wl, band_ref=band[0], band_x=band[1], g=(0.0, -9.81, 0.0))
+    assert np.max(np.abs(o0["v"] - o["v"])) > 100 * max(tol, 2e-5)
