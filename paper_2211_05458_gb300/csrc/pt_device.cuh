@@ -421,6 +421,114 @@ __device__ __forceinline__ void resid_df(const float* __restrict__ Xh,
   }
 }
 
+// Lagrange basis at z (l) and its increment dl = l(z + dz) - l(z), the latter
+// without cancellation: with f_m = z - x_m and F_m = f_m + dz, the product
+// difference telescopes, prod F - prod f = dz sum_j (prod_{i<j} f_i)(prod_{i>j} F_i),
+// so dl carries the relative accuracy of FP32 however small dz is.
+template <int G>
+__device__ __forceinline__ void lagr_inc(float z, float dz, const float* xn, const float* w,
+                                         float* l, float* dl) {
+  float f[G], F[G];
+#pragma unroll
+  for (int m = 0; m < G; ++m) {
+    f[m] = z - xn[m];
+    F[m] = f[m] + dz;
+  }
+#pragma unroll
+  for (int a = 0; a < G; ++a) {
+    float suf[G], sp = 1.f;
+#pragma unroll
+    for (int m = G - 1; m >= 0; --m) {
+      suf[m] = sp;
+      if (m != a) sp *= F[m];
+    }
+    float pre = 1.f, acc = 0.f;
+#pragma unroll
+    for (int m = 0; m < G; ++m) {
+      if (m == a) continue;
+      acc = fmaf(pre, suf[m], acc);
+      pre *= f[m];
+    }
+    l[a] = w[a] * pre;
+    dl[a] = w[a] * dz * acc;
+  }
+}
+
+// Increment of the element map between two nearby points, dchi = chi(z + dz) -
+// chi(z), in FP32 without cancellation: with L = l + dl the bases at z + dz,
+//   prod L - prod l = dl0 L1 L2 + l0 dl1 L2 + l0 l1 dl2
+// (and likewise for the 8-corner form of trilinear coordinates), so every term
+// carries a factor dl and the result has FP32 relative accuracy.  Used for the
+// second residual of the final Newton iterations: r(z + dz) = r(z) + dchi, with
+// r(z) from the double-float residual.  Nodes: FP32 high parts, relative to the
+// element centre (the low parts change dchi by ~1e-8 of itself).
+template <int G>
+__device__ __forceinline__ void map_inc32(const float* __restrict__ X, const float* z,
+                                          const float* dz, int tm, const DevConsts& k,
+                                          float* dchi) {
+  constexpr int G3 = G * G * G;
+  float l0[G], dl0[G], l1[G], dl1[G], l2[G], dl2[G];
+  lagr_inc<G>(z[0], dz[0], k.gn32, k.gw32, l0, dl0);
+  lagr_inc<G>(z[1], dz[1], k.gn32, k.gw32, l1, dl1);
+  lagr_inc<G>(z[2], dz[2], k.gn32, k.gw32, l2, dl2);
+  float hp[3], hm[3], dh[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    hp[d] = 0.5f * (1.f + z[d]);
+    hm[d] = 0.5f * (1.f - z[d]);
+    dh[d] = 0.5f * dz[d];
+  }
+#pragma unroll 1
+  for (int q = 0; q < 3; ++q) {
+    const float* Xq = X + q * G3;
+    float acc = 0.f;
+    if ((tm >> q) & 1) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float a0 = (c & 1) ? hp[0] : hm[0], a1 = (c & 2) ? hp[1] : hm[1],
+                    a2 = (c & 4) ? hp[2] : hm[2];
+        const float d0 = (c & 1) ? dh[0] : -dh[0], d1 = (c & 2) ? dh[1] : -dh[1],
+                    d2 = (c & 4) ? dh[2] : -dh[2];
+        const float A1 = a1 + d1, A2 = a2 + d2;
+        const float dw = d0 * A1 * A2 + a0 * d1 * A2 + a0 * a1 * d2;
+        acc = fmaf(__ldg(Xq + corner_node<G>(c)), dw, acc);
+      }
+    } else {
+      float t1 = 0.f, t2 = 0.f, t3 = 0.f;
+#pragma unroll 1
+      for (int c = 0; c < G; ++c) {
+        float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+        for (int b = 0; b < G; ++b) {
+          float row[G];
+          load_row<G>(Xq + G * (b + G * c), row);
+          float A = 0.f, B = 0.f;
+#pragma unroll
+          for (int a = 0; a < G; ++a) {
+            A = fmaf(row[a], dl0[a], A);
+            B = fmaf(row[a], l0[a], B);
+          }
+          s1 = fmaf(A, l1[b] + dl1[b], s1);
+          s2 = fmaf(B, dl1[b], s2);
+          s3 = fmaf(B, l1[b], s3);
+        }
+        float lc = l2[0], dc = dl2[0];
+#pragma unroll
+        for (int j = 1; j < G; ++j)
+          if (j == c) {
+            lc = l2[j];
+            dc = dl2[j];
+          }
+        t1 = fmaf(s1, lc + dc, t1);
+        t2 = fmaf(s2, lc + dc, t2);
+        t3 = fmaf(s3, dc, t3);
+      }
+      acc = t1 + t2 + t3;
+    }
+    dchi[q] = acc;
+  }
+}
+
 template <int G>
 __device__ __noinline__ bool newton64_cold(const double* X64, const double* xl, double* xi,
                                            const DevConsts& k, int& it64) {
@@ -465,15 +573,36 @@ __device__ __forceinline__ bool newton_df(const DevMesh& m, const DevConsts& k, 
 #pragma unroll
     for (int q = 0; q < 3; ++q) zd[q] = df_from(z[q]);
     const float tol = (float)k.newton_tol;
-    #pragma unroll 1
+    // Each step needs the residual at the current iterate.  The first is the
+    // double-float residual at the FP32 iterate z.  After a first step d with
+    // |d| <= 4e-7 the next residual is r(z) + [chi(z - d) - chi(z)], the
+    // bracket an exact FP32 increment (it carries ~1e-7 of a term of size
+    // |J d|, far below the tolerance); later residuals are double-float again.
+    float rp[3] = {0.f, 0.f, 0.f}, dz[3] = {0.f, 0.f, 0.f};
+    bool inc = false;
+#pragma unroll 1
     for (int it = 0; it < 6; ++it) {
       float r[3], d[3];
-      resid_df<G>(X32, X32l, zd, tm, xd, k, r);
+      if (inc) {
+        float dchi[3];
+        map_inc32<G>(X32, z, dz, tm, k, dchi);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) r[q] = rp[q] + dchi[q];
+      } else {
+        resid_df<G>(X32, X32l, zd, tm, xd, k, r);
+      }
       matvec3(Ji, r, d);
 #pragma unroll
       for (int q = 0; q < 3; ++q) zd[q] = df_sub(zd[q], df_from(d[q]));
       ++it64;
-      if (tmax3(d[0], d[1], d[2]) < tol) return true;
+      const float md = tmax3(d[0], d[1], d[2]);
+      if (md < tol) return true;
+      inc = it == 0 && md <= 4e-7f;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        rp[q] = r[q];
+        dz[q] = -d[q];
+      }
     }
   }
   // fallback: full FP64 Newton
