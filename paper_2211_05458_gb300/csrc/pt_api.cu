@@ -24,35 +24,46 @@ int fam_g3_fp64_push(int, const PushArgs&, int, int, void*);
 int fam_g3_fp32_push(int, const PushArgs&, int, int, void*);
 int fam_g4_fp64_push(int, const PushArgs&, int, int, void*);
 int fam_g4_fp32_push(int, const PushArgs&, int, int, void*);
+int fam_g5_fp64_push(int, const PushArgs&, int, int, void*);
+int fam_g5_fp32_push(int, const PushArgs&, int, int, void*);
 int fam_g2_fp64_dep(int, int, const DepositArgs&, int, int, void*);
 int fam_g2_fp32_dep(int, int, const DepositArgs&, int, int, void*);
 int fam_g3_fp64_dep(int, int, const DepositArgs&, int, int, void*);
 int fam_g3_fp32_dep(int, int, const DepositArgs&, int, int, void*);
 int fam_g4_fp64_dep(int, int, const DepositArgs&, int, int, void*);
 int fam_g4_fp32_dep(int, int, const DepositArgs&, int, int, void*);
+int fam_g5_fp64_dep(int, int, const DepositArgs&, int, int, void*);
+int fam_g5_fp32_dep(int, int, const DepositArgs&, int, int, void*);
 int fam_g2_fp64_occ(int, int);
 int fam_g2_fp32_occ(int, int);
 int fam_g3_fp64_occ(int, int);
 int fam_g3_fp32_occ(int, int);
 int fam_g4_fp64_occ(int, int);
 int fam_g4_fp32_occ(int, int);
+int fam_g5_fp64_occ(int, int);
+int fam_g5_fp32_occ(int, int);
 int fam_g2_fp64_loc(const LocateArgs&, int, int, void*);
 int fam_g2_fp32_loc(const LocateArgs&, int, int, void*);
 int fam_g3_fp64_loc(const LocateArgs&, int, int, void*);
 int fam_g3_fp32_loc(const LocateArgs&, int, int, void*);
 int fam_g4_fp64_loc(const LocateArgs&, int, int, void*);
 int fam_g4_fp32_loc(const LocateArgs&, int, int, void*);
+int fam_g5_fp64_loc(const LocateArgs&, int, int, void*);
+int fam_g5_fp32_loc(const LocateArgs&, int, int, void*);
 int fam_g2_fp64_find(const FindArgs&, int, int, void*);
 int fam_g2_fp32_find(const FindArgs&, int, int, void*);
 int fam_g3_fp64_find(const FindArgs&, int, int, void*);
 int fam_g3_fp32_find(const FindArgs&, int, int, void*);
 int fam_g4_fp64_find(const FindArgs&, int, int, void*);
 int fam_g4_fp32_find(const FindArgs&, int, int, void*);
+int fam_g5_fp64_find(const FindArgs&, int, int, void*);
+int fam_g5_fp32_find(const FindArgs&, int, int, void*);
 
 #define PT_DISPATCH(g, f64, SUFFIX, ...)                                          \
   ((g) == 2 ? ((f64) ? fam_g2_fp64_##SUFFIX(__VA_ARGS__) : fam_g2_fp32_##SUFFIX(__VA_ARGS__)) \
    : (g) == 3 ? ((f64) ? fam_g3_fp64_##SUFFIX(__VA_ARGS__) : fam_g3_fp32_##SUFFIX(__VA_ARGS__)) \
-   : ((f64) ? fam_g4_fp64_##SUFFIX(__VA_ARGS__) : fam_g4_fp32_##SUFFIX(__VA_ARGS__)))
+   : (g) == 4 ? ((f64) ? fam_g4_fp64_##SUFFIX(__VA_ARGS__) : fam_g4_fp32_##SUFFIX(__VA_ARGS__)) \
+   : ((f64) ? fam_g5_fp64_##SUFFIX(__VA_ARGS__) : fam_g5_fp32_##SUFFIX(__VA_ARGS__)))
 
 int launch_push(int g, bool f64, int np, const PushArgs& a, int grid, int block, void* s) {
   return PT_DISPATCH(g, f64, push, np, a, grid, block, s);
@@ -643,7 +654,7 @@ pt_status pt_init_mesh(pt_ctx** out, const pt_mesh_desc* md, const pt_config* cf
   if (!md || !md->xgeo || !md->neighbor || !md->nbr_face || !md->bc || !md->shift)
     return fail(nullptr, PT_ERR_ARG, "mesh descriptor or one of its arrays is NULL");
   if (md->nelem <= 0) return fail(nullptr, PT_ERR_ARG, "nelem must be > 0");
-  if (md->ngeo < 1 || md->ngeo > 3) return fail(nullptr, PT_ERR_ARG, "ngeo must be 1..3");
+  if (md->ngeo < 1 || md->ngeo > 4) return fail(nullptr, PT_ERR_ARG, "ngeo must be 1..4");
   if (md->nelem > (1 << 28)) return fail(nullptr, PT_ERR_ARG, "nelem too large");
   pt_status s = check_config(cfg);
   if (s) return s;

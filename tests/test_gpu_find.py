@@ -36,7 +36,7 @@ def _check(mesh, precision, pts, xi_tol):
 
 
 @pytest.mark.parametrize("precision,xi_tol", [("fp64", 1e-12), ("fp32", 2e-12)])
-@pytest.mark.parametrize("ngeo", [1, 2, 3])
+@pytest.mark.parametrize("ngeo", [1, 2, 3, 4])
 def test_find_element_curved_channel(precision, xi_tol, ngeo):
     mesh = W.channel_mesh((6, 5, 4), ngeo)
     rng = np.random.default_rng(ngeo)

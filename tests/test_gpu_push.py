@@ -48,7 +48,7 @@ def test_tgv_box_full_config_fp64():
     assert res["checked"] >= 9900
 
 
-@pytest.mark.parametrize("ngeo,N", [(2, 5), (3, 5), (1, 4), (2, 7)])
+@pytest.mark.parametrize("ngeo,N", [(2, 5), (3, 5), (1, 4), (2, 7), (4, 5)])
 def test_curved_channel_fp64_matches_oracle(ngeo, N):
     wl = W.curved_channel((6, 6, 6), ngeo, N, P=400, nsteps=40, dt=2e-3, st=(0.1, 100.0))
     _speed_up(wl)
@@ -57,7 +57,7 @@ def test_curved_channel_fp64_matches_oracle(ngeo, N):
     assert res["stats"]["wall_hits"] >= 1
 
 
-@pytest.mark.parametrize("ngeo,N", [(2, 5), (3, 5)])
+@pytest.mark.parametrize("ngeo,N", [(2, 5), (3, 5), (4, 5)])
 def test_curved_channel_fp32_matches_oracle(ngeo, N):
     wl = W.curved_channel((6, 6, 6), ngeo, N, P=400, nsteps=40, dt=2e-3)
     _speed_up(wl)
