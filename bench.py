@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / fp64 / cpu legs")
     ap.add_argument("--extras", default="trilinear,reference,e2e,fp64,cpu",
                     help="comma list of extra legs to run (trilinear, reference, e2e, fp64, cpu)")
+    ap.add_argument("--config", default="c3", choices=["c1", "c2", "c3", "c4", "c5"],
+                    help="c3 (default): the learned-start 64^3 channel; c1: 8^3 TGV box FP64; "
+                         "c2: 32^3 NGeo=2 channel FP64; c4: 128 batched boxes FP32; "
+                         "c5: 128x64x64 N=7 two-way channel FP32 with deposition")
     return ap.parse_args()
 
 
@@ -203,6 +207,146 @@ class OracleSample:
         return sample_particles * sample_steps / dt, self.threads, dt
 
 
+def fp64_peak_tflops(clk_max_mhz=2070.0, sms=152, dfma_per_clk=2):
+    return sms * dfma_per_clk * 2 * clk_max_mhz * 1e6 / 1e12
+
+
+def config_workloads(cfg, dev, seed):
+    """The workloads other than the default one (seeded, synthetic)."""
+    from paper_2211_05458_gb300 import workloads as W
+    if cfg == "c1":
+        return [W.tgv_box(8, 3, P=10_000, nsteps=100, seed=seed, device=dev)]
+    if cfg == "c2":
+        return [W.curved_channel((32, 32, 32), 2, 5, P=1_000_000, nsteps=200, seed=seed,
+                                 device=dev)]
+    if cfg == "c4":
+        return W.batched_boxes(nbox=128, seed=1 + seed, device=dev, nsteps=50)
+    if cfg == "c5":
+        return [W.curved_channel((128, 64, 64), 2, 7, P=20_000_000, nsteps=50, seed=seed,
+                                 device=dev, mass_loading=0.3)]
+    raise ValueError(cfg)
+
+
+def run_config(args):
+    """--config c1|c2|c4|c5: one JSON line for that workload (same schema)."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2211_05458_gb300 import pt
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    cfg = args.config
+    wls = config_workloads(cfg, dev, rank)
+    f64 = cfg in ("c1", "c2")
+    prec = pt.FP64 if f64 else pt.FP32
+    dt_ = torch.float64 if f64 else torch.float32
+    ctxs, parts = [], []
+    for wl in wls:
+        c = pt.Context(wl.mesh, stream=stream, precision=prec, mu=wl.mu, rho_p=wl.rho_p,
+                       drag_law=wl.drag_law, rebin_every=args.inner)
+        c.set_fluid(wl.N, wl.node_type, wl.U.to(dt_).contiguous())
+        ctxs.append(c)
+        parts.append(pt.ParticleSet.create(wl.x, wl.v, wl.d, wl.elem, prec, dev))
+    P = sum(p.n for p in parts)
+    dt = wls[0].dt
+    inner = 50 if cfg == "c4" else args.inner
+    S = None
+    if cfg == "c5":
+        n3 = (wls[0].N + 1) ** 3
+        S = torch.empty((wls[0].mesh.nelem, 4, n3), dtype=torch.float32, device=dev)
+    dep_ev = []
+
+    def step():
+        if cfg == "c4":
+            pt.push_batch(ctxs, parts, inner, dt, stats=False)
+        else:
+            ctxs[0].push(parts[0], inner, dt, stats=False)
+        if S is not None:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctxs[0].deposit(parts[0], pt.DEPOSIT_SEGMENTED, S)
+            e1.record(stream)
+            dep_ev.append((e0, e1))
+
+    warm = max(args.warmup, 3)  # the batched push tunes, then captures its graph
+    for _ in range(warm):
+        step()
+    torch.cuda.synchronize()
+    dep_ev.clear()
+    with ClockSampler(local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    ms = reduce_time_ms(ev0.elapsed_time(ev1), world, dev)
+    value = P * inner * args.steps * world / (ms / 1e3)
+    wl0 = wls[0]
+    G, NP = wl0.mesh.ngeo + 1, wl0.N + 1
+    flops = algorithmic_flops_per_particle_stage(G=G, NP=NP, ntri=3 if G == 2 else 2)
+    if f64:
+        # FP64 mode: the same operation count in FP64, against the FP64 rate
+        peak = fp64_peak_tflops()
+        peak_kind = "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz"
+    else:
+        peak = fp32_peak_tflops()
+        peak_kind = "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+    achieved = flops * 5 * value / world / 1e12
+    names = {"c1": "TGV box 8^3 NGeo=1 N=3 Gauss, 10^4 particles, Stokes, FP64",
+             "c2": "curved channel 32^3 NGeo=2 N=5 Gauss, 10^6 particles, Schiller-Naumann, FP64",
+             "c4": f"128 periodic TGV boxes (sides 8..40, N 3..7, {P} particles), FP32, "
+                   "graph of 50 steps",
+             "c5": "two-way channel 128x64x64 NGeo=2 N=7, 2x10^7 particles, FP32, push of "
+                   f"{inner} steps + segmented deposition"}
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": warm, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if f64 else "f32", "data": "synthetic",
+            "config": {"workload": names[cfg], "inner_steps_per_call": inner,
+                       "parallelism": f"weak, {world} independent GPU(s)"},
+            "gpu_launches": None, "clocks": clk.summary(),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "whole step",
+                         "peak_kind": peak_kind, "flops_per_particle_stage": flops}}
+    if dep_ev:
+        dep_ms = sum(a.elapsed_time(b) for a, b in dep_ev) / len(dep_ev)
+        Sbytes = S.numel() * 4
+        line["deposit"] = {"ms": dep_ms, "share_of_step": dep_ms / (ms / args.steps),
+                           "S_bytes": Sbytes, "S_write_gbs": Sbytes / (dep_ms / 1e3) / 1e9}
+    if rank == 0 and not args.no_extras:
+        try:
+            samp = {"c1": (2000, 5), "c2": (2000, 2), "c4": (2000, 2), "c5": (2000, 1)}[cfg]
+            wl_s = max(wls, key=lambda w: w.x.shape[0]) if cfg == "c4" else wl0
+            wl_s.U = wl_s.U.cpu()
+            wl_s.x, wl_s.v, wl_s.d, wl_s.elem = (wl_s.x.cpu(), wl_s.v.cpu(), wl_s.d.cpu(),
+                                                 wl_s.elem.cpu())
+            n_s = min(samp[0], wl_s.x.shape[0])
+            rate, threads, _ = OracleSample(wl_s).run(n_s, samp[1])
+            rate1, _, _ = OracleSample(wl_s, max_threads=1).run(max(n_s // 8, 1), samp[1])
+            line["cpu_baseline"] = {"value": rate, "unit": METRIC, "cores": threads,
+                                    "kind": "oracle", "single_thread": rate1,
+                                    "sample": f"{n_s} particles x {samp[1]} time steps"
+                                              + (" of the largest box" if cfg == "c4" else "")}
+        except Exception as e:  # pragma: no cover
+            line["cpu_baseline"] = {"unavailable": str(e)[:200]}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle on the host cores, same workload/metric."""
     rank, world, _ = dist_env()
@@ -239,6 +383,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config != "c3":
+        return run_config(args)
     import torch
     import torch.distributed as dist
 
