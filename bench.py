@@ -145,19 +145,25 @@ def make_workload(args, device, seed, precision):
 TRAFFIC_BYTES_PER_PARTICLE_STEP = 353.0
 
 
-def algorithmic_flops_per_particle_stage(G=4, NP=6, ntri=2):
-    """FP32 flops (FMA = 2) of one particle-stage of the FP32-mode push as the
-    method prescribes it: trilinear start, 2 FP32 Newton iterations (chi and J),
-    2 double-float residual iterations, interpolation of 4 conserved variables,
-    drag + RK + slab test.  ntri of the 3 coordinates are trilinear in xi."""
+def algorithmic_flops_per_particle_stage(G=4, NP=6, ntri=2, it_full=2.0, it_resid=2.0):
+    """Flops of one particle-stage as the method prescribes them (a multiply-add
+    is 2 flops whatever precision or emulation carries it out): the trilinear
+    start; it_full Newton iterations that evaluate chi and J (the FP32
+    iterations of the FP32 mode, every iteration of the FP64 mode) and it_resid
+    iterations that need the residual only (the final iterations of the FP32
+    mode), each sum-factorised, ntri of the 3 coordinates in 8-corner trilinear
+    form; interpolation of 4 variables; drag, RK update and the 6 slab tests.
+    The double-float emulation and the learned start are not counted."""
     full = 3 - ntri
-    basis_d = 3 * (G + 10 * G)                       # Lagrange values + derivatives
-    newton32 = basis_d + full * (4 * G ** 3 + 6 * G ** 2 + 8 * G) + ntri * 104 + 12 + 60 + 24
-    basis_df = 3 * (11 * G + 7 * (3 * G - 1))
-    resid_df = basis_df + 150 + full * (12 * G ** 3 + 18 * G ** 2 + 18 * G) + ntri * 96 + 84
-    interp = 3 * 4 * NP + 4 * 2 * (NP ** 3 + NP ** 2 + NP)
-    misc = 21 + 180
-    return 2 * newton32 + 2 * resid_df + interp + misc
+    basis_d = 3 * 6 * G                                   # product-form values + derivatives
+    basis = 3 * 4 * G
+    map_j = full * 2 * (2 * G ** 3 + 3 * G ** 2 + 4 * G) + ntri * 64
+    map_v = full * 2 * (G ** 3 + G ** 2 + G) + ntri * 32
+    newton_full = basis_d + map_j + 74                    # + 3x3 inverse, product, update
+    newton_resid = basis + map_v + 24
+    interp = 3 * 5 * NP + 4 * 2 * (NP ** 3 + NP ** 2 + NP)
+    misc = 30 + 30 + 24 + 48                              # start, drag, RK, slabs
+    return int(round(it_full * newton_full + it_resid * newton_resid + interp + misc))
 
 
 def fp32_peak_tflops(clk_max_mhz=2070.0, sms=152, lanes=128):
@@ -295,7 +301,21 @@ def run_config(args):
     value = P * inner * args.steps * world / (ms / 1e3)
     wl0 = wls[0]
     G, NP = wl0.mesh.ngeo + 1, wl0.N + 1
-    flops = algorithmic_flops_per_particle_stage(G=G, NP=NP, ntri=3 if G == 2 else 2)
+    # measured Newton iterations per particle-stage, from one more step with counters
+    if cfg == "c4":
+        sts = pt.push_batch(ctxs, parts, 1, dt, stats=True)
+        st = {k: sum(x[k] for x in sts) for k in ("particle_steps", "newton_it_fp32",
+                                                    "newton_it_fp64")}
+    else:
+        st = ctxs[0].push(parts[0], 1, dt, stats=True)
+    nps = max(st["particle_steps"], 1) * 5
+    it32, it64 = st["newton_it_fp32"] / nps, st["newton_it_fp64"] / nps
+    if f64:
+        flops = algorithmic_flops_per_particle_stage(G=G, NP=NP, ntri=3 if G == 2 else 2,
+                                                     it_full=it64, it_resid=0.0)
+    else:
+        flops = algorithmic_flops_per_particle_stage(G=G, NP=NP, ntri=3 if G == 2 else 2,
+                                                     it_full=it32, it_resid=it64)
     if f64:
         # FP64 mode: the same operation count in FP64, against the FP64 rate
         peak = fp64_peak_tflops()
@@ -319,7 +339,9 @@ def run_config(args):
             "gpu_launches": None, "clocks": clk.summary(),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "whole step",
-                         "peak_kind": peak_kind, "flops_per_particle_stage": flops}}
+                         "peak_kind": peak_kind, "flops_per_particle_stage": flops,
+                         "newton_iterations_per_stage": {"full": it64 if f64 else it32,
+                                                         "residual_only": 0.0 if f64 else it64}}}
     if dep_ev:
         dep_ms = sum(a.elapsed_time(b) for a, b in dep_ev) / len(dep_ev)
         Sbytes = S.numel() * 4
@@ -451,7 +473,10 @@ def main():
 
     # roofline of the dominant kernel (k_push): it is bound by FP32 arithmetic and
     # issue latency, not by memory (DRAM traffic is a few percent of peak)
-    flops_stage = algorithmic_flops_per_particle_stage(G=4, NP=wl.N + 1, ntri=2)
+    nps = max(stats["particle_steps"], 1) * 5
+    it32, it64 = stats["newton_it_fp32"] / nps, stats["newton_it_fp64"] / nps
+    flops_stage = algorithmic_flops_per_particle_stage(G=4, NP=wl.N + 1, ntri=2, it_full=it32,
+                                                       it_resid=it64)
     avg_launch_s = (kern_ms / 1e3) / max(launches, 1)
     flops_launch = flops_stage * 5 * args.inner * P
     achieved = flops_launch / avg_launch_s / 1e12
@@ -462,6 +487,7 @@ def main():
                 "kernel": "k_push<4,6,fp32,%s>" % ("learned" if guess else "trilinear"),
                 "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                 "flops_per_particle_stage": flops_stage,
+                "newton_iterations_per_stage": {"full": it32, "residual_only": it64},
                 "launch_ms": avg_launch_s * 1e3,
                 "kernel_share_of_step": (kern_ms / ms) if ms > 0 else None,
                 "hbm_frac_of_measured": (TRAFFIC_BYTES_PER_PARTICLE_STEP * P * args.inner

@@ -71,8 +71,13 @@ __global__ void k_scatter_batch(const BatchArgs a, int* cursor, int* perm) {
 
 constexpr int kMaxBoxCounters = 256;
 
+// the boxes are straight-sided (NGeo = 1): a smaller kernel, for which 3
+// resident blocks per SM (168 registers) measured faster than 2
+#ifndef PT_BATCH_MINB
+#define PT_BATCH_MINB 3
+#endif
 template <int G>
-__global__ void __launch_bounds__(128, PT_PUSH_MINB) k_push_batch(const BatchArgs a) {
+__global__ void __launch_bounds__(128, PT_BATCH_MINB) k_push_batch(const BatchArgs a) {
   __shared__ unsigned long long sc[kMaxBoxCounters][6];
   for (int i = threadIdx.x; i < kMaxBoxCounters * 6; i += blockDim.x) (&sc[0][0])[i] = 0ull;
   __syncthreads();

@@ -6,10 +6,11 @@
 #include "pt_mlp_infer.cuh"
 
 // minimum resident blocks of 128 threads per SM for the push kernel (sets the
-// register budget: 3 -> 168 registers per thread, 2 -> 255); the FP64 mode
-// keeps the larger budget
+// register budget: 2 -> 255 registers per thread, 3 -> 168, 4 -> 128).  At the
+// 64^3 NGeo=3 workload 2 measured best (FP32: +1-2 % over 3, 3 +8-14 % over 4):
+// spills cost more than the lower occupancy
 #ifndef PT_PUSH_MINB
-#define PT_PUSH_MINB 3
+#define PT_PUSH_MINB 2
 #endif
 #define PT_PUSH_MINB_F64 2
 
