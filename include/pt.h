@@ -222,7 +222,9 @@ pt_status pt_push_host(pt_ctx* ctx, const pt_particles* p_host, int32_t nsteps, 
  * of the element volume (the paper's projection operator).  Summation:
  * PT_DEPOSIT_ATOMIC adds with FP32 atomics (order-dependent rounding);
  * PT_DEPOSIT_SEGMENTED sums each element's particles in index order (bitwise
- * reproducible).  Other mode bits: PT_ERR_ARG. */
+ * reproducible); it first computes every particle's source into a library-
+ * owned device buffer of 32 bytes per particle (grown on demand, released by
+ * pt_destroy), then reduces per element.  Other mode bits: PT_ERR_ARG. */
 pt_status pt_deposit(pt_ctx* ctx, const pt_particles* p, int32_t mode, float* S_dev);
 
 /* pt_deposit without any device allocation (the paper has no counterpart).

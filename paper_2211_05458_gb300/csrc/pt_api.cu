@@ -889,6 +889,7 @@ pt_status pt_push_host(pt_ctx* c, const pt_particles* h, int32_t nsteps, double 
   const size_t bytes = n * (24 + 3 * rs + rs + 12);
   if (c->stage_bytes < bytes) {
     if (c->d_stage) cudaFree(c->d_stage);
+  if (c->d_src) cudaFree(c->d_src);
     c->d_stage = nullptr;
     CK(cudaMalloc(&c->d_stage, std::max<size_t>(bytes, 64) + 256));
     c->stage_bytes = bytes;
@@ -978,7 +979,19 @@ pt_status pt_deposit(pt_ctx* c, const pt_particles* p, int32_t mode, float* S) {
   a.perm = c->d_perm;
   a.offs = offs;
   a.S = S;
+  a.src = nullptr;
   const bool f64 = c->cfg.precision == PT_FP64;
+  if (mode & PT_DEPOSIT_SEGMENTED) {
+    // two passes: the sources of all particles, then the per-element sums
+    if (c->src_cap < n) {
+      if (c->d_src) cudaFree(c->d_src);
+      c->d_src = nullptr;
+      c->src_cap = 0;
+      CK(cudaMalloc(&c->d_src, sizeof(float4) * 2 * std::max<int64_t>(n, 1)));
+      c->src_cap = n;
+    }
+    a.src = c->d_src;
+  }
   if (!(mode & PT_DEPOSIT_SEGMENTED)) {
     CK(cudaMemsetAsync(S, 0, sizeof(float) * 4 * n3 * c->nelem, c->stream));
     if (n == 0) return PT_OK;
@@ -986,7 +999,7 @@ pt_status pt_deposit(pt_ctx* c, const pt_particles* p, int32_t mode, float* S) {
     rc = launch_deposit(c->g, f64, np, mode, a, grid, 128, c->stream);
   } else {
     int grid = std::min(c->nelem, c->nsm * 32);
-    rc = launch_deposit(c->g, f64, np, mode, a, grid, 256, c->stream);
+    rc = launch_deposit(c->g, f64, np, mode | 4, a, grid, 256, c->stream);
   }
   if (rc) return fail(c, PT_ERR_CUDA, "deposit launch: %s", cudaGetErrorString((cudaError_t)rc));
   return PT_OK;
@@ -1158,6 +1171,7 @@ pt_status pt_destroy(pt_ctx* c) {
   if (c->d_scratch) cudaFree(c->d_scratch);
   if (c->d_perm) cudaFree(c->d_perm);
   if (c->d_stage) cudaFree(c->d_stage);
+  if (c->d_src) cudaFree(c->d_src);
   pt_mlp_release(c);
   pt_batch_release(c);
   delete c;

@@ -44,6 +44,9 @@ struct pt_ctx {
   int64_t perm_cap = 0;
   void* d_stage = nullptr;
   size_t stage_bytes = 0;
+  // per-particle sources of the two-pass segmented deposition
+  float4* d_src = nullptr;
+  int64_t src_cap = 0;
   // learned guess
   pt_mlp_state* mlp = nullptr;
   bool mlp_ready = false;

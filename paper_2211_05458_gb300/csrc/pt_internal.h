@@ -133,6 +133,7 @@ struct DepositArgs {
   const int* perm;        // sorted order (segmented mode)
   const int* offs;        // [E+1] element segment offsets (segmented mode)
   float* S;               // [E][4][n^3]
+  float4* src;            // [2 n] per-particle sources of the two-pass segmented mode
 };
 
 // kernel entry points, one family per (g, mode) translation unit

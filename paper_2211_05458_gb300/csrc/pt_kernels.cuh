@@ -791,7 +791,7 @@ __global__ void __launch_bounds__(128) k_find(const __grid_constant__ FindArgs a
 template <int G, int NP, bool F64, bool NEAR>
 __device__ __forceinline__ bool particle_source(const DepositArgs& a, int64_t ip, int& e,
                                                 float* f, float* l1, float* l2, float* l3,
-                                                int* node) {
+                                                int* node, float* xi_out = nullptr) {
   using R = typename RealOf<F64>::type;
   constexpr int N3 = NP * NP * NP;
   const int64_t n = a.p.n;
@@ -810,6 +810,11 @@ __device__ __forceinline__ bool particle_source(const DepositArgs& a, int64_t ip
   double xi[3];
   int i32 = 0, i64 = 0;
   if (!locate_one<G, F64>(a.m, a.k, e, x, guess, xi, i32, i64)) return false;
+  if (xi_out) {
+    xi_out[0] = (float)xi[0];
+    xi_out[1] = (float)xi[1];
+    xi_out[2] = (float)xi[2];
+  }
   R lr1[NP], lr2[NP], lr3[NP], Uv[4];
   lagr<NP, R>((R)xi[0], Nodes<R>::sol(a.k), Nodes<R>::solw(a.k), lr1);
   lagr<NP, R>((R)xi[1], Nodes<R>::sol(a.k), Nodes<R>::solw(a.k), lr2);
@@ -983,6 +988,113 @@ __global__ void __launch_bounds__(256) k_deposit_segmented(const DepositArgs a) 
   }
 }
 
+// Two-pass deterministic deposition.  Pass 1: one thread per particle (in the
+// element-sorted order t) computes its source and writes src[2t] = f (or f/V),
+// src[2t+1] = (xi, flag): flag 1 live, 0 skipped; for the nearest-node
+// projection the node index instead, -1 when skipped.  All threads do the
+// expensive part (inverse map, interpolation, drag) instead of one per
+// particle of the element being reduced.
+template <int G, int NP, bool F64, bool NEAR>
+__global__ void __launch_bounds__(128) k_deposit_src(const DepositArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.p.n; t += stride) {
+    const int64_t ip = a.perm[t];
+    int e, node;
+    float f[4], l1[NP], l2[NP], l3[NP], xi[3] = {0.f, 0.f, 0.f};
+    const bool ok = particle_source<G, NP, F64, NEAR>(a, ip, e, f, l1, l2, l3, &node, xi);
+    float4 w0 = make_float4(0.f, 0.f, 0.f, 0.f), w1 = make_float4(xi[0], xi[1], xi[2], 0.f);
+    if (ok) w0 = make_float4(f[0], f[1], f[2], f[3]);
+    if (NEAR)
+      w1.w = __int_as_float(ok ? node : -1);
+    else
+      w1.w = ok ? 1.f : 0.f;
+    a.src[2 * t] = w0;
+    a.src[2 * t + 1] = w1;
+  }
+}
+
+// Pass 2: one block per element.  The element's particles are taken in index
+// order (so the sums are bitwise reproducible), CH at a time; each particle's
+// weights are staged as the two factors of S[q][i,j,k] = sum_p (f_q l_k)(l_i l_j):
+// A[p][q NP + k] = f_q l3_k and B[p][i + NP j] = l1_i l2_j, so every output
+// needs two shared loads and one FMA per particle.  Nearest-node projection:
+// each output adds the densities of the particles whose node it is.
+template <int NP, bool NEAR>
+__global__ void __launch_bounds__(256) k_deposit_seg2(const DepositArgs a) {
+  constexpr int N3 = NP * NP * NP;
+  constexpr int CH = 64;
+  constexpr int NO = (4 * N3 + 255) / 256;
+  __shared__ int idx[CH];
+  __shared__ float sA[CH][4 * NP];
+  __shared__ float sB[CH][NP * NP];
+  __shared__ int snode[CH];
+  for (int e = blockIdx.x; e < a.m.nelem; e += gridDim.x) {
+    const int beg = a.offs[e], end = a.offs[e + 1];
+    const int total = end - beg;
+    float acc[NO];
+#pragma unroll
+    for (int r = 0; r < NO; ++r) acc[r] = 0.f;
+    for (int base = 0; base < total; base += CH) {
+      const int cnt = min(CH, total - base);
+      __syncthreads();
+      for (int j = threadIdx.x; j < total; j += blockDim.x) {
+        const int my = a.perm[beg + j];
+        int rank = 0;
+        for (int q = 0; q < total; ++q) rank += a.perm[beg + q] < my;
+        if (rank >= base && rank < base + CH) idx[rank - base] = beg + j;
+      }
+      __syncthreads();
+      if (threadIdx.x < cnt) {
+        const int t = idx[threadIdx.x];
+        const float4 w0 = a.src[2 * (int64_t)t], w1 = a.src[2 * (int64_t)t + 1];
+        const float f[4] = {w0.x, w0.y, w0.z, w0.w};
+        if (NEAR) {
+          snode[threadIdx.x] = __float_as_int(w1.w);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) sA[threadIdx.x][q] = f[q];
+        } else {
+          const bool ok = w1.w != 0.f;
+          float l1[NP], l2[NP], l3[NP];
+          lagr<NP, float>(w1.x, a.k.sn32, a.k.sw32, l1);
+          lagr<NP, float>(w1.y, a.k.sn32, a.k.sw32, l2);
+          lagr<NP, float>(w1.z, a.k.sn32, a.k.sw32, l3);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < NP; ++k) sA[threadIdx.x][q * NP + k] = ok ? f[q] * l3[k] : 0.f;
+#pragma unroll
+          for (int j = 0; j < NP; ++j)
+#pragma unroll
+            for (int i = 0; i < NP; ++i) sB[threadIdx.x][i + NP * j] = l1[i] * l2[j];
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < NO; ++r) {
+        const int o = threadIdx.x + 256 * r;
+        if (o < 4 * N3) {
+          const int q = o / N3, node = o - q * N3;
+          float sacc = acc[r];
+          if (NEAR) {
+            for (int p = 0; p < cnt; ++p)
+              if (snode[p] == node) sacc += sA[p][q];
+          } else {
+            const int row = q * NP + node / (NP * NP), col = node % (NP * NP);
+            for (int p = 0; p < cnt; ++p) sacc = fmaf(sA[p][row], sB[p][col], sacc);
+          }
+          acc[r] = sacc;
+        }
+      }
+    }
+    float* Se = a.S + (size_t)e * 4 * N3;
+#pragma unroll
+    for (int r = 0; r < NO; ++r) {
+      const int o = threadIdx.x + 256 * r;
+      if (o < 4 * N3) Se[o] = acc[r];
+    }
+  }
+}
+
 // launch helpers for one (G, mode) family
 template <int G, bool F64>
 struct Family {
@@ -1004,6 +1116,22 @@ struct Family {
       case 1: k_deposit_segmented<G, NP, F64, false><<<grid, 256, 0, s>>>(a); break;
       case 2: k_deposit_atomic<G, NP, F64, true><<<grid, block, 0, s>>>(a); break;
       case 3: k_deposit_segmented<G, NP, F64, true><<<grid, 256, 0, s>>>(a); break;
+      // bit 2: two-pass segmented summation with the sources in a.src
+      case 5:
+      case 7: {
+        const int g1 = (int)std::min<int64_t>((a.p.n + 127) / 128, (int64_t)grid * 8);
+        if (a.p.n > 0) {
+          if (mode == 5)
+            k_deposit_src<G, NP, F64, false><<<std::max(g1, 1), 128, 0, s>>>(a);
+          else
+            k_deposit_src<G, NP, F64, true><<<std::max(g1, 1), 128, 0, s>>>(a);
+        }
+        if (mode == 5)
+          k_deposit_seg2<NP, false><<<grid, 256, 0, s>>>(a);
+        else
+          k_deposit_seg2<NP, true><<<grid, 256, 0, s>>>(a);
+        break;
+      }
       default: return (int)cudaErrorInvalidValue;
     }
     return (int)cudaGetLastError();
