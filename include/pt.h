@@ -124,7 +124,11 @@ typedef struct {
   int32_t buoyancy;     /* 1: gravity acts on m_p - m_f, i.e. g (1 - rho/rho_p)
                            with the interpolated fluid density (Eq. theory:maxey);
                            0: g acts on m_p alone (default 0)                     */
-  int32_t reserved[4];
+  int32_t curved_faces; /* intersection with curved faces (Sec. 3.2.4): 0 Newton from
+                           the roots of the face's bilinear patch (default; a
+                           crossing it misses is found by the walk after the
+                           stage); 1 Bezier clipping of the face's control net   */
+  int32_t reserved[3];
 } pt_config;
 
 /* Particles, structure of arrays, all device memory, caller-owned, updated in

@@ -527,6 +527,11 @@ static void fill_consts(const pt_ctx* c, DevConsts& k) {
   double gn[PT_MAXG], gw[PT_MAXG];
   for (int a = 0; a < c->g; ++a) gn[a] = c->g > 1 ? -1.0 + 2.0 * a / (c->g - 1) : 0.0;
   bary(c->g, gn, gw);
+  {
+    std::vector<double> M;
+    bezier_matrix(c->g, M);
+    for (int q = 0; q < c->g * c->g; ++q) k.gbz[q] = M[q];
+  }
   for (int a = 0; a < c->g; ++a) {
     k.gn[a] = gn[a];
     k.gw[a] = gw[a];
@@ -564,6 +569,7 @@ static void fill_consts(const pt_ctx* c, DevConsts& k) {
   k.lift = c->cfg.lift;
   k.track = c->cfg.track;
   k.buoyancy = c->cfg.buoyancy;
+  k.curved_clip = c->cfg.curved_faces;
   {
     // Haider & Levenspiel (1989) fits in the sphericity
     const double f = c->cfg.sphericity;
@@ -610,6 +616,8 @@ static pt_status check_config(const pt_config* cfg) {
       !(cfg->sphericity > 0.0 && cfg->sphericity <= 1.0))
     return fail(nullptr, PT_ERR_ARG, "sphericity must be in (0, 1]");
   if (cfg->lift != 0 && cfg->lift != 1) return fail(nullptr, PT_ERR_ARG, "lift must be 0 or 1");
+  if (cfg->curved_faces != 0 && cfg->curved_faces != 1)
+    return fail(nullptr, PT_ERR_ARG, "curved_faces must be 0 or 1");
   if (cfg->buoyancy != 0 && cfg->buoyancy != 1)
     return fail(nullptr, PT_ERR_ARG, "buoyancy must be 0 or 1");
   if (cfg->track != PT_TRACK_PHYSICAL && cfg->track != PT_TRACK_REFERENCE)

@@ -1044,6 +1044,209 @@ __device__ __forceinline__ bool curved_refine(const double* X64, const float* __
   return false;
 }
 
+// ---------------------------------------------------------------------------
+// Bezier clipping (Sec. 3.2.4; Nishita, Sederberg & Kakimoto 1990)
+// ---------------------------------------------------------------------------
+
+// x-range where the convex hull of the points (x_i, y_i) meets y = 0: the hull
+// meets the axis exactly where some segment between two of its points does.
+__device__ __forceinline__ bool hull_axis(const double* x, const double* y, int n, double& lo,
+                                          double& hi) {
+  lo = 1e300;
+  hi = -1e300;
+  for (int i = 0; i < n; ++i) {
+    if (y[i] == 0.0) {
+      lo = fmin(lo, x[i]);
+      hi = fmax(hi, x[i]);
+    }
+    for (int j = i + 1; j < n; ++j)
+      if ((y[i] < 0.0 && y[j] > 0.0) || (y[i] > 0.0 && y[j] < 0.0)) {
+        const double xc = x[i] + (x[j] - x[i]) * (y[i] / (y[i] - y[j]));
+        lo = fmin(lo, xc);
+        hi = fmax(hi, xc);
+      }
+  }
+  return lo <= hi;
+}
+
+// Control values of a tensor Bernstein polynomial restricted to [a, b] in its
+// first (dir 0) or second (dir 1) parameter, by two de Casteljau splits.
+template <int G>
+__device__ __forceinline__ void bz_restrict(double (&D)[G][G], int dir, double a, double b) {
+  for (int l = 0; l < G; ++l) {
+    double c[G];
+    for (int i = 0; i < G; ++i) c[i] = dir == 0 ? D[i][l] : D[l][i];
+    // [0, b]: the left control points of the split at b
+    double w[G], left[G];
+    for (int i = 0; i < G; ++i) w[i] = c[i];
+    for (int r = 0; r < G; ++r) {
+      left[r] = w[0];
+      for (int i = 0; i + 1 < G - r; ++i) w[i] = (1.0 - b) * w[i] + b * w[i + 1];
+    }
+    // [a/b, 1] of that: the right control points of the split at a/b
+    const double t = b > 0.0 ? a / b : 0.0;
+    for (int i = 0; i < G; ++i) w[i] = left[i];
+    for (int r = 0; r < G; ++r) {
+      c[G - 1 - r] = w[G - 1 - r];
+      for (int i = 0; i + 1 < G - r; ++i) w[i] = (1.0 - t) * w[i] + t * w[i + 1];
+    }
+    for (int i = 0; i < G; ++i) {
+      if (dir == 0)
+        D[i][l] = c[i];
+      else
+        D[l][i] = c[i];
+    }
+  }
+}
+
+// Interval of the first (dir 0) or second (dir 1) parameter in [0, 1] outside
+// which the Bernstein polynomial with control values D has no zero.
+template <int G>
+__device__ __forceinline__ bool bz_clip(const double (&D)[G][G], int dir, double& lo,
+                                        double& hi) {
+  double x[2 * G], y[2 * G];
+  for (int i = 0; i < G; ++i) {
+    double mn = 1e300, mx = -1e300;
+    for (int l = 0; l < G; ++l) {
+      const double v = dir == 0 ? D[i][l] : D[l][i];
+      mn = fmin(mn, v);
+      mx = fmax(mx, v);
+    }
+    x[2 * i] = x[2 * i + 1] = G > 1 ? (double)i / (G - 1) : 0.0;
+    y[2 * i] = mn;
+    y[2 * i + 1] = mx;
+  }
+  if (!hull_axis(x, y, 2 * G, lo, hi)) return false;
+  lo = fmax(0.0, lo - 1e-12);
+  hi = fmin(1.0, hi + 1e-12);
+  return lo <= hi;
+}
+
+// All crossings of the line xs + alpha td (frame n1, n2 normal to td) with a
+// curved face, by Bezier clipping: the face's control net is projected on the
+// two planes through the line, and the parameter domain is cut to where the
+// convex hulls of both projections can vanish, in s and in t; a domain whose
+// area does not at least halve is split in two, and pending domains wait on a
+// stack of parameter boxes (their nets are restricted again from the face's).
+// A domain below 1e-9 gives a candidate, refined by curved_refine (kept as it
+// is if the refinement does not settle).  Writes up to maxr (s, t, alpha) with
+// s, t in [-1, 1]; returns their number.
+template <int G>
+__device__ __noinline__ int bezier_clip_roots(const double* X64, const float* X32, int f,
+                                              const double* xs, const double* td,
+                                              const double* n1, const double* n2,
+                                              const DevConsts& k, double L, double* rs,
+                                              double* rt, double* ra, int maxr) {
+  constexpr int kStack = 64;
+  double full[2][G][G];
+  int base, sm, sk;
+  face_strides<G>(f, base, sm, sk);
+  for (int i = 0; i < G; ++i)
+    for (int j = 0; j < G; ++j) {
+      double c[3] = {0.0, 0.0, 0.0};
+      for (int mm = 0; mm < G; ++mm)
+        for (int kk = 0; kk < G; ++kk) {
+          const double w = k.gbz[i * G + mm] * k.gbz[j * G + kk];
+          const double* P = X64 + 3 * (base + mm * sm + kk * sk);
+          for (int r = 0; r < 3; ++r) c[r] = fma(w, __ldg(P + r), c[r]);
+        }
+      const double q[3] = {c[0] - xs[0], c[1] - xs[1], c[2] - xs[2]};
+      full[0][i][j] = n1[0] * q[0] + n1[1] * q[1] + n1[2] * q[2];
+      full[1][i][j] = n2[0] * q[0] + n2[1] * q[1] + n2[2] * q[2];
+    }
+  double box[kStack][4];
+  box[0][0] = 0.0;
+  box[0][1] = 1.0;
+  box[0][2] = 0.0;
+  box[0][3] = 1.0;
+  int top = 1, nr = 0;
+#pragma unroll 1
+  for (int visit = 0; visit < 600 && top > 0; ++visit) {
+    --top;
+    double u0 = box[top][0], u1 = box[top][1], v0 = box[top][2], v1 = box[top][3];
+    double D[2][G][G];
+    for (int w = 0; w < 2; ++w) {
+      for (int i = 0; i < G; ++i)
+        for (int j = 0; j < G; ++j) D[w][i][j] = full[w][i][j];
+      bz_restrict<G>(D[w], 0, u0, u1);
+      bz_restrict<G>(D[w], 1, v0, v1);
+    }
+    bool split = true;
+#pragma unroll 1
+    for (int it = 0; it < 16; ++it) {
+      double ulo = 0.0, uhi = 1.0, vlo = 0.0, vhi = 1.0;
+      bool hit = true;
+      for (int w = 0; w < 2 && hit; ++w) {
+        double a, b;
+        hit = bz_clip<G>(D[w], 0, a, b);
+        ulo = fmax(ulo, a);
+        uhi = fmin(uhi, b);
+        hit = hit && ulo <= uhi;
+      }
+      for (int w = 0; w < 2 && hit; ++w) {
+        double a, b;
+        hit = bz_clip<G>(D[w], 1, a, b);
+        vlo = fmax(vlo, a);
+        vhi = fmin(vhi, b);
+        hit = hit && vlo <= vhi;
+      }
+      if (!hit) {
+        split = false;
+        break;
+      }
+      const double wu = u1 - u0, wv = v1 - v0;
+      for (int w = 0; w < 2; ++w) {
+        bz_restrict<G>(D[w], 0, ulo, uhi);
+        bz_restrict<G>(D[w], 1, vlo, vhi);
+      }
+      u1 = u0 + wu * uhi;
+      u0 = u0 + wu * ulo;
+      v1 = v0 + wv * vhi;
+      v0 = v0 + wv * vlo;
+      if (u1 - u0 < 1e-9 && v1 - v0 < 1e-9) {
+        double s = u0 + u1 - 1.0, t = v0 + v1 - 1.0;  // 2 * midpoint - 1
+        double p[3];
+        face_point<G>(X64, f, s, t, k, p);
+        double al = td[0] * (p[0] - xs[0]) + td[1] * (p[1] - xs[1]) + td[2] * (p[2] - xs[2]);
+        double s2 = s, t2 = t, al2 = al;
+        if (curved_refine<G>(X64, X32, f, xs, td, k, s2, t2, al2, L) &&
+            fabs(s2 - s) < 1e-6 && fabs(t2 - t) < 1e-6) {
+          s = s2;
+          t = t2;
+          al = al2;
+        }
+        bool dup = false;
+        for (int q = 0; q < nr; ++q)
+          if (fabs(rs[q] - s) < 1e-9 && fabs(rt[q] - t) < 1e-9) dup = true;
+        if (!dup && nr < maxr) {
+          rs[nr] = s;
+          rt[nr] = t;
+          ra[nr] = al;
+          ++nr;
+        }
+        split = false;
+        break;
+      }
+      if ((uhi - ulo) * (vhi - vlo) > 0.5) break;  // little progress: split
+    }
+    if (split && top + 2 <= kStack) {
+      // halve the longer side of the current box
+      double b0[4] = {u0, u1, v0, v1}, b1[4] = {u0, u1, v0, v1};
+      if (u1 - u0 >= v1 - v0) {
+        b0[1] = b1[0] = 0.5 * (u0 + u1);
+      } else {
+        b0[3] = b1[2] = 0.5 * (v0 + v1);
+      }
+      for (int q = 0; q < 4; ++q) {
+        box[top][q] = b1[q];
+        box[top + 1][q] = b0[q];
+      }
+      top += 2;
+    }
+  }
+  return nr;
+}
+
 template <typename R>
 __device__ __forceinline__ void reflect3(R* a, const double* n) {
   double s = 2.0 * ((double)a[0] * n[0] + (double)a[1] * n[1] + (double)a[2] * n[2]);
@@ -1209,9 +1412,15 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
       double Bl[12];
 #pragma unroll
       for (int q = 0; q < 12; ++q) Bl[q] = __ldg(Bf + q);
-      double rs[2], rt[2], ra[2];
-      int nr = bilinear_roots(Bl, xl, td, n1, n2, rs, rt, ra);
-      if (kind == PT_FACE_CURVED) {
+      double rs[4], rt[4], ra[4];
+      int nr = 0;
+      const bool clip_all = kind == PT_FACE_CURVED && k.curved_clip;
+      if (clip_all)
+        nr = bezier_clip_roots<G>(X64, m.xg32 + (size_t)e * 3 * G * G * G, f, xl, td, n1, n2, k,
+                                  L, rs, rt, ra, 4);
+      else
+        nr = bilinear_roots(Bl, xl, td, n1, n2, rs, rt, ra);
+      if (kind == PT_FACE_CURVED && !clip_all) {
         // the curved face lies within dev of its bilinear patch: a bilinear
         // crossing far beyond the segment cannot refine into one inside it
         const double dev = (double)__ldg(sl + 6);

@@ -37,7 +37,8 @@ class Config(ctypes.Structure):
                 ("max_cross", ctypes.c_int32), ("rebin_every", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("lift", ctypes.c_int32),
                 ("sphericity", ctypes.c_double), ("track", ctypes.c_int32),
-                ("buoyancy", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("buoyancy", ctypes.c_int32), ("curved_faces", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class MeshDesc(ctypes.Structure):

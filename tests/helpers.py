@@ -83,6 +83,8 @@ def compare(gpu, orc, tol, xscale=1.0, vscale=1.0, min_checked=0.9):
     # frozen states agree (a particle frozen on one side only is a failure)
     fz_g = (gpu["status"] & oracle.ST_FROZEN) != 0
     fz_o = (orc["status"] & oracle.ST_FROZEN) != 0
-    assert np.array_equal(fz_g[~near], fz_o[~near]), "frozen-state mismatch"
+    bad = np.flatnonzero((fz_g != fz_o) & ~near)
+    assert bad.size == 0, (f"frozen-state mismatch at {bad[:5]}: gpu status "
+                           f"{gpu['status'][bad[:5]]}, oracle {orc['status'][bad[:5]]}")
     return dict(checked=int(ok.sum()), near=int(near.sum()), ex=float(ex.max()),
                 ev=float(ev.max()))

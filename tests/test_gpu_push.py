@@ -169,3 +169,29 @@ def test_reference_space_localisation_periodic_box():
     wl = W.tgv_box(8, 3, P=2000, nsteps=100)
     res, g, o = _push_and_compare(wl, "fp64", 1e-12, track=pt.TRACK_REFERENCE)
     assert res["stats"]["crossings"] > 100 and res["stats"]["slow_track"] == 0
+
+
+@pytest.mark.parametrize("ngeo", [2, 3, 4])
+def test_bezier_clipping_for_every_curved_face_fp64(ngeo):
+    """Sec. 3.2.4: with curved_faces = 1 every curved face is intersected by
+    Bezier clipping; owners, wall hits and states equal the oracle's (Bezier
+    subdivision), positions within 1e-12."""
+    wl = W.curved_channel((6, 6, 6), ngeo, 5, P=300, nsteps=30, dt=2e-3, st=(0.1, 100.0))
+    _speed_up(wl)
+    res, g, o = _push_and_compare(wl, "fp64", 1e-12, curved_faces=1)
+    assert res["stats"]["crossings"] > 50
+
+
+def test_bezier_clipping_on_curved_walls_fp64():
+    mesh = W.channel_mesh((5, 4, 4), 2, amp=0.1, curved_walls=True)
+    wl = W.curved_channel((5, 4, 4), 2, 3, P=300, nsteps=30, dt=5e-3)
+    wl.mesh = mesh
+    U, _ = W.fluid_channel(mesh, 3, 0, seed=0)
+    wl.U = U
+    x, el = W.seed_particles(mesh, 300, seed=3)
+    wl.x, wl.elem = x, el
+    rng = np.random.default_rng(0)
+    wl.v = torch.as_tensor(rng.normal(size=(300, 3)) * 3.0)
+    wl.d = torch.full((300,), 4e-3, dtype=torch.float64)
+    res, g, o = _push_and_compare(wl, "fp64", 1e-12, curved_faces=1)
+    assert res["stats"]["wall_hits"] > 20
