@@ -1137,7 +1137,7 @@ __device__ __noinline__ int bezier_clip_roots(const double* X64, const float* X3
                                               const double* n1, const double* n2,
                                               const DevConsts& k, double L, double* rs,
                                               double* rt, double* ra, int maxr) {
-  constexpr int kStack = 64;
+  constexpr int kStack = 24;
   double full[2][G][G];
   int base, sm, sk;
   face_strides<G>(f, base, sm, sk);
@@ -1303,7 +1303,7 @@ __device__ __forceinline__ int slab_touch(const DevMesh& m, int e, const float* 
 // continue in the neighbour on the same ray.  Periodic: same, translated.
 // Wall: restart at the hit point with the remaining length, mirroring the
 // direction, v, kx and kv by I - 2 n n^T (Sec. 2.4).  Open: stop there.
-template <int G, typename R>
+template <int G, typename R, bool CLIP = false>
 __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, int& e, double* x,
                                         double* xe, R* v, R* kx, R* kv, int& hits, unsigned& st,
                                         TrackCounters& tc);
@@ -1321,7 +1321,9 @@ __device__ __forceinline__ void track(const DevMesh& m, const DevConsts& k, int&
   track_slow<G, R>(m, k, e, x, xe, v, kx, kv, hits, st, tc);
 }
 
-template <int G, typename R>
+// CLIP: curved faces by Bezier clipping (a separate instantiation, so that the
+// default path carries none of its code)
+template <int G, typename R, bool CLIP>
 __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, int& e, double* x,
                                         double* xe, R* v, R* kx, R* kv, int& hits, unsigned& st,
                                         TrackCounters& tc) {
@@ -1412,14 +1414,19 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
       double Bl[12];
 #pragma unroll
       for (int q = 0; q < 12; ++q) Bl[q] = __ldg(Bf + q);
-      double rs[4], rt[4], ra[4];
+      constexpr int MR = CLIP ? 4 : 2;
+      double rs[MR], rt[MR], ra[MR];
       int nr = 0;
-      const bool clip_all = kind == PT_FACE_CURVED && k.curved_clip;
-      if (clip_all)
-        nr = bezier_clip_roots<G>(X64, m.xg32 + (size_t)e * 3 * G * G * G, f, xl, td, n1, n2, k,
-                                  L, rs, rt, ra, 4);
-      else
+      const bool clip_all = CLIP && kind == PT_FACE_CURVED;
+      if constexpr (CLIP) {
+        if (clip_all)
+          nr = bezier_clip_roots<G>(X64, m.xg32 + (size_t)e * 3 * G * G * G, f, xl, td, n1, n2,
+                                    k, L, rs, rt, ra, MR);
+        else
+          nr = bilinear_roots(Bl, xl, td, n1, n2, rs, rt, ra);
+      } else {
         nr = bilinear_roots(Bl, xl, td, n1, n2, rs, rt, ra);
+      }
       if (kind == PT_FACE_CURVED && !clip_all) {
         // the curved face lies within dev of its bilinear patch: a bilinear
         // crossing far beyond the segment cannot refine into one inside it

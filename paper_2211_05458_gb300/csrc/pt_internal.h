@@ -49,7 +49,6 @@ struct DevMesh {
 // Constants of one run: node sets, RK table, physics and tolerances.
 struct DevConsts {
   double gn[PT_MAXG], gw[PT_MAXG];   // geometry nodes / barycentric weights
-  double gbz[PT_MAXG * PT_MAXG];     // Bezier control values = gbz x nodal values
   float gn32[PT_MAXG], gw32[PT_MAXG];
   float gn_hi[PT_MAXG], gn_lo[PT_MAXG], gw_hi[PT_MAXG], gw_lo[PT_MAXG];  // double-float copies
   double sn[PT_MAXN], sw[PT_MAXN];   // solution nodes / barycentric weights
@@ -61,6 +60,7 @@ struct DevConsts {
   double newton_tol, band_ref, band_x, lost_tol;
   double hl[4];                      // Haider-Levenspiel A, B, C, D
   int drag_law, max_newton, max_cross, guess, lift, track, buoyancy, curved_clip;
+  double gbz[PT_MAXG * PT_MAXG];     // Bezier control values = gbz x nodal values
 };
 
 struct DevParticles {

@@ -310,7 +310,7 @@ __device__ __noinline__ int settle_f32(const DevMesh& m, const DevConsts& k, int
 // the whole call (the fluid state is constant during it).  Every lane of a
 // warp must call it (the learned start is warp-collective); lanes without a
 // particle pass inrange = false.
-template <int G, int NP, bool F64, bool MLP>
+template <int G, int NP, bool F64, bool MLP, bool CLIP = false>
 __device__ __forceinline__ void push_particle(const DevMesh& m, const DevConsts& k, MlpSmem* sm,
                                               const DevMLP* mlpp,
                                               const typename RealOf<F64>::type* __restrict__ U,
@@ -432,7 +432,7 @@ __device__ __forceinline__ void push_particle(const DevMesh& m, const DevConsts&
         for (int r = 0; r < 3; ++r) x[r] = xe[r];
         pending = touch != 0;
       } else {
-        track_slow<G, R>(m, k, e, x, xe, v, kx, kv, hits, st, c.tc);
+        track_slow<G, R, CLIP>(m, k, e, x, xe, v, kx, kv, hits, st, c.tc);
         pending = true;
       }
       if (st & PT_ST_FROZEN) live = false;
@@ -464,7 +464,7 @@ __device__ __forceinline__ void push_particle(const DevMesh& m, const DevConsts&
 // double-float offset from the owning element's centre, so that a stage issues
 // no FP64 instruction except in the exact face-intersection path (the FP64
 // position is formed again at the end and around that path).
-template <int G, int NP, bool MLP>
+template <int G, int NP, bool MLP, bool CLIP = false>
 __device__ __forceinline__ void push_particle_f32(const DevMesh& m, const DevConsts& k,
                                                   MlpSmem* sm, const DevMLP* mlpp,
                                                   const float* __restrict__ U,
@@ -609,7 +609,7 @@ __device__ __forceinline__ void push_particle_f32(const DevMesh& m, const DevCon
           xs[r] = cr + df_to_double(xd[r]);
           xg[r] = cr + df_to_double(xe[r]);
         }
-        track_slow<G, float>(m, k, e, xs, xg, v, kx, kv, hits, st, c.tc);
+        track_slow<G, float, CLIP>(m, k, e, xs, xg, v, kx, kv, hits, st, c.tc);
         if (st & PT_ST_FROZEN) {
           live = false;
 #pragma unroll
@@ -659,7 +659,7 @@ __device__ __forceinline__ void push_particle_f32(const DevMesh& m, const DevCon
 
 // One thread per particle, visiting particles in element-sorted order (perm)
 // so that a warp shares its element's data through L1.  Persistent grid.
-template <int G, int NP, bool F64, bool MLP>
+template <int G, int NP, bool F64, bool MLP, bool CLIP = false>
 __global__ void __launch_bounds__(128, F64 ? PT_PUSH_MINB_F64 : PT_PUSH_MINB)
     k_push(const __grid_constant__ PushArgs a) {
   using R = typename RealOf<F64>::type;
@@ -673,10 +673,10 @@ __global__ void __launch_bounds__(128, F64 ? PT_PUSH_MINB_F64 : PT_PUSH_MINB)
     const bool inrange = t < n;
     const int64_t ip = inrange ? (a.perm ? (int64_t)a.perm[t] : t) : 0;
     if constexpr (F64)
-      push_particle<G, NP, true, false>(a.m, a.k, sm, &a.mlp, U, a.p, ip, inrange, a.nsteps, a.dt,
+      push_particle<G, NP, true, false, CLIP>(a.m, a.k, sm, &a.mlp, U, a.p, ip, inrange, a.nsteps, a.dt,
                                         c);
     else
-      push_particle_f32<G, NP, MLP>(a.m, a.k, sm, &a.mlp, (const float*)U, a.p, ip, inrange, a.nsteps,
+      push_particle_f32<G, NP, MLP, CLIP>(a.m, a.k, sm, &a.mlp, (const float*)U, a.p, ip, inrange, a.nsteps,
                                a.dt, c);
   }
   count_add(a.stats, PT_C_STEPS, c.steps);
@@ -1102,10 +1102,19 @@ struct Family {
   static constexpr bool kMlp = (G == 4) && !F64;
   template <int NP>
   static int push(const PushArgs& a, int grid, int block, cudaStream_t s) {
-    if (kMlp && a.k.guess == PT_GUESS_MLP)
+    // curved faces by Bezier clipping: separate instantiations, so that the
+    // default kernels carry none of its code
+    const bool mlp = kMlp && a.k.guess == PT_GUESS_MLP;
+    if (a.k.curved_clip) {
+      if (mlp)
+        k_push<G, NP, F64, kMlp, true><<<grid, block, 0, s>>>(a);
+      else
+        k_push<G, NP, F64, false, true><<<grid, block, 0, s>>>(a);
+    } else if (mlp) {
       k_push<G, NP, F64, kMlp><<<grid, block, 0, s>>>(a);
-    else
+    } else {
       k_push<G, NP, F64, false><<<grid, block, 0, s>>>(a);
+    }
     return (int)cudaGetLastError();
   }
   // mode bit 0: segmented summation, bit 1: nearest-node projection

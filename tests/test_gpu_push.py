@@ -182,6 +182,15 @@ def test_bezier_clipping_for_every_curved_face_fp64(ngeo):
     assert res["stats"]["crossings"] > 50
 
 
+def test_bezier_clipping_fp32():
+    wl = W.curved_channel((6, 6, 6), 3, 5, P=300, nsteps=30, dt=2e-3, st=(0.1, 100.0))
+    _speed_up(wl)
+    h = 2.0 / 6
+    res, g, o = _push_and_compare(wl, "fp32", 2e-5, band=(2e-4, 1e-4 * h), band_ref=2e-4,
+                                  band_x=1e-4 * h, curved_faces=1, min_checked=0.85)
+    assert res["stats"]["crossings"] > 50
+
+
 def test_bezier_clipping_on_curved_walls_fp64():
     mesh = W.channel_mesh((5, 4, 4), 2, amp=0.1, curved_walls=True)
     wl = W.curved_channel((5, 4, 4), 2, 3, P=300, nsteps=30, dt=5e-3)
