@@ -17,7 +17,7 @@
 // rolled loop (one copy of the code, values through local memory), which
 // shrinks the hot loop's instruction footprint
 #ifndef PT_ROLL_BASIS
-#define PT_ROLL_BASIS 0
+#define PT_ROLL_BASIS 1
 #endif
 // 1: screen each touched face in FP32 before its exact FP64 solve
 #ifndef PT_FACE_SCREEN
