@@ -51,8 +51,11 @@ enum {
   PT_ST_OPEN = 1u << 5         /* left through an open boundary: frozen    */
 };
 
-/* boundary kinds (pt_mesh_desc.bc) */
-enum { PT_BC_INTERNAL = 0, PT_BC_WALL = 1, PT_BC_PERIODIC = 2, PT_BC_OPEN = 3 };
+/* boundary kinds (pt_mesh_desc.bc); PT_BC_MORTAR marks the big side of a
+ * non-conforming face (Sec. 3.2.3), see pt_mesh_desc.mortar */
+enum { PT_BC_INTERNAL = 0, PT_BC_WALL = 1, PT_BC_PERIODIC = 2, PT_BC_OPEN = 3, PT_BC_MORTAR = 4 };
+/* mortar types (pt_mesh_desc.mortar[m][0]) */
+enum { PT_MORTAR_FOUR = 1, PT_MORTAR_S = 2, PT_MORTAR_T = 3 };
 
 typedef enum { PT_FP64 = 0, PT_FP32 = 1 } pt_precision;
 typedef enum {
@@ -85,6 +88,19 @@ typedef enum {
  *   bc       [nelem][6]   PT_BC_* of face f
  *   shift    [nelem][6][3] translation added to a particle crossing a
  *                          periodic face (ignored for other kinds)
+ *   nmortar  number of rows of mortar (0 for a conforming mesh)
+ *   mortar   [nmortar][9]  non-conforming faces (Sec. 3.2.3): the big side
+ *            (e, f) of a mortar has bc PT_BC_MORTAR, neighbor[e][f] = its row
+ *            m and nbr_face[e][f] = -1; row m holds
+ *              [0]    PT_MORTAR_FOUR: four small faces, small face k = i_s + 2 i_t
+ *                     covers the part of the big face with s < 0 (i_s = 0) or
+ *                     s > 0 (i_s = 1), likewise t; PT_MORTAR_S: two, k = i_s;
+ *                     PT_MORTAR_T: two, k = i_t ((s,t): the big face's parameters)
+ *              [1..4] the small elements, [5..8] their local faces (-1 unused)
+ *            Every small face is PT_BC_INTERNAL with the big element and face as
+ *            neighbour.  Small faces must tile the big face (to rounding).
+ *            Mortar faces are not periodic (zero shift).  May be NULL if
+ *            nmortar = 0.
  * Local faces: 0: xi1=-1, 1: xi1=+1, 2: xi2=-1, 3: xi2=+1, 4: xi3=-1, 5: xi3=+1;
  * face parameters (s,t) run along the two free reference directions in order. */
 typedef struct {
@@ -95,6 +111,8 @@ typedef struct {
   const int32_t* nbr_face;
   const int32_t* bc;
   const double* shift;
+  int32_t nmortar;
+  const int32_t* mortar;
 } pt_mesh_desc;
 
 /* Run-time configuration.  pt_config_default() fills the documented defaults. */
@@ -178,7 +196,8 @@ void pt_config_default(pt_config* cfg);
  * tables.  stream: cudaStream_t used for all later work (NULL = default).
  * Returns PT_ERR_ARG for inconsistent connectivity (a neighbour that does not
  * point back, an out-of-range element or face index, a non-periodic face with
- * a shift, unsupported ngeo (1..4)).  *ctx is NULL on error. */
+ * a shift, a malformed mortar row or one not referenced by exactly one big
+ * face, unsupported ngeo (1..4)).  *ctx is NULL on error. */
 pt_status pt_init_mesh(pt_ctx** ctx, const pt_mesh_desc* mesh, const pt_config* cfg,
                        void* stream);
 

@@ -88,6 +88,7 @@ def lib():
             L.or_create.restype = vp
             L.or_create.argtypes = [ctypes.c_int, ctypes.c_int, _D, _I, _I, _I, _D]
             L.or_destroy.argtypes = [vp]
+            L.or_set_mortars.argtypes = [vp, ctypes.c_int, _I]
             L.or_set_fluid.argtypes = [vp, ctypes.c_int, ctypes.c_int, _D]
             L.or_nodes.argtypes = [ctypes.c_int, ctypes.c_int, _D]
             L.or_lagrange.restype = ctypes.c_double
@@ -210,6 +211,11 @@ class Oracle:
                              _ip(k["nbr_face"]), _ip(k["bc"]), _dp(k["shift"]))
         if not self.h:
             raise ValueError("oracle: bad mesh")
+        mortar = mesh.get("mortar")
+        if mortar is not None and len(mortar):
+            self._keep["mortar"] = _i32(mortar)
+            if not L.or_set_mortars(self.h, len(mortar), _ip(self._keep["mortar"])):
+                raise ValueError("oracle: bad mortar table")
         self.N = None
 
     def close(self):

@@ -19,6 +19,8 @@ struct or_ctx {
   double* xgeo;
   int32_t *nbr, *nbf, *bc;
   double* shift;
+  int nmortar;
+  int32_t* mortar; /* [nmortar][9] non-conforming faces, layout in oracle.h */
   double* ctrl; /* [nelem][6][g*g][3] Bezier control points of every face */
   double* bbox; /* [nelem][6][6]    lo xyz, hi xyz of those control points */
   double geo_nodes[MAXG];
@@ -711,7 +713,45 @@ static void track(const or_ctx* c, const or_params* p, int32_t* elem, double x[3
     }
     if (bf < 0) break;
     int kind = c->bc[e * 6 + bf];
-    if (kind == 0 || kind == 2) {
+    if (kind == 4) {
+      /* big side of a mortar (Sec. 3.2.3): the crossing is searched again on
+       * the small faces matched to it; the one whose crossing lies closest to
+       * the big face's (lowest index on ties) is the face the particle enters
+       * by.  The ray is the same, only its entry and exit roles swap, so
+       * the search needs no inversion here: face_hits_ray reports both. */
+      const int32_t* mt = c->mortar + 9 * (size_t)c->nbr[e * 6 + bf];
+      int ns = mt[0] == 1 ? 4 : 2, kb = -1;
+      double dbest = INFINITY, ka = best, km = 0.0;
+      for (int k = 0; k < ns; ++k) {
+        hitlist hl;
+        face_hits_ray(c, mt[1 + k], mt[5 + k], xs, td, L, p->band_x, &hl);
+        for (int i = 0; i < hl.n; ++i) {
+          double al = hl.h[i].alpha, s = hl.h[i].s, t = hl.h[i].t;
+          double m = fabs(s) > fabs(t) ? fabs(s) : fabs(t);
+          if (m > 1.0 + p->band_ref) continue;
+          if (al < a0 - p->band_x || al > L + p->band_x) continue;
+          if (fabs(al - best) < dbest) {
+            dbest = fabs(al - best);
+            kb = k;
+            ka = al;
+            km = m;
+          }
+        }
+      }
+      if (kb < 0) {
+        /* no small face reports the crossing (a gap of rounding size at their
+         * shared edges): take the small face whose part of the big face holds
+         * the big face's crossing parameters */
+        int is = bs > 0.0, it = bt > 0.0;
+        kb = mt[0] == 1 ? is + 2 * it : (mt[0] == 2 ? is : it);
+        ka = best;
+        km = 1.0;
+      }
+      if (fabs(km - 1.0) < p->band_ref) *status |= OR_ST_NEAR_FACE;
+      e = mt[1 + kb];
+      fin = mt[5 + kb];
+      a0 = ka;
+    } else if (kind == 0 || kind == 2) {
       if (kind == 2) {
         const double* sh = c->shift + ((size_t)e * 6 + bf) * 3;
         for (int r = 0; r < 3; ++r) {
@@ -1210,6 +1250,22 @@ or_ctx* or_create(int nelem, int ngeo, const double* xgeo, const int32_t* neighb
   return c;
 }
 
+int or_set_mortars(or_ctx* c, int nmortar, const int32_t* mortar) {
+  if (nmortar < 0) return 0;
+  for (int m = 0; m < nmortar; ++m) {
+    const int32_t* mt = mortar + 9 * (size_t)m;
+    int ns = mt[0] == 1 ? 4 : 2;
+    if (mt[0] < 1 || mt[0] > 3) return 0;
+    for (int k = 0; k < ns; ++k)
+      if (mt[1 + k] < 0 || mt[1 + k] >= c->nelem || mt[5 + k] < 0 || mt[5 + k] > 5) return 0;
+  }
+  free(c->mortar);
+  c->mortar = (int32_t*)malloc(sizeof(int32_t) * 9 * (size_t)(nmortar > 0 ? nmortar : 1));
+  if (nmortar > 0) memcpy(c->mortar, mortar, sizeof(int32_t) * 9 * (size_t)nmortar);
+  c->nmortar = nmortar;
+  return 1;
+}
+
 int or_set_fluid(or_ctx* c, int N, int node_type, const double* U) {
   if (N < 0 || N + 1 > MAXN || (node_type != 0 && node_type != 1)) return 0;
   c->N = N;
@@ -1230,6 +1286,7 @@ void or_destroy(or_ctx* c) {
   free(c->nbf);
   free(c->bc);
   free(c->shift);
+  free(c->mortar);
   free(c->ctrl);
   free(c->bbox);
   free(c->U);

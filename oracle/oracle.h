@@ -63,10 +63,20 @@ typedef struct or_ctx or_ctx;
 /* mesh: xgeo[nelem][(ngeo+1)^3][3], node (a,b,c) at index a+g*(b+g*c) on
  * equidistant reference nodes; neighbor/nbr_face/bc[nelem][6]; shift[nelem][6][3].
  * Local faces: 0: xi1=-1, 1: xi1=+1, 2: xi2=-1, 3: xi2=+1, 4: xi3=-1, 5: xi3=+1.
- * bc: 0 internal, 1 wall, 2 periodic, 3 open.  Arrays are copied. */
+ * bc: 0 internal, 1 wall, 2 periodic, 3 open, 4 mortar (or_set_mortars).  Arrays are copied. */
 or_ctx* or_create(int nelem, int ngeo, const double* xgeo, const int32_t* neighbor,
                   const int32_t* nbr_face, const int32_t* bc, const double* shift);
 void    or_destroy(or_ctx* c);
+/* non-conforming faces (Sec. 3.2.3): a face with bc 4 is the big side of a
+ * mortar; its neighbor entry is a row m of mortar[nmortar][9]:
+ *   [0] type 1: four small faces, small face k = i_s + 2 i_t covers the part of
+ *       the big face with s < 0 (i_s = 0) or s > 0 (i_s = 1), likewise t;
+ *       type 2: two small faces, k = i_s; type 3: two small faces, k = i_t
+ *       ((s,t) the big face's parameters)
+ *   [1..4] small elements, [5..8] their local faces (unused entries -1).
+ * Each small face is an internal face whose neighbour is the big element.
+ * The table is copied.  Returns 0 on a malformed table. */
+int     or_set_mortars(or_ctx* c, int nmortar, const int32_t* mortar);
 /* fluid: U[nelem][5][(N+1)^3] with node (i,j,k) at i+n*(j+n*k); node_type 0 Gauss, 1 GLL.
  * The array is copied. */
 int     or_set_fluid(or_ctx* c, int N, int node_type, const double* U);

@@ -311,6 +311,10 @@ static pt_status upload_mesh(pt_ctx* c, const pt_mesh_desc* md) {
   std::vector<double> M;
   bezier_matrix(g, M);
   const double bx = c->cfg.band_x;
+  const int nmort = md->nmortar;
+  if (nmort < 0 || (nmort > 0 && md->mortar == nullptr))
+    return fail(nullptr, PT_ERR_ARG, "bad mortar table (%d rows)", nmort);
+  std::vector<int> big_of((size_t)nmort, -1);
   int ncurved = 0;
   for (int e = 0; e < E; ++e) {
     const double* X = md->xgeo + (size_t)e * g3 * 3;
@@ -366,13 +370,33 @@ static pt_status upload_mesh(pt_ctx* c, const pt_mesh_desc* md) {
       const int k6 = 6 * e + f;
       int bc = md->bc[k6];
       int nb = md->neighbor[k6], nf = md->nbr_face[k6];
-      if (bc < 0 || bc > 3) return fail(nullptr, PT_ERR_ARG, "element %d face %d: bad bc %d", e, f, bc);
+      if (bc < 0 || bc > 4) return fail(nullptr, PT_ERR_ARG, "element %d face %d: bad bc %d", e, f, bc);
       if (bc == PT_BC_INTERNAL || bc == PT_BC_PERIODIC) {
         if (nb < 0 || nb >= E || nf < 0 || nf > 5)
           return fail(nullptr, PT_ERR_ARG, "element %d face %d: bad neighbour %d/%d", e, f, nb, nf);
-        if (md->neighbor[6 * nb + nf] != e || md->nbr_face[6 * nb + nf] != f)
+        if (md->bc[6 * nb + nf] == PT_BC_MORTAR) {
+          // small side of a mortar: the big face's row must list this face
+          const int row = md->neighbor[6 * nb + nf];
+          bool listed = false;
+          if (bc == PT_BC_INTERNAL && row >= 0 && row < nmort)
+            for (int q = 0; q < 4; ++q)
+              listed |= md->mortar[9 * (size_t)row + 1 + q] == e &&
+                        md->mortar[9 * (size_t)row + 5 + q] == f;
+          if (!listed)
+            return fail(nullptr, PT_ERR_ARG,
+                        "element %d face %d: not a small face of the mortar of element %d", e, f,
+                        nb);
+        } else if (md->neighbor[6 * nb + nf] != e || md->nbr_face[6 * nb + nf] != f) {
           return fail(nullptr, PT_ERR_ARG, "element %d face %d: neighbour %d does not point back", e,
                       f, nb);
+        }
+      } else if (bc == PT_BC_MORTAR) {
+        if (nb < 0 || nb >= nmort)
+          return fail(nullptr, PT_ERR_ARG, "element %d face %d: bad mortar row %d", e, f, nb);
+        if (big_of[nb] >= 0)
+          return fail(nullptr, PT_ERR_ARG, "mortar row %d referenced twice", nb);
+        big_of[nb] = k6;
+        nf = 0;
       } else {
         nb = -1;
         nf = 0;
@@ -417,7 +441,7 @@ static pt_status upload_mesh(pt_ctx* c, const pt_mesh_desc* md) {
                                      : PT_FACE_CURVED;
       ncurved += kind == PT_FACE_CURVED;
       fnbr[k6] = nb;
-      finfo[k6] = bc | (kind << 2) | (nf << 4);
+      finfo[k6] = bc | (kind << 3) | (nf << 5);
       // slab: centre normal b x c rounded to FP32, range over the Bezier
       // control points (their convex hull contains the face), widened
       double nrm[3] = {Bf[4] * Bf[8] - Bf[5] * Bf[7], Bf[5] * Bf[6] - Bf[3] * Bf[8],
@@ -473,6 +497,30 @@ static pt_status upload_mesh(pt_ctx* c, const pt_mesh_desc* md) {
     }
   }
   c->ncurved = ncurved;
+  // mortar rows: every listed small face points back at the big face
+  for (int r = 0; r < nmort; ++r) {
+    const int32_t* mt = md->mortar + 9 * (size_t)r;
+    if (big_of[r] < 0) return fail(nullptr, PT_ERR_ARG, "mortar row %d: no big face", r);
+    if (mt[0] < PT_MORTAR_FOUR || mt[0] > PT_MORTAR_T)
+      return fail(nullptr, PT_ERR_ARG, "mortar row %d: bad type %d", r, mt[0]);
+    const int ns = mt[0] == PT_MORTAR_FOUR ? 4 : 2;
+    for (int q = 0; q < 4; ++q) {
+      const int es = mt[1 + q], fs = mt[5 + q];
+      if (q >= ns) {
+        if (es != -1 || fs != -1)
+          return fail(nullptr, PT_ERR_ARG, "mortar row %d: entry %d must be unused", r, q);
+        continue;
+      }
+      if (es < 0 || es >= E || fs < 0 || fs > 5)
+        return fail(nullptr, PT_ERR_ARG, "mortar row %d: bad small face %d/%d", r, es, fs);
+      const int ks = 6 * es + fs;
+      if (md->bc[ks] != PT_BC_INTERNAL || 6 * md->neighbor[ks] + md->nbr_face[ks] != big_of[r])
+        return fail(nullptr, PT_ERR_ARG, "mortar row %d: small face %d/%d does not point back", r,
+                    es, fs);
+    }
+  }
+  std::vector<int> mort((size_t)std::max(nmort, 1) * 9, -1);
+  if (nmort > 0) std::memcpy(mort.data(), md->mortar, sizeof(int) * 9 * (size_t)nmort);
   cudaError_t err;
   pt_ctx* cc = c;
   c->d_xg64 = dmalloc<double>(cc, xg64.size(), &err);
@@ -501,6 +549,9 @@ static pt_status upload_mesh(pt_ctx* c, const pt_mesh_desc* md) {
   if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
   c->d_shift = dmalloc<double>(cc, shift.size(), &err);
   if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
+  c->d_mort = dmalloc<int>(cc, mort.size(), &err);
+  if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
+  c->nmortar = nmort;
   c->d_stats = dmalloc<unsigned long long>(cc, PT_C_COUNT, &err);
   if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(err));
   struct {
@@ -514,7 +565,8 @@ static pt_status upload_mesh(pt_ctx* c, const pt_mesh_desc* md) {
             {c->d_fnbr, fnbr.data(), fnbr.size() * 4}, {c->d_finfo, finfo.data(), finfo.size() * 4},
             {c->d_slab, slab.data(), slab.size() * 4}, {c->d_bil, bil.data(), bil.size() * 8},
             {c->d_bil32, bil32.data(), bil32.size() * 4},
-            {c->d_shift, shift.data(), shift.size() * 8}};
+            {c->d_shift, shift.data(), shift.size() * 8},
+            {c->d_mort, mort.data(), mort.size() * 4}};
   for (auto& q : cp) {
     err = cudaMemcpy(q.d, q.h, q.b, cudaMemcpyHostToDevice);
     if (err) return fail(nullptr, PT_ERR_CUDA, "cudaMemcpy: %s", cudaGetErrorString(err));
@@ -599,6 +651,7 @@ static DevMesh dev_mesh(const pt_ctx* c) {
   m.bil = c->d_bil;
   m.bil32 = c->d_bil32;
   m.shift = c->d_shift;
+  m.mort = c->d_mort;
   m.mlp_pre = c->d_mlp_pre;
   return m;
 }

@@ -31,6 +31,8 @@ struct pt_ctx {
   double* d_bil = nullptr;
   float* d_bil32 = nullptr;
   double* d_shift = nullptr;
+  int* d_mort = nullptr;  // [max(M,1)][9] mortar rows
+  int nmortar = 0;
   unsigned long long* d_stats = nullptr;
   std::vector<void*> allocs;
   // fluid

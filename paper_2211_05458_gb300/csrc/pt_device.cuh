@@ -1321,6 +1321,86 @@ __device__ __forceinline__ void track(const DevMesh& m, const DevConsts& k, int&
   track_slow<G, R>(m, k, e, x, xe, v, kx, kv, hits, st, tc);
 }
 
+// Big side of a mortar (Sec. 3.2.3): the crossing found on the big face is
+// searched again on the small faces matched to it -- their own tables and
+// geometry, the same ray (a root finder that reports every crossing needs no
+// inverted ray) -- and the small face whose accepted crossing lies closest to
+// the big face's one (lowest index on ties) becomes the entry face.  If none
+// reports it (a rounding-size gap at the small faces' shared edges), the small
+// face whose part of the big face holds the big face's crossing parameters
+// (bs, bt) is taken.  Out of line: mortar crossings are rare.
+template <int G, bool CLIP>
+__device__ __noinline__ void mortar_enter(const DevMesh& m, const DevConsts& k, int row, double bs,
+                                          double bt, const double* xs, const double* td,
+                                          const double* n1, const double* n2, double L, double a0,
+                                          double best, int& e, int& fin, double& anew,
+                                          unsigned& st) {
+  const int* mt = m.mort + 9 * (size_t)row;
+  const int type = __ldg(mt);
+  const int ns = type == PT_MORTAR_FOUR ? 4 : 2;
+  int kb = -1;
+  double db = 1e300, ka = best, km = 1.0;
+#pragma unroll 1
+  for (int q = 0; q < ns; ++q) {
+    const int es = __ldg(mt + 1 + q), fs = __ldg(mt + 5 + q);
+    const double* ce = m.ce + 3 * (size_t)es;
+    const double xl[3] = {xs[0] - __ldg(ce), xs[1] - __ldg(ce + 1), xs[2] - __ldg(ce + 2)};
+    const double* X64 = m.xg64 + (size_t)es * 3 * G * G * G;
+    const float* X32 = m.xg32 + (size_t)es * 3 * G * G * G;
+    const int kind = finfo_kind(__ldg(m.finfo + 6 * (size_t)es + fs));
+    constexpr int MR = CLIP ? 4 : 2;
+    double rs[MR], rt[MR], ra[MR];
+    int nr;
+    if (CLIP && kind == PT_FACE_CURVED) {
+      nr = bezier_clip_roots<G>(X64, X32, fs, xl, td, n1, n2, k, L, rs, rt, ra, MR);
+    } else {
+      const double* Bf = m.bil + 72 * (size_t)es + 12 * fs;
+      double Bl[12];
+#pragma unroll
+      for (int i = 0; i < 12; ++i) Bl[i] = __ldg(Bf + i);
+      nr = bilinear_roots(Bl, xl, td, n1, n2, rs, rt, ra);
+      if (kind == PT_FACE_CURVED) {
+        int kk = 0;
+#pragma unroll 1
+        for (int i = 0; i < nr; ++i) {
+          double s = rs[i], t = rt[i], al = ra[i];
+          if (!(fabs(s) < 2.0 && fabs(t) < 2.0)) continue;
+          if (curved_refine<G>(X64, X32, fs, xl, td, k, s, t, al, L)) {
+            rs[kk] = s;
+            rt[kk] = t;
+            ra[kk] = al;
+            kk++;
+          }
+        }
+        nr = kk;
+      }
+    }
+#pragma unroll 1
+    for (int i = 0; i < nr; ++i) {
+      const double mm = fmax(fabs(rs[i]), fabs(rt[i]));
+      if (mm > 1.0 + k.band_ref) continue;
+      if (ra[i] < a0 - k.band_x || ra[i] > L + k.band_x) continue;
+      const double dd = fabs(ra[i] - best);
+      if (dd < db) {
+        db = dd;
+        kb = q;
+        ka = ra[i];
+        km = mm;
+      }
+    }
+  }
+  if (kb < 0) {
+    const int is = bs > 0.0, it = bt > 0.0;
+    kb = type == PT_MORTAR_FOUR ? is + 2 * it : (type == PT_MORTAR_S ? is : it);
+    ka = best;
+    km = 1.0;
+  }
+  if (fabs(km - 1.0) < k.band_ref) st |= PT_ST_NEAR_FACE;
+  e = __ldg(mt + 1 + kb);
+  fin = __ldg(mt + 5 + kb);
+  anew = ka;
+}
+
 // CLIP: curved faces by Bezier clipping (a separate instantiation, so that the
 // default path carries none of its code)
 template <int G, typename R, bool CLIP>
@@ -1382,7 +1462,7 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
       const float pb = pa + Lf * cosf_;
       if (fmaxf(pa, pb) < __ldg(sl + 3) || fminf(pa, pb) > __ldg(sl + 4)) continue;
       const int info = __ldg(m.finfo + 6 * (size_t)e + f);
-      const int kind = (info >> 2) & 3;
+      const int kind = finfo_kind(info);
       // FP32 screen: skip the exact solve when every FP32 root is clearly
       // outside the segment or the face (margins ~100x the FP32 error)
       float fs[2], ft[2], fa[2];
@@ -1471,8 +1551,12 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
     }
     if (bf < 0) break;
     const int info = __ldg(m.finfo + 6 * (size_t)e + bf);
-    const int bc = info & 3;
-    if (bc == PT_BC_INTERNAL || bc == PT_BC_PERIODIC) {
+    const int bc = finfo_bc(info);
+    if (bc == PT_BC_MORTAR) {
+      mortar_enter<G, CLIP>(m, k, __ldg(m.fnbr + 6 * (size_t)e + bf), bs, bt, xs, td, n1, n2, L,
+                            a0, best, e, fin, a0, st);
+      tc.cross++;
+    } else if (bc == PT_BC_INTERNAL || bc == PT_BC_PERIODIC) {
       if (bc == PT_BC_PERIODIC) {
         const double* sh = m.shift + 18 * (size_t)e + 3 * bf;
 #pragma unroll
@@ -1481,13 +1565,13 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
           xe[r] += __ldg(sh + r);
         }
       }
-      fin = (info >> 4) & 7;
+      fin = finfo_nf(info);
       e = __ldg(m.fnbr + 6 * (size_t)e + bf);
       a0 = best;
       tc.cross++;
     } else if (bc == PT_BC_WALL) {
       double ps[3], pt[3], nrm[3];
-      const int kind = (info >> 2) & 3;
+      const int kind = finfo_kind(info);
       if (kind == PT_FACE_CURVED) {
         double p[3];
         face_eval<G>(X64, bf, bs, bt, k, p, ps, pt);

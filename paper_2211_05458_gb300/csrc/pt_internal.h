@@ -15,6 +15,10 @@
 
 // face kinds (by bounding-box flatness / bilinearity of the face nodes)
 enum { PT_FACE_PLANAR = 0, PT_FACE_BILINEAR = 1, PT_FACE_CURVED = 2 };
+// packed face record (DevMesh::finfo)
+__host__ __device__ __forceinline__ int finfo_bc(int info) { return info & 7; }
+__host__ __device__ __forceinline__ int finfo_kind(int info) { return (info >> 3) & 3; }
+__host__ __device__ __forceinline__ int finfo_nf(int info) { return (info >> 5) & 7; }
 
 // stats counter slots (device uint64 array)
 enum {
@@ -37,8 +41,9 @@ struct DevMesh {
   const double* ce;       // [E][3]
   const float* tri;       // [E][12]       trilinear centre (3) and inverse Jacobian (9)
   const int* tmask;       // [E]           bit q: coordinate q is trilinear in xi (8-corner form)
-  const int* fnbr;        // [E][6]        neighbour element
-  const int* finfo;       // [E][6]        bc | kind << 2 | nbr_face << 4
+  const int* fnbr;        // [E][6]        neighbour element (mortar row on a PT_BC_MORTAR face)
+  const int* finfo;       // [E][6]        bc | kind << 3 | nbr_face << 5
+  const int* mort;        // [M][9]        mortar rows as in pt_mesh_desc (null if none)
   const float* slab;      // [E][6][8]     unit normal (3), lo, hi, -, -, - (local coords)
   const double* bil;      // [E][6][12]    p(s,t) = a st + b s + c t + d (local coords)
   const float* bil32;     // [E][6][12]    FP32 copy of bil (screening)

@@ -222,6 +222,18 @@ __device__ __forceinline__ int settle_face(const double* z) {
   return 2 * d + (z[d] > 0.0 ? 1 : 0);
 }
 
+// The walk across a mortar's big face enters the small element whose part of
+// the big face holds the point's face parameters (the two xi components other
+// than the crossed one, in order).
+__device__ __forceinline__ int mortar_small(const DevMesh& m, int row, int f, const double* z) {
+  const int* mt = m.mort + 9 * (size_t)row;
+  const int d = f >> 1;
+  const double s = z[d == 0 ? 1 : 0], t = z[d == 2 ? 1 : 2];
+  const int type = __ldg(mt), is = s > 0.0, it = t > 0.0;
+  const int q = type == PT_MORTAR_FOUR ? is + 2 * it : (type == PT_MORTAR_S ? is : it);
+  return __ldg(mt + 1 + q);
+}
+
 // Walk threshold: with physical tracking a position up to lost_tol outside is
 // accepted (the tracking decided the owner); with reference-space localisation
 // the owner is decided here, to the near-face band.
@@ -252,14 +264,15 @@ __device__ __noinline__ int settle64(const DevMesh& m, const DevConsts& k, int& 
     if (tmax3(xi[0], xi[1], xi[2]) <= 1.0 + wtol) return 0;
     if (w == 4) return tmax3(xi[0], xi[1], xi[2]) <= 1.0 + k.lost_tol ? 0 : 2;
     const int f = settle_face(xi);
-    const int bc = __ldg(m.finfo + 6 * (size_t)e + f) & 3;
-    if (bc != PT_BC_INTERNAL && bc != PT_BC_PERIODIC) break;
+    const int bc = finfo_bc(__ldg(m.finfo + 6 * (size_t)e + f));
+    if (bc != PT_BC_INTERNAL && bc != PT_BC_PERIODIC && bc != PT_BC_MORTAR) break;
     if (bc == PT_BC_PERIODIC) {
       const double* sh = m.shift + 18 * (size_t)e + 3 * f;
 #pragma unroll
       for (int r = 0; r < 3; ++r) x[r] += __ldg(sh + r);
     }
-    e = __ldg(m.fnbr + 6 * (size_t)e + f);
+    e = bc == PT_BC_MORTAR ? mortar_small(m, __ldg(m.fnbr + 6 * (size_t)e + f), f, xi)
+                           : __ldg(m.fnbr + 6 * (size_t)e + f);
     ++cross;
   }
   return 2;
@@ -284,8 +297,8 @@ __device__ __noinline__ int settle_f32(const DevMesh& m, const DevConsts& k, int
     if (tmax3(z[0], z[1], z[2]) <= 1.0 + wtol) return 0;
     if (w == 4) return tmax3(z[0], z[1], z[2]) <= 1.0 + k.lost_tol ? 0 : 2;
     const int f = settle_face(z);
-    const int bc = __ldg(m.finfo + 6 * (size_t)e + f) & 3;
-    if (bc != PT_BC_INTERNAL && bc != PT_BC_PERIODIC) break;
+    const int bc = finfo_bc(__ldg(m.finfo + 6 * (size_t)e + f));
+    if (bc != PT_BC_INTERNAL && bc != PT_BC_PERIODIC && bc != PT_BC_MORTAR) break;
     const double* ce = m.ce + 3 * (size_t)e;
     double xg[3];
 #pragma unroll
@@ -295,7 +308,8 @@ __device__ __noinline__ int settle_f32(const DevMesh& m, const DevConsts& k, int
 #pragma unroll
       for (int r = 0; r < 3; ++r) xg[r] += __ldg(sh + r);
     }
-    e = __ldg(m.fnbr + 6 * (size_t)e + f);
+    e = bc == PT_BC_MORTAR ? mortar_small(m, __ldg(m.fnbr + 6 * (size_t)e + f), f, z)
+                           : __ldg(m.fnbr + 6 * (size_t)e + f);
     const double* cn = m.ce + 3 * (size_t)e;
 #pragma unroll
     for (int r = 0; r < 3; ++r) xd[r] = df_from_double(xg[r] - __ldg(cn + r));
@@ -352,8 +366,8 @@ __device__ __forceinline__ void push_particle(const DevMesh& m, const DevConsts&
       const R Bs = F64 ? (R)k.B[s] : (R)k.B32[s];
       const int eg = live ? e : 0;
       const double* ce = m.ce + 3 * (size_t)eg;
-      const double xl[3] = {x[0] - __ldg(ce), x[1] - __ldg(ce + 1), x[2] - __ldg(ce + 2)};
-      const float xf[3] = {(float)xl[0], (float)xl[1], (float)xl[2]};
+      double xl[3] = {x[0] - __ldg(ce), x[1] - __ldg(ce + 1), x[2] - __ldg(ce + 2)};
+      float xf[3] = {(float)xl[0], (float)xl[1], (float)xl[2]};
       float guess[3];
       start_guess_local<G, MLP>(m, k, sm, mlpp, eg, xf, live, guess);
       if (!live) continue;
@@ -384,6 +398,13 @@ __device__ __forceinline__ void push_particle(const DevMesh& m, const DevConsts&
           continue;
         }
         mx = tmax3(xi[0], xi[1], xi[2]);
+        // the stage segment's slab test below works in the new element's frame
+        const double* cn = m.ce + 3 * (size_t)e;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          xl[r] = x[r] - __ldg(cn + r);
+          xf[r] = (float)xl[r];
+        }
       }
       pending = false;
       if (mx > 1.0 - k.band_ref) st |= PT_ST_NEAR_FACE;
@@ -512,7 +533,7 @@ __device__ __forceinline__ void push_particle_f32(const DevMesh& m, const DevCon
       const float As = k.A32[s];
       const float Bs = k.B32[s];
       const int eg = live ? e : 0;
-      const float xf[3] = {xd[0].hi, xd[1].hi, xd[2].hi};
+      float xf[3] = {xd[0].hi, xd[1].hi, xd[2].hi};
       float guess[3];
       start_guess_local<G, MLP>(m, k, sm, mlpp, eg, xf, live, guess);
       if (!live) continue;
@@ -548,7 +569,10 @@ __device__ __forceinline__ void push_particle_f32(const DevMesh& m, const DevCon
             continue;
           }
 #pragma unroll
-          for (int q = 0; q < 3; ++q) xi[q] = zd[q].hi + zd[q].lo;
+          for (int q = 0; q < 3; ++q) {
+            xi[q] = zd[q].hi + zd[q].lo;
+            xf[q] = xd[q].hi;  // the slab test below works in the new element's frame
+          }
           md = fmax(fmax(fabs(df_to_double(zd[0])), fabs(df_to_double(zd[1]))),
                     fabs(df_to_double(zd[2])));
         }

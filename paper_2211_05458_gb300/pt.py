@@ -43,7 +43,8 @@ class Config(ctypes.Structure):
 
 class MeshDesc(ctypes.Structure):
     _fields_ = [("nelem", ctypes.c_int32), ("ngeo", ctypes.c_int32), ("xgeo", _vp),
-                ("neighbor", _vp), ("nbr_face", _vp), ("bc", _vp), ("shift", _vp)]
+                ("neighbor", _vp), ("nbr_face", _vp), ("bc", _vp), ("shift", _vp),
+                ("nmortar", ctypes.c_int32), ("mortar", _vp)]
 
 
 class CParticles(ctypes.Structure):
@@ -210,8 +211,12 @@ class Context:
                           nbr_face=np.ascontiguousarray(md["nbr_face"], dtype=np.int32),
                           bc=np.ascontiguousarray(md["bc"], dtype=np.int32),
                           shift=np.ascontiguousarray(md["shift"], dtype=np.float64))
+        mortar = md.get("mortar")
+        if mortar is not None and len(mortar):
+            self._host["mortar"] = np.ascontiguousarray(mortar, dtype=np.int32).reshape(-1, 9)
         d = MeshDesc()
         d.nelem, d.ngeo = int(md["nelem"]), int(md["ngeo"])
+        d.nmortar = len(self._host["mortar"]) if "mortar" in self._host else 0
         for k, a in self._host.items():
             setattr(d, k, a.ctypes.data)
         self.cfg = default_config(**cfg)

@@ -18,6 +18,14 @@ Recipes (the readings of arXiv 2211.05458 used for the five workloads):
   (1 - y^2)^2 psi(x), psi a sum of random-phase Fourier modes with |k| <= 8,
   integer k_x, even k_z, amplitude |k|^(-5/6) / |k| (energy spectrum ~ k^-5/3),
   scaled to u'_rms = 0.1 at the nodes; rho = 1, p = 100/1.4.
+* mortar box: [0,1]^3 with n^3 elements joined at x = 1 by non-conforming
+  faces to [1,2]x[0,1]^2 refined by two in x and in one or both transverse
+  directions (each big face matched to four or two small faces), walls
+  outside; geometry moved by a warp of degree <= 2 per direction
+  (x' = x + A (y^2 - y z), y' = y + A x (2 - x)(1 + z), z' = z + A x y) or of
+  degree 1 (x' = x + A y z, y' = y + A x z, z' = z + A x y), which both
+  blocks' nodes reproduce exactly at NGeo >= 2 (>= 1), so the small faces
+  tile the big one to rounding.
 * particles: element drawn uniformly, reference position uniform in
   [-(1-m), 1-m]^3 mapped by the same analytic node placement (so the draw is
   uniform in reference space, not exactly uniform in x); margin m keeps the
@@ -35,7 +43,10 @@ P0 = 100.0 / 1.4
 GAMMA = 1.4
 
 # local faces: 0: xi1=-1, 1: xi1=+1, 2: xi2=-1, 3: xi2=+1, 4: xi3=-1, 5: xi3=+1
-BC_INTERNAL, BC_WALL, BC_PERIODIC, BC_OPEN = 0, 1, 2, 3
+BC_INTERNAL, BC_WALL, BC_PERIODIC, BC_OPEN, BC_MORTAR = 0, 1, 2, 3, 4
+# mortar table rows: type (1: four small faces, 2: two split along s, 3: two
+# split along t), four small elements, their four local faces (-1 unused)
+MORTAR_FOUR, MORTAR_S, MORTAR_T = 1, 2, 3
 
 
 def gauss_nodes(n: int) -> np.ndarray:
@@ -72,10 +83,11 @@ class Mesh:
     warp: str = "none"
     amp: float = 0.0
     extra: dict = field(default_factory=dict)
+    mortar: np.ndarray = field(default_factory=lambda: np.zeros((0, 9), np.int32))
 
     def as_dict(self) -> dict:
         return dict(nelem=self.nelem, ngeo=self.ngeo, xgeo=self.xgeo, neighbor=self.neighbor,
-                    nbr_face=self.nbr_face, bc=self.bc, shift=self.shift)
+                    nbr_face=self.nbr_face, bc=self.bc, shift=self.shift, mortar=self.mortar)
 
 
 def _warp_torch(kind: str, amp: float, x, y, z):
@@ -88,6 +100,13 @@ def _warp_torch(kind: str, amp: float, x, y, z):
     if kind == "poly":
         # a polynomial warp of degree 2 per axis (exactly representable at NGeo >= 2)
         return x, y + amp * x * x * (1.0 + z), z + 0.5 * amp * x * y
+    if kind == "mortar_poly":
+        # degree <= 2 per direction; the plane x = 1 becomes curved
+        return (x + amp * (y * y - y * z), y + amp * x * (2.0 - x) * (1.0 + z),
+                z + amp * x * y)
+    if kind == "mortar_trilinear":
+        # degree 1 per direction (exactly representable at NGeo >= 1)
+        return x + amp * y * z, y + amp * x * z, z + amp * x * y
     raise ValueError(kind)
 
 
@@ -155,9 +174,66 @@ def channel_mesh(dims, ngeo: int, amp: float = 0.05, curved_walls: bool = False)
                     warp="channel_curved_walls" if curved_walls else "channel", amp=amp)
 
 
+def mortar_box(n: int = 4, ngeo: int = 2, split: str = "st", amp: float = 0.04,
+               warp: str = "mortar_poly", boundary_bc: int = BC_WALL) -> Mesh:
+    """Non-conforming mesh: block A = [0,1]^3 with n^3 elements, block B =
+    [1,2]x[0,1]^2 with (2n, 2n, 2n) elements (split "st": every big face of A
+    at x = 1 matched to four small faces of B), (2n, 2n, n) (split "s": two
+    small faces along y, the big face's s) or (2n, n, 2n) (split "t": along
+    z).  Small face k of a big face covers the part of its (s,t) range given
+    by the mortar type (MORTAR_FOUR: k = i_s + 2 i_t; MORTAR_S: k = i_s;
+    MORTAR_T: k = i_t; i = 0 below the midpoint, 1 above).  Outer faces get
+    boundary_bc.  Block B's element (i, j, k) has index n^3 + i + nbx (j + nby k)."""
+    ry, rz = {"st": (2, 2), "s": (2, 1), "t": (1, 2)}[split]
+    mtype = {"st": MORTAR_FOUR, "s": MORTAR_S, "t": MORTAR_T}[split]
+    per = (False, False, False)
+    A = box_mesh((n, n, n), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), ngeo, per, warp, amp, boundary_bc)
+    fd = (2 * n, ry * n, rz * n)
+    B = box_mesh(fd, (1.0, 0.0, 0.0), (2.0, 1.0, 1.0), ngeo, per, warp, amp, boundary_bc)
+    Ea, Eb = A.nelem, B.nelem
+    xgeo = np.concatenate([A.xgeo, B.xgeo])
+    nbrB = np.where(B.neighbor >= 0, B.neighbor + Ea, -1).astype(np.int32)
+    neighbor = np.concatenate([A.neighbor, nbrB])
+    nbr_face = np.concatenate([A.nbr_face, B.nbr_face])
+    bc = np.concatenate([A.bc, B.bc])
+    shift = np.concatenate([A.shift, B.shift])
+    mortar = np.full((n * n, 9), -1, np.int32)
+    mortar[:, 0] = mtype
+    for kc in range(n):
+        for jc in range(n):
+            m = jc + n * kc
+            big = (n - 1) + n * (jc + n * kc)
+            neighbor[big, 1], nbr_face[big, 1], bc[big, 1] = m, -1, BC_MORTAR
+            for it in range(rz):
+                for is_ in range(ry):
+                    jf, kf = ry * jc + is_, rz * kc + it
+                    small = Ea + 0 + fd[0] * (jf + fd[1] * kf)
+                    slot = is_ + 2 * it if mtype == MORTAR_FOUR else (is_ if ry == 2 else it)
+                    mortar[m, 1 + slot], mortar[m, 5 + slot] = small, 0
+                    neighbor[small, 0], nbr_face[small, 0], bc[small, 0] = big, 1, BC_INTERNAL
+    lo = np.zeros((Ea + Eb, 3))
+    h = np.zeros((Ea + Eb, 3))
+    for blk, (dims, off, base) in enumerate(((A.dims, (0.0, 0.0, 0.0), 0),
+                                             (fd, (1.0, 0.0, 0.0), Ea))):
+        e = np.arange(dims[0] * dims[1] * dims[2])
+        ijk = (e % dims[0], (e // dims[0]) % dims[1], e // (dims[0] * dims[1]))
+        for d in range(3):
+            h[base + e, d] = 1.0 / dims[d]
+            lo[base + e, d] = off[d] + ijk[d] / dims[d]
+    return Mesh(Ea + Eb, ngeo, xgeo, neighbor, nbr_face, bc, shift, dims=(3 * n, n, n),
+                lo=(0.0, 0.0, 0.0), hi=(2.0, 1.0, 1.0), warp=warp, amp=amp,
+                extra=dict(elem_lo=lo, elem_h=h, split=split), mortar=mortar)
+
+
 def _element_points(mesh: Mesh, ref: torch.Tensor, elem: torch.Tensor):
     """Analytic physical position of reference points ref[..., 3] in elements
     elem[...] (straight lattice map followed by the warp)."""
+    if "elem_lo" in mesh.extra:
+        # blocks of different resolution: per-element lower corner and size
+        lo = torch.as_tensor(mesh.extra["elem_lo"], device=elem.device)[elem.long()]
+        h = torch.as_tensor(mesh.extra["elem_h"], device=elem.device)[elem.long()]
+        X, Y, Z = (lo[..., d] + 0.5 * (ref[..., d] + 1.0) * h[..., d] for d in range(3))
+        return _warp_torch(mesh.warp, mesh.amp, X, Y, Z)
     nx, ny, nz = mesh.dims
     i = elem % nx
     j = (elem // nx) % ny
@@ -393,6 +469,32 @@ def curved_channel(dims=(32, 32, 32), ngeo=2, N=5, P=1_000_000, nsteps=200, seed
         dd = torch.full((P,), dval, dtype=torch.float64, device=device)
     return Workload("curved_channel", mesh, N, 0, U, x, vel, dd, el, mu, rho_p, 1, dt, nsteps,
                     precision, guess=guess, info=dict(scale=scale))
+
+
+def mortar_tgv(n=3, ngeo=2, split="st", N=4, P=400, nsteps=40, seed=0, device="cpu",
+               precision="fp64", st=(0.1, 100.0), rho_p=1000.0, mu=1e-5, dt=2e-3,
+               warp=None, amp=0.04) -> Workload:
+    """Non-conforming two-block box (mortar_box) with the Taylor-Green vortex of
+    period 1 and Schiller-Naumann drag; particles start at the fluid velocity
+    times 4 plus N(0, 1.5^2) noise, in the elements next to the mortar
+    interface at x = 1, so that they cross it both ways and hit the walls
+    within a few steps."""
+    warp = warp or ("mortar_trilinear" if ngeo == 1 else "mortar_poly")
+    mesh = mortar_box(n, ngeo, split, amp, warp)
+    U = fluid_tgv(mesh, N, 0, device)
+    # owners drawn from the elements next to the interface: the last column of
+    # the coarse block and the first two of the fine one
+    lo = mesh.extra["elem_lo"]
+    near = np.flatnonzero((lo[:, 0] >= 1.0 - 1.0 / n - 1e-12) & (lo[:, 0] < 1.0 + 1.0 / n - 1e-12))
+    pick = torch.randint(0, len(near), (P,), generator=torch.Generator().manual_seed(seed + 1))
+    x, el = seed_particles(mesh, P, seed, device=device, elem=near[pick.numpy()])
+    u, v, w = tgv_velocity(x[:, 0], x[:, 1], x[:, 2])
+    gen = torch.Generator(device="cpu").manual_seed(seed + 104729)
+    vel = 4.0 * torch.stack([u, v, w], dim=1) + 1.5 * torch.randn(
+        (P, 3), generator=gen, dtype=torch.float64).to(device)
+    dd = stokes_diameters(P, st[0], st[1], mu, rho_p, seed, device=device)
+    return Workload(f"mortar_{split}", mesh, N, 0, U, x, vel, dd, el, mu, rho_p, 1, dt, nsteps,
+                    precision)
 
 
 def batched_boxes(nbox=128, seed=1, device="cpu", side_range=(8, 40), N_set=(3, 4, 5, 6, 7),

@@ -784,3 +784,79 @@ def test_push_with_lift_drifts_toward_faster_fluid_and_deposits_it():
     FS = oracle.saffman_force(oracle.make_params(lift=1, **common), 1.2, rel,
                               np.array([0.0, 0.0, -g]), d[0])
     assert abs(S1[:, 1].sum() + FS[1]) <= 1e-9 * abs(FS[1])
+
+
+# ---------------------------------------------------------------------------
+# non-conforming (mortar) faces, Sec. 3.2.3
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("split,ngeo", [("st", 1), ("st", 3), ("s", 2), ("t", 2)])
+def test_mortar_small_faces_tile_the_big_face(split, ngeo):
+    """The generator's small faces are the parts of the big face that the row
+    layout names: mapped into the big element, the corners of small face k lie
+    on the big face (xi_1 = +1) at the corners of its half / quarter."""
+    warp = "mortar_trilinear" if ngeo == 1 else "mortar_poly"
+    mesh = W.mortar_box(2, ngeo, split, warp=warp)
+    orc = oracle.Oracle(mesh.as_dict())
+    g = ngeo + 1
+    p = oracle.make_params()
+    for m, row in enumerate(mesh.mortar):
+        big = int(np.flatnonzero((mesh.bc[:, 1] == W.BC_MORTAR) & (mesh.neighbor[:, 1] == m))[0])
+        ns = 4 if row[0] == W.MORTAR_FOUR else 2
+        for q in range(ns):
+            es, fs = int(row[1 + q]), int(row[5 + q])
+            assert fs == 0
+            X = mesh.xgeo[es].reshape(g, g, g, 3)  # [c][b][a]
+            i_s = q % 2 if row[0] != W.MORTAR_T else 0
+            i_t = (q // 2 if row[0] == W.MORTAR_FOUR else (q if row[0] == W.MORTAR_T else 0))
+            for cb, cc in ((0, 0), (g - 1, 0), (0, g - 1), (g - 1, g - 1)):
+                ok, xi, _ = orc.newton(big, X[cc, cb, 0], p)
+                assert ok
+                assert abs(xi[0] - 1.0) < 1e-12
+                s_lo, s_hi = (-1.0, 1.0) if row[0] == W.MORTAR_T else ((-1.0, 0.0), (0.0, 1.0))[i_s]
+                t_lo, t_hi = (-1.0, 1.0) if row[0] == W.MORTAR_S else ((-1.0, 0.0), (0.0, 1.0))[i_t]
+                want_s = s_lo if cb == 0 else s_hi
+                want_t = t_lo if cc == 0 else t_hi
+                assert abs(xi[1] - want_s) < 1e-12 and abs(xi[2] - want_t) < 1e-12
+
+
+def _mortar_run(wl):
+    orc = oracle.Oracle(wl.mesh.as_dict())
+    orc.set_fluid(wl.N, 0, _np(wl.U))
+    p = oracle.make_params(mu=wl.mu, rho_p=wl.rho_p, drag_law=wl.drag_law)
+    out = orc.push(p, _np(wl.x), _np(wl.v), _np(wl.d), _np(wl.elem), nsteps=wl.nsteps, dt=wl.dt)
+    return orc, out
+
+
+@pytest.mark.parametrize("split,ngeo", [("st", 1), ("st", 3), ("s", 2), ("t", 2), ("st", 4)])
+def test_mortar_tracking_owner_is_bruteforce_owner(split, ngeo):
+    """Tracking across big -> small and small -> big mortar faces ends every
+    particle in the one element that brute-force location finds."""
+    wl = W.mortar_tgv(3, ngeo, split, N=3, P=120, nsteps=40)
+    orc, out = _mortar_run(wl)
+    assert np.all(out["status"] & oracle.ST_FROZEN == 0)
+    Ea = 27
+    start_a, end_a = _np(wl.elem) < Ea, out["elem"] < Ea
+    assert np.sum(start_a & ~end_a) >= 5 and np.sum(~start_a & end_a) >= 5
+    ncheck = 0
+    for i in range(len(out["elem"])):
+        if out["status"][i] & oracle.ST_NEAR_FACE:
+            continue
+        owners = orc.locate_bruteforce(out["x"][i], tol=1e-10)
+        assert list(owners) == [out["elem"][i]], (i, owners, out["elem"][i])
+        ncheck += 1
+    assert ncheck >= 110
+
+
+def test_mortar_entry_face_is_found_by_intersection_not_by_row_order():
+    """The small face entered is the one the ray crosses (the search on the
+    small faces), so permuting a row's small faces changes nothing."""
+    wl = W.mortar_tgv(3, 2, "st", N=3, P=120, nsteps=40)
+    _, out = _mortar_run(wl)
+    perm = wl.mesh.mortar.copy()
+    perm[:, 1:5] = perm[:, [4, 3, 2, 1]]
+    perm[:, 5:9] = perm[:, [8, 7, 6, 5]]
+    wl.mesh.mortar = perm
+    _, out2 = _mortar_run(wl)
+    for k in ("x", "v", "elem", "hits", "status"):
+        assert np.array_equal(out[k], out2[k]), k
