@@ -13,7 +13,9 @@
 //   layers 2, 3: [32 x 64] x [64 x 64], accumulators initialised with the bias;
 //   output: [32 x 64] x [64 x 8] (3 columns used).
 // GELU runs on packed BF16 pairs -- its result is rounded to BF16 for the next
-// product anyway.
+// product anyway.  Its factor 1/2 is moved into the weights of the layer that
+// consumes it (layers 2, 3 and the output), which is exact in BF16: the
+// hidden activations are 2 GELU(z).
 #pragma once
 #include <cuda_bf16.h>
 
@@ -36,30 +38,30 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// GELU in its tanh form, 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)))
+// Twice the GELU in its tanh form, z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)))
 // (Hendrycks & Gimpel 2016), on a packed pair, in BF16 arithmetic with the
 // hardware tanh approximation: within a few BF16 ulps of the erf form the
 // network was trained with.
-__device__ __forceinline__ uint32_t gelu_bf16x2(float z0, float z1) {
+__device__ __forceinline__ uint32_t gelu2_bf16x2(float z0, float z1) {
   const uint32_t z = pack_bf16(z0, z1);
-  // sqrt(2/pi) * 0.044715 and sqrt(2/pi) and 0.5, as bf16 pairs
-  const uint32_t ka = 0x3D123D12u, kc = 0x3F4C3F4Cu, kh = 0x3F003F00u;
-  uint32_t z2, p, u, t, h, out;
+  // sqrt(2/pi) * 0.044715 and sqrt(2/pi), as bf16 pairs
+  const uint32_t ka = 0x3D123D12u, kc = 0x3F4C3F4Cu;
+  uint32_t z2, p, u, t, out;
   asm("mul.rn.bf16x2 %0, %1, %1;" : "=r"(z2) : "r"(z));
   asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(p) : "r"(z2), "r"(ka), "r"(kc));
   asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(u) : "r"(z), "r"(p));
   asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(u));
-  asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(h) : "r"(z), "r"(kh));
-  asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(out) : "r"(h), "r"(t));
+  asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(out) : "r"(z), "r"(t));
   return out;
 }
 
 // Fills the block's weight copy (call by every thread, followed by __syncthreads).
 __device__ __forceinline__ void mlp_load(MlpSmem& s, const DevMLP& p) {
+  // layers that consume a hidden activation carry GELU's factor 1/2
   for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
     const int o = i >> 6, c = i & 63;
-    s.w[0][o * MLP_LD + c] = __ushort_as_bfloat16(p.w2[i]);
-    s.w[1][o * MLP_LD + c] = __ushort_as_bfloat16(p.w3[i]);
+    s.w[0][o * MLP_LD + c] = __float2bfloat16_rn(0.5f * __bfloat162float(__ushort_as_bfloat16(p.w2[i])));
+    s.w[1][o * MLP_LD + c] = __float2bfloat16_rn(0.5f * __bfloat162float(__ushort_as_bfloat16(p.w3[i])));
   }
   for (int i = threadIdx.x; i < 64 * MLP_LD1; i += blockDim.x) {
     const int o = i / MLP_LD1, k = i - o * MLP_LD1;
@@ -67,7 +69,7 @@ __device__ __forceinline__ void mlp_load(MlpSmem& s, const DevMLP& p) {
   }
   for (int i = threadIdx.x; i < 8 * MLP_LD; i += blockDim.x) {
     const int q = i / MLP_LD, c = i - q * MLP_LD;
-    s.w4[i] = __float2bfloat16_rn(q < 3 && c < 64 ? p.w4[q * 64 + c] : 0.f);
+    s.w4[i] = __float2bfloat16_rn(q < 3 && c < 64 ? 0.5f * p.w4[q * 64 + c] : 0.f);
   }
   for (int i = threadIdx.x; i < 64; i += blockDim.x) {
     s.b[0][i] = p.b2[i];
@@ -108,10 +110,10 @@ __device__ __forceinline__ void acc_to_operand(uint32_t (&A)[2][4][4], const flo
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int kt = half * 2 + j;
-      A[mt][kt][0] = gelu_bf16x2(acc[mt][2 * j][0], acc[mt][2 * j][1]);
-      A[mt][kt][1] = gelu_bf16x2(acc[mt][2 * j][2], acc[mt][2 * j][3]);
-      A[mt][kt][2] = gelu_bf16x2(acc[mt][2 * j + 1][0], acc[mt][2 * j + 1][1]);
-      A[mt][kt][3] = gelu_bf16x2(acc[mt][2 * j + 1][2], acc[mt][2 * j + 1][3]);
+      A[mt][kt][0] = gelu2_bf16x2(acc[mt][2 * j][0], acc[mt][2 * j][1]);
+      A[mt][kt][1] = gelu2_bf16x2(acc[mt][2 * j][2], acc[mt][2 * j][3]);
+      A[mt][kt][2] = gelu2_bf16x2(acc[mt][2 * j + 1][0], acc[mt][2 * j + 1][1]);
+      A[mt][kt][3] = gelu2_bf16x2(acc[mt][2 * j + 1][2], acc[mt][2 * j + 1][3]);
     }
 }
 
