@@ -142,7 +142,7 @@ def make_workload(args, device, seed, precision):
 # DRAM bytes per particle-step of k_push, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum of the push kernel on the 32^3, 10^6-particle case, per
 # particle-step; see profiles/); traffic scales with the particles processed.
-TRAFFIC_BYTES_PER_PARTICLE_STEP = 132.0
+TRAFFIC_BYTES_PER_PARTICLE_STEP = 136.0
 
 
 def algorithmic_flops_per_particle_stage(G=4, NP=6, ntri=2, it_full=2.0, it_resid=2.0):
