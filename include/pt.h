@@ -219,7 +219,8 @@ pt_status pt_set_fluid(pt_ctx* ctx, int32_t N, int32_t node_type, const void* U_
  * drag (Eqs. dragforce, dragfactor) plus gravity, the RK update of x and v,
  * and tracking of the straight stage segment (Eq. parttrajectory) through
  * element faces with specular reflection at walls (Sec. 2.4), periodic
- * translation and removal at open faces.
+ * translation, removal at open faces and, across the big side of a mortar,
+ * entry by the small face the segment crosses (Sec. 3.2.3).
  * out: host pointer or NULL; when non-NULL the call synchronises the stream
  * and fills the totals.  Returns PT_OK, or (only when out != NULL) the first
  * of PT_ERR_NEWTON / PT_ERR_LOST / PT_ERR_CROSS whose count is non-zero, or
