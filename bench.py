@@ -142,7 +142,9 @@ def make_workload(args, device, seed, precision):
 # DRAM bytes per particle-step of k_push, from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum of the push kernel on the 32^3, 10^6-particle case, per
 # particle-step; see profiles/); traffic scales with the particles processed.
-TRAFFIC_BYTES_PER_PARTICLE_STEP = 136.0
+# None while the kernel has changed since the last capture (the capture of
+# 136 B per particle-step predates the FP32-decided face crossings).
+TRAFFIC_BYTES_PER_PARTICLE_STEP = None
 
 
 def algorithmic_flops_per_particle_stage(G=4, NP=6, ntri=2, it_full=2.0, it_resid=2.0):
@@ -483,15 +485,17 @@ def main():
     fp32_peak = fp32_peak_tflops(clk_max_mhz=2070.0)
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak,
-                "traffic": TRAFFIC_BYTES_PER_PARTICLE_STEP * P * args.inner,
+                "traffic": (TRAFFIC_BYTES_PER_PARTICLE_STEP * P * args.inner
+                            if TRAFFIC_BYTES_PER_PARTICLE_STEP else None),
                 "kernel": "k_push<4,6,fp32,%s>" % ("learned" if guess else "trilinear"),
                 "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                 "flops_per_particle_stage": flops_stage,
                 "newton_iterations_per_stage": {"full": it32, "residual_only": it64},
                 "launch_ms": avg_launch_s * 1e3,
                 "kernel_share_of_step": (kern_ms / ms) if ms > 0 else None,
-                "hbm_frac_of_measured": (TRAFFIC_BYTES_PER_PARTICLE_STEP * P * args.inner
-                                         / avg_launch_s / 1e9) / float(peaks.get("hbm_gbs", 6800.0))}
+                "hbm_frac_of_measured": ((TRAFFIC_BYTES_PER_PARTICLE_STEP * P * args.inner
+                                          / avg_launch_s / 1e9) / float(peaks.get("hbm_gbs", 6800.0))
+                                         if TRAFFIC_BYTES_PER_PARTICLE_STEP else None)}
     if guess:
         # the learned start's own products run on the tensor cores (BF16, FP32
         # accumulate): 3x64 + 2 x 64x64 + 64x3 multiply-adds per particle-stage

@@ -23,6 +23,11 @@
 #ifndef PT_FACE_SCREEN
 #define PT_FACE_SCREEN 1
 #endif
+// 1 (FP32 mode): an internal or periodic crossing that the FP32 screen finds
+// unambiguous is taken without the FP64 solve (see track_slow)
+#ifndef PT_FP32_DECIDE
+#define PT_FP32_DECIDE 1
+#endif
 
 namespace pt {
 
@@ -1452,9 +1457,26 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
     const float xlf[3] = {(float)xl[0], (float)xl[1], (float)xl[2]};
     double best = 1e300, bs = 0.0, bt = 0.0;
     int bf = -1;
+    // FP32 decision (FP32 mode): when exactly one face survives the screen,
+    // it is internal or periodic, and its only FP32 crossing lies clearly
+    // inside the face (max(|s|,|t|) < 1 - dl) and clearly inside the segment
+    // (by the screen's margin ta, ~100x the FP32 error) while its other roots
+    // are clearly outside, that crossing decides the exit face without the
+    // FP64 solve: the owner follows from the face alone, the position is the
+    // stage end point, and no near-face band can be met.  Otherwise the
+    // provisional faces are solved exactly in a second pass.
+    constexpr bool kFast = PT_FP32_DECIDE && PT_FACE_SCREEN && std::is_same<R, float>::value;
+    int pf = -1, npro = 0;
+    bool exact_seen = false;
+    float pa32 = 0.f, ps32 = 0.f, pt32 = 0.f;
+    unsigned redo = 0u;
+#pragma unroll 1
+    for (int pass = 0; pass < (kFast ? 2 : 1); ++pass) {
+    if (pass == 1 && (pf < 0 || (npro == 1 && !exact_seen))) break;
 #pragma unroll 1
     for (int f = 0; f < 6; ++f) {
       if (f == fin) continue;
+      if (pass == 1 && !((redo >> f) & 1u)) continue;
       // slab prefilter (FP32, conservative: the margins cover its rounding)
       const float* sl = m.slab + 48 * (size_t)e + 8 * f;
       const float cosf_ = __ldg(sl) * tdf[0] + __ldg(sl + 1) * tdf[1] + __ldg(sl + 2) * tdf[2];
@@ -1476,20 +1498,46 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
         const float ta = 1e-4f * (__ldg(sl + 5) + Lf) / fmaxf(fabsf(cosf_), 1e-2f) +
                          4.f * (float)k.band_x;
         const float a0f = (float)a0;
-        bool any = ill;
+        const float dl = fmaxf(1e-3f, 2.f * (float)k.band_ref);
+        bool any = ill, amb = ill;
+        int nin = 0, iin = 0;
         #pragma unroll 1
         for (int i = 0; i < n32 && !ill; ++i) {
           if (kind == PT_FACE_CURVED &&
               !curved_newton_f32<G>(m.xg32 + (size_t)e * 3 * G * G * G, f, xlf, tdf, k, fs[i],
                                     ft[i], fa[i])) {
             any = true;
+            amb = true;
             break;
           }
           const float mm = fmaxf(fabsf(fs[i]), fabsf(ft[i]));
           if (!(fa[i] < a0f - ta || fa[i] > Lf + ta || mm > 1.f + 1e-3f)) any = true;
+          if constexpr (kFast) {
+            const bool out = fa[i] < a0f - ta || fa[i] > Lf + ta || mm > 1.f + dl;
+            if (mm < 1.f - dl && fa[i] > a0f + ta && fa[i] < Lf - ta) {
+              ++nin;
+              iin = i;
+            } else if (!out) {
+              amb = true;
+            }
+          }
         }
         if (!any) continue;
+        if constexpr (kFast) {
+          const int bcf = finfo_bc(info);
+          if (pass == 0 && !amb && nin == 1 && !(CLIP && kind == PT_FACE_CURVED) &&
+              (bcf == PT_BC_INTERNAL || bcf == PT_BC_PERIODIC)) {
+            ++npro;
+            pf = f;
+            pa32 = fa[iin];
+            ps32 = fs[iin];
+            pt32 = ft[iin];
+            redo |= 1u << f;
+            continue;
+          }
+        }
       }
+      exact_seen = true;
       const double* Bf = m.bil + 72 * (size_t)e + 12 * f;
       double Bl[12];
 #pragma unroll
@@ -1548,6 +1596,13 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
           bt = t;
         }
       }
+    }
+    }
+    if (kFast && pf >= 0 && npro == 1 && !exact_seen) {
+      best = (double)pa32;
+      bf = pf;
+      bs = (double)ps32;
+      bt = (double)pt32;
     }
     if (bf < 0) break;
     const int info = __ldg(m.finfo + 6 * (size_t)e + bf);
