@@ -119,3 +119,60 @@ def test_particle_set_never_aliases_its_inputs():
     ps.elem[0] = 99
     ps.d[0] = -1.0
     assert int(el[0]) == 0 and float(d[0]) >= 0.0
+
+
+def _init_rc(md):
+    """pt_init_mesh on a mesh description; returns (status, message).  Only
+    malformed meshes are passed: they are rejected before any device call."""
+    from paper_2211_05458_gb300 import build, pt
+    build.build()
+    L = pt.lib()
+    keep = {k: np.ascontiguousarray(md[k], dtype=np.float64 if k in ("xgeo", "shift")
+                                    else np.int32)
+            for k in ("xgeo", "neighbor", "nbr_face", "bc", "shift", "mortar")}
+    d = pt.MeshDesc()
+    d.nelem, d.ngeo = int(md["nelem"]), int(md["ngeo"])
+    for k in ("xgeo", "neighbor", "nbr_face", "bc", "shift"):
+        setattr(d, k, keep[k].ctypes.data)
+    d.nmortar = len(keep["mortar"])
+    d.mortar = keep["mortar"].ctypes.data if len(keep["mortar"]) else None
+    cfg = pt.default_config()
+    h = ctypes.c_void_p()
+    rc = L.pt_init_mesh(ctypes.byref(h), ctypes.byref(d), ctypes.byref(cfg), None)
+    assert not h.value
+    return rc, L.pt_last_error(None).decode()
+
+
+def _edit(md, key, idx, val):
+    out = {k: (v.copy() if hasattr(v, "copy") else v) for k, v in md.items()}
+    out[key][idx] = val
+    return out
+
+
+def test_mesh_validation_rejects_malformed_connectivity():
+    """Host-side checks of pt_init_mesh (conforming and mortar connectivity,
+    boundary kinds, shifts), each with its own message."""
+    from paper_2211_05458_gb300 import pt
+    md = W.mortar_box(2, 2, "st").as_dict()
+    big = int(np.flatnonzero(md["bc"][:, 1] == W.BC_MORTAR)[0])
+    small = int(md["mortar"][0, 1])
+    cases = [
+        (_edit(md, "mortar", (0, 0), 7), "bad type"),
+        (_edit(md, "mortar", (0, 0), W.MORTAR_S), "must be unused"),
+        (_edit(md, "mortar", (0, 1), 0), "not a small face"),
+        (_edit(md, "mortar", (0, 5), 3), "not a small face"),
+        (_edit(md, "neighbor", (big, 1), 99), "bad mortar row"),
+        (_edit(md, "neighbor", (big, 1), (md["neighbor"][big, 1] + 1) % len(md["mortar"])),
+         "referenced twice"),
+        (_edit(md, "nbr_face", (small, 0), 2), "does not point back"),
+        (_edit(md, "bc", (0, 0), 5), "bad bc"),
+        (_edit(md, "shift", (0, 0, 0), 1.0), "shift on a non-periodic face"),
+        (dict(md, mortar=md["mortar"][:-1]), "bad mortar row"),
+        (dict(md, ngeo=5), "ngeo"),
+    ]
+    box = W.box_mesh((3, 3, 3), (0, 0, 0), (1, 1, 1), 1).as_dict()
+    cases.append((_edit(box, "neighbor", (0, 1), 5), "does not point back"))
+    for mdx, msg in cases:
+        rc, err = _init_rc(mdx)
+        assert rc == pt.PT_ERR_ARG, (msg, rc, err)
+        assert msg in err, (msg, err)
