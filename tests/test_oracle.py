@@ -231,38 +231,67 @@ def test_stokes_relaxation_discrete_and_analytic():
     assert np.allclose(out["x"][0] - shift, xex, atol=1e-6)
 
 
-@pytest.mark.parametrize("St", [0.1, 1.0, 10.0])
+def _golden(name):
+    """key = value fixture under tests/golden (lists comma-separated)."""
+    import os
+    out = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", name)):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            k, v = (t.strip() for t in line.split("=", 1))
+            vals = [float(x) for x in v.split(",")]
+            out[k] = vals if len(vals) > 1 else vals[0]
+    return out
+
+
+_SEC51 = _golden("sec5_1_high_order_time_integration.txt")
+
+
+@pytest.mark.parametrize("St", _SEC51["stokes_numbers"])
 def test_high_order_time_integration_case(St):
-    """Sec. 5.1: linear shear u = (y/y0, 0, 0), gravity in y, drag on x only."""
-    y0, g = 2.0, -9.81
-    mesh = W.box_mesh((2, 4, 2), (0.0, 0.5, 0.0), (2.0, 4.5, 2.0), 1,
+    """Sec. 5.1 with the printed setup: linear shear u = (y/y0, 0, 0), gravity
+    in y, drag on x only (f_D = 1), the printed time steps; the oracle's
+    position error against the analytic solution falls with the printed
+    order 4."""
+    G = _SEC51
+    y0, g = G["y0"], G["gravity"][1]
+    n = int(G["elements_per_direction"])
+    lo, hi = G["domain_lo"], G["domain_hi"]
+    # reading: the printed start (0, 2, 0.5) lies on the boundary of [0,2]^3;
+    # the particle starts at (0.5, 2, 0.5) in [0,2] x [0.5,4.5] x [0,2], with
+    # elements of the printed size (the flow u = y/2 is unchanged)
+    shift = 0.5
+    mesh = W.box_mesh((n, 2 * n, n), (lo[0], lo[1] + shift, lo[2]),
+                      (hi[0], hi[1] + shift + (hi[1] - lo[1]), hi[2]), 1,
                       periodic=(False, False, False))
     N = 3
     U = W.fluid_linear_shear(mesh, N, y0)
     orc = oracle.Oracle(mesh.as_dict())
     orc.set_fluid(N, 0, _np(U))
-    tau = St * 2.0 / 1.0
+    # Eq. stokesnumber with u_c = y/2 = 1 at the start and L_c = 2
+    tau = St * G["characteristic_length"] / 1.0
     mu, rho_p = 1e-5, 1000.0
     d = math.sqrt(18 * mu * tau / rho_p)
     p = oracle.make_params(mu=mu, rho_p=rho_p, drag_law=0, g=(0, g, 0), mask=(1, 0, 0))
-    x0 = np.array([[0.5, y0, 0.5]])
+    x0 = np.array([[G["start_position"][0] + shift, G["start_position"][1],
+                    G["start_position"][2]]])
     e0 = orc.locate_bruteforce(x0[0])
     assert len(e0) == 1
-    T = 0.4
+    T = G["t_end"]
     c = g / (2 * y0)
-    x1 = 0.5 + T - tau * (1 - math.exp(-T / tau)) + c * (
+    x1 = x0[0, 0] + T - tau * (1 - math.exp(-T / tau)) + c * (
         T ** 3 / 3 - T ** 2 * tau + 2 * tau ** 2 * T + 2 * tau ** 3 * (math.exp(-T / tau) - 1))
     v1 = 1 - math.exp(-T / tau) + c * (T ** 2 - 2 * T * tau + 2 * tau ** 2 -
                                         2 * tau ** 2 * math.exp(-T / tau))
     errs = []
-    for k in range(4):
-        dt = 0.1 / 2 ** k
+    dts = sorted(G["dt"], reverse=True)
+    for dt in dts:
         out = orc.push(p, x0, np.zeros((1, 3)), [d], e0, nsteps=int(round(T / dt)), dt=dt)
         assert out["status"][0] & oracle.ST_FROZEN == 0
         assert abs(out["x"][0, 1] - (y0 + 0.5 * g * T ** 2)) < 1e-12
         assert abs(out["v"][0, 1] - g * T) < 1e-12
         errs.append(abs(out["x"][0, 0] - x1))
-        if k == 3:
+        if dt == dts[-1]:
             assert abs(out["v"][0, 0] - v1) < 1e-6
     errs = np.array(errs)
     slopes = np.log2(errs[:-1] / errs[1:])
@@ -271,7 +300,9 @@ def test_high_order_time_integration_case(St):
     # not yet dominate the truncation error
     usable = errs[1:] > 5e-11
     assert usable.sum() >= 1
-    assert np.all(slopes[usable] > 3.6) and np.all(slopes[usable] < 4.6), (errs, slopes)
+    order = G["order"]
+    assert np.all(slopes[usable] > order - 0.4) and np.all(slopes[usable] < order + 0.6), (
+        errs, slopes)
 
 
 def test_schiller_naumann_terminal_velocity():
