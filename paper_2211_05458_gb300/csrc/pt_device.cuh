@@ -1472,131 +1472,131 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
     unsigned redo = 0u;
 #pragma unroll 1
     for (int pass = 0; pass < (kFast ? 2 : 1); ++pass) {
-    if (pass == 1 && (pf < 0 || (npro == 1 && !exact_seen))) break;
+      if (pass == 1 && (pf < 0 || (npro == 1 && !exact_seen))) break;
 #pragma unroll 1
-    for (int f = 0; f < 6; ++f) {
-      if (f == fin) continue;
-      if (pass == 1 && !((redo >> f) & 1u)) continue;
-      // slab prefilter (FP32, conservative: the margins cover its rounding)
-      const float* sl = m.slab + 48 * (size_t)e + 8 * f;
-      const float cosf_ = __ldg(sl) * tdf[0] + __ldg(sl + 1) * tdf[1] + __ldg(sl + 2) * tdf[2];
-      const float pa = __ldg(sl) * xlf[0] + __ldg(sl + 1) * xlf[1] + __ldg(sl + 2) * xlf[2];
-      const float pb = pa + Lf * cosf_;
-      if (fmaxf(pa, pb) < __ldg(sl + 3) || fminf(pa, pb) > __ldg(sl + 4)) continue;
-      const int info = __ldg(m.finfo + 6 * (size_t)e + f);
-      const int kind = finfo_kind(info);
-      // FP32 screen: skip the exact solve when every FP32 root is clearly
-      // outside the segment or the face (margins ~100x the FP32 error)
-      float fs[2], ft[2], fa[2];
-      bool ill = fabsf(cosf_) < 1e-2f;
-      if (PT_FACE_SCREEN) {
-        const float* Bf32 = m.bil32 + 72 * (size_t)e + 12 * f;
-        float B32[12];
+      for (int f = 0; f < 6; ++f) {
+        if (f == fin) continue;
+        if (pass == 1 && !((redo >> f) & 1u)) continue;
+        // slab prefilter (FP32, conservative: the margins cover its rounding)
+        const float* sl = m.slab + 48 * (size_t)e + 8 * f;
+        const float cosf_ = __ldg(sl) * tdf[0] + __ldg(sl + 1) * tdf[1] + __ldg(sl + 2) * tdf[2];
+        const float pa = __ldg(sl) * xlf[0] + __ldg(sl + 1) * xlf[1] + __ldg(sl + 2) * xlf[2];
+        const float pb = pa + Lf * cosf_;
+        if (fmaxf(pa, pb) < __ldg(sl + 3) || fminf(pa, pb) > __ldg(sl + 4)) continue;
+        const int info = __ldg(m.finfo + 6 * (size_t)e + f);
+        const int kind = finfo_kind(info);
+        // FP32 screen: skip the exact solve when every FP32 root is clearly
+        // outside the segment or the face (margins ~100x the FP32 error)
+        float fs[2], ft[2], fa[2];
+        bool ill = fabsf(cosf_) < 1e-2f;
+        if (PT_FACE_SCREEN) {
+          const float* Bf32 = m.bil32 + 72 * (size_t)e + 12 * f;
+          float B32[12];
 #pragma unroll
-        for (int q = 0; q < 12; ++q) B32[q] = __ldg(Bf32 + q);
-        const int n32 = bilinear_roots_f32(B32, xlf, tdf, n1f, n2f, fs, ft, fa, ill);
-        const float ta = 1e-4f * (__ldg(sl + 5) + Lf) / fmaxf(fabsf(cosf_), 1e-2f) +
-                         4.f * (float)k.band_x;
-        const float a0f = (float)a0;
-        const float dl = fmaxf(1e-3f, 2.f * (float)k.band_ref);
-        bool any = ill, amb = ill;
-        int nin = 0, iin = 0;
-        #pragma unroll 1
-        for (int i = 0; i < n32 && !ill; ++i) {
-          if (kind == PT_FACE_CURVED &&
-              !curved_newton_f32<G>(m.xg32 + (size_t)e * 3 * G * G * G, f, xlf, tdf, k, fs[i],
-                                    ft[i], fa[i])) {
-            any = true;
-            amb = true;
-            break;
-          }
-          const float mm = fmaxf(fabsf(fs[i]), fabsf(ft[i]));
-          if (!(fa[i] < a0f - ta || fa[i] > Lf + ta || mm > 1.f + 1e-3f)) any = true;
-          if constexpr (kFast) {
-            const bool out = fa[i] < a0f - ta || fa[i] > Lf + ta || mm > 1.f + dl;
-            if (mm < 1.f - dl && fa[i] > a0f + ta && fa[i] < Lf - ta) {
-              ++nin;
-              iin = i;
-            } else if (!out) {
+          for (int q = 0; q < 12; ++q) B32[q] = __ldg(Bf32 + q);
+          const int n32 = bilinear_roots_f32(B32, xlf, tdf, n1f, n2f, fs, ft, fa, ill);
+          const float ta = 1e-4f * (__ldg(sl + 5) + Lf) / fmaxf(fabsf(cosf_), 1e-2f) +
+                           4.f * (float)k.band_x;
+          const float a0f = (float)a0;
+          const float dl = fmaxf(1e-3f, 2.f * (float)k.band_ref);
+          bool any = ill, amb = ill;
+          int nin = 0, iin = 0;
+          #pragma unroll 1
+          for (int i = 0; i < n32 && !ill; ++i) {
+            if (kind == PT_FACE_CURVED &&
+                !curved_newton_f32<G>(m.xg32 + (size_t)e * 3 * G * G * G, f, xlf, tdf, k, fs[i],
+                                      ft[i], fa[i])) {
+              any = true;
               amb = true;
+              break;
+            }
+            const float mm = fmaxf(fabsf(fs[i]), fabsf(ft[i]));
+            if (!(fa[i] < a0f - ta || fa[i] > Lf + ta || mm > 1.f + 1e-3f)) any = true;
+            if constexpr (kFast) {
+              const bool out = fa[i] < a0f - ta || fa[i] > Lf + ta || mm > 1.f + dl;
+              if (mm < 1.f - dl && fa[i] > a0f + ta && fa[i] < Lf - ta) {
+                ++nin;
+                iin = i;
+              } else if (!out) {
+                amb = true;
+              }
+            }
+          }
+          if (!any) continue;
+          if constexpr (kFast) {
+            const int bcf = finfo_bc(info);
+            if (pass == 0 && !amb && nin == 1 && !(CLIP && kind == PT_FACE_CURVED) &&
+                (bcf == PT_BC_INTERNAL || bcf == PT_BC_PERIODIC)) {
+              ++npro;
+              pf = f;
+              pa32 = fa[iin];
+              ps32 = fs[iin];
+              pt32 = ft[iin];
+              redo |= 1u << f;
+              continue;
             }
           }
         }
-        if (!any) continue;
-        if constexpr (kFast) {
-          const int bcf = finfo_bc(info);
-          if (pass == 0 && !amb && nin == 1 && !(CLIP && kind == PT_FACE_CURVED) &&
-              (bcf == PT_BC_INTERNAL || bcf == PT_BC_PERIODIC)) {
-            ++npro;
-            pf = f;
-            pa32 = fa[iin];
-            ps32 = fs[iin];
-            pt32 = ft[iin];
-            redo |= 1u << f;
-            continue;
-          }
-        }
-      }
-      exact_seen = true;
-      const double* Bf = m.bil + 72 * (size_t)e + 12 * f;
-      double Bl[12];
+        exact_seen = true;
+        const double* Bf = m.bil + 72 * (size_t)e + 12 * f;
+        double Bl[12];
 #pragma unroll
-      for (int q = 0; q < 12; ++q) Bl[q] = __ldg(Bf + q);
-      constexpr int MR = CLIP ? 4 : 2;
-      double rs[MR], rt[MR], ra[MR];
-      int nr = 0;
-      const bool clip_all = CLIP && kind == PT_FACE_CURVED;
-      if constexpr (CLIP) {
-        if (clip_all)
-          nr = bezier_clip_roots<G>(X64, m.xg32 + (size_t)e * 3 * G * G * G, f, xl, td, n1, n2,
-                                    k, L, rs, rt, ra, MR);
-        else
+        for (int q = 0; q < 12; ++q) Bl[q] = __ldg(Bf + q);
+        constexpr int MR = CLIP ? 4 : 2;
+        double rs[MR], rt[MR], ra[MR];
+        int nr = 0;
+        const bool clip_all = CLIP && kind == PT_FACE_CURVED;
+        if constexpr (CLIP) {
+          if (clip_all)
+            nr = bezier_clip_roots<G>(X64, m.xg32 + (size_t)e * 3 * G * G * G, f, xl, td, n1, n2,
+                                      k, L, rs, rt, ra, MR);
+          else
+            nr = bilinear_roots(Bl, xl, td, n1, n2, rs, rt, ra);
+        } else {
           nr = bilinear_roots(Bl, xl, td, n1, n2, rs, rt, ra);
-      } else {
-        nr = bilinear_roots(Bl, xl, td, n1, n2, rs, rt, ra);
-      }
-      if (kind == PT_FACE_CURVED && !clip_all) {
-        // the curved face lies within dev of its bilinear patch: a bilinear
-        // crossing far beyond the segment cannot refine into one inside it
-        const double dev = (double)__ldg(sl + 6);
-        const double reach = 4.0 * dev / fmax((double)fabsf(cosf_), 0.05) + 2.0 * k.band_x;
-        int kk = 0;
+        }
+        if (kind == PT_FACE_CURVED && !clip_all) {
+          // the curved face lies within dev of its bilinear patch: a bilinear
+          // crossing far beyond the segment cannot refine into one inside it
+          const double dev = (double)__ldg(sl + 6);
+          const double reach = 4.0 * dev / fmax((double)fabsf(cosf_), 0.05) + 2.0 * k.band_x;
+          int kk = 0;
+          #pragma unroll 1
+          for (int i = 0; i < nr; ++i) {
+            double s = rs[i], t = rt[i], al = ra[i];
+            if (!(fabs(s) < 2.0 && fabs(t) < 2.0)) continue;
+            if (al > L + reach || al < a0 - reach) continue;
+            if (curved_refine<G>(X64, m.xg32 + (size_t)e * 3 * G * G * G, f, xl, td, k, s, t,
+                                 al, L)) {
+              bool dup = false;
+              for (int j = 0; j < kk; ++j)
+                if (fabs(rs[j] - s) < 1e-10 && fabs(rt[j] - t) < 1e-10) dup = true;
+              if (!dup) {
+                rs[kk] = s;
+                rt[kk] = t;
+                ra[kk] = al;
+                kk++;
+              }
+            }
+          }
+          nr = kk;
+        }
         #pragma unroll 1
         for (int i = 0; i < nr; ++i) {
-          double s = rs[i], t = rt[i], al = ra[i];
-          if (!(fabs(s) < 2.0 && fabs(t) < 2.0)) continue;
-          if (al > L + reach || al < a0 - reach) continue;
-          if (curved_refine<G>(X64, m.xg32 + (size_t)e * 3 * G * G * G, f, xl, td, k, s, t,
-                               al, L)) {
-            bool dup = false;
-            for (int j = 0; j < kk; ++j)
-              if (fabs(rs[j] - s) < 1e-10 && fabs(rt[j] - t) < 1e-10) dup = true;
-            if (!dup) {
-              rs[kk] = s;
-              rt[kk] = t;
-              ra[kk] = al;
-              kk++;
-            }
+          double al = ra[i], s = rs[i], t = rt[i];
+          double mm = fmax(fabs(s), fabs(t));
+          if (mm > 1.0 + k.band_ref) continue;
+          if (al < a0 - k.band_x || al > L + k.band_x) continue;
+          if (fabs(mm - 1.0) < k.band_ref || fabs(al - a0) < k.band_x || fabs(L - al) < k.band_x)
+            st |= PT_ST_NEAR_FACE;
+          if (mm <= 1.0 && al > a0 && al <= L && al < best) {
+            best = al;
+            bf = f;
+            bs = s;
+            bt = t;
           }
         }
-        nr = kk;
       }
-      #pragma unroll 1
-      for (int i = 0; i < nr; ++i) {
-        double al = ra[i], s = rs[i], t = rt[i];
-        double mm = fmax(fabs(s), fabs(t));
-        if (mm > 1.0 + k.band_ref) continue;
-        if (al < a0 - k.band_x || al > L + k.band_x) continue;
-        if (fabs(mm - 1.0) < k.band_ref || fabs(al - a0) < k.band_x || fabs(L - al) < k.band_x)
-          st |= PT_ST_NEAR_FACE;
-        if (mm <= 1.0 && al > a0 && al <= L && al < best) {
-          best = al;
-          bf = f;
-          bs = s;
-          bt = t;
-        }
-      }
-    }
     }
     if (kFast && pf >= 0 && npro == 1 && !exact_seen) {
       best = (double)pa32;
