@@ -607,10 +607,14 @@ def main():
         try:
             wl.U = wl.U.cpu()
             wl.x, wl.v, wl.d, wl.elem = wl.x.cpu(), wl.v.cpu(), wl.d.cpu(), wl.elem.cpu()
-            rate, threads, dt = OracleSample(wl).run(4000, 2)
+            osamp = OracleSample(wl)
+            rate, threads, dt = osamp.run(100_000, 2)
+            osamp.threads = 1
+            rate1, _, _ = osamp.run(2000, 2)
             line["cpu_baseline"] = {"value": rate, "unit": METRIC, "cores": threads,
-                                    "kind": "oracle",
-                                    "sample": "4000 particles x 2 time steps of the same workload"}
+                                    "kind": "oracle", "single_thread": rate1,
+                                    "sample": "100000 particles x 2 time steps of the same "
+                                              "workload (single thread: 2000 x 2)"}
         except Exception as e:  # pragma: no cover
             line["cpu_baseline"] = {"unavailable": str(e)[:200]}
     if rank == 0:
