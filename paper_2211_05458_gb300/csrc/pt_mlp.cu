@@ -134,7 +134,7 @@ __global__ void k_particle_features(DevMesh m, int64_t n, const double* x, const
 
 // Training pairs: element and reference point from the counter-based hash of
 // (seed, i); x = chi(xi) in FP64; label = FP64 Newton inverse of x from the
-// trilinear start (plain Newton is the judge of the learned start).
+// trilinear start (plain Newton measures the learned start's error).
 __global__ void k_mlp_pairs(DevMesh m, DevConsts k, int64_t n, uint64_t seed, const float* feat48,
                             float* in, float* tgt, unsigned* nfail) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
