@@ -652,6 +652,34 @@ def test_mlp_features_affine_element():
         assert np.abs(f[3:]).max() < 1e-13
 
 
+def test_mlp_features_quadratic_warp_closed_form():
+    """The 48 deviation features on elements of the warp y' = y + A x^2 (1 + z):
+    the trilinear map of the corners reproduces y and interpolates x^2 (1 + z)
+    linearly in x, so a node's y deviation is A (1 + z)(x - x0)(x - x1) (lattice
+    coordinates), divided by the y length of the element's xi2-edges."""
+    A = 0.05
+    mesh = W.box_mesh((2, 2, 2), (0.0, 0.0, 0.0), (1.0, 2.0, 1.0), 3,
+                      periodic=(False, False, False), warp="poly", amp=A)
+    orc = oracle.Oracle(mesh.as_dict())
+    hx, hy, hz = 0.5, 1.0, 0.5
+    for e in range(mesh.nelem):
+        i, k = e % 2, e // 4
+        x0, z0 = i * hx, k * hz
+        f = orc.mlp_features(e, mesh.xgeo[e].mean(axis=0))
+        want = []
+        for c in range(4):
+            for b in range(4):
+                for a in range(4):
+                    nb = (a in (0, 3)) + (b in (0, 3)) + (c in (0, 3))
+                    if nb not in (1, 2):
+                        continue
+                    x, z = x0 + a * hx / 3, z0 + c * hz / 3
+                    want.append(A * (1 + z) * (x - x0) * (x - x0 - hx) / hy)
+        assert len(want) == 48
+        assert np.allclose(f[3:], want, rtol=0, atol=1e-14), e
+        assert np.abs(np.asarray(want)).max() > 1e-3
+
+
 @pytest.mark.parametrize("n", range(2, 9))
 def test_quadrature_weights(n):
     # Gauss weights against numpy; GLL weights integrate polynomials of degree 2n-3
