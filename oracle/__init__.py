@@ -8,9 +8,8 @@ library: ``oracle.c`` is compiled here with gcc and driven through ctypes.
 Every routine restates the paper directly (see ``oracle.h`` for the section
 and equation each one follows).  Functions without an independent pin are
 listed in the module docstring of ``tests/test_oracle.py``; none is left
-"parity unpinned" except the synthetic channel fluid, a reading of the inputs
-rather than a computation of the method.  The 48 geometry features are pinned
-by closed forms on affine and on quadratically warped elements.
+"parity unpinned".  The 48 geometry features are pinned by closed forms on
+affine and on quadratically warped elements.
 """
 from __future__ import annotations
 

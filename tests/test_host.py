@@ -176,3 +176,30 @@ def test_mesh_validation_rejects_malformed_connectivity():
         rc, err = _init_rc(mdx)
         assert rc == pt.PT_ERR_ARG, (msg, rc, err)
         assert msg in err, (msg, err)
+
+
+def test_channel_flow_generator_properties():
+    """The synthetic channel turbulence is divergence-free (curl of a vector
+    potential), vanishes on the walls y = +-1, is periodic over [0, 2pi] x
+    [0, pi] in x and z, and its perturbation has the requested rms."""
+    g = torch.Generator().manual_seed(3)
+    n = 4000
+    x = torch.rand(n, generator=g, dtype=torch.float64) * 2 * np.pi
+    y = torch.rand(n, generator=g, dtype=torch.float64) * 1.8 - 0.9
+    z = torch.rand(n, generator=g, dtype=torch.float64) * np.pi
+    u, v, w, scale = W.channel_velocity(x, y, z, seed=5)
+    pert = torch.stack([u - (1 - y * y), v, w])
+    assert abs(float(torch.sqrt((pert ** 2).mean())) - 0.1) < 0.02
+    h = 1e-5
+
+    def vel(dx, dy, dz):
+        return W.channel_velocity(x + dx, y + dy, z + dz, seed=5, scale=scale)[:3]
+    div = ((vel(h, 0, 0)[0] - vel(-h, 0, 0)[0]) + (vel(0, h, 0)[1] - vel(0, -h, 0)[1]) +
+           (vel(0, 0, h)[2] - vel(0, 0, -h)[2])) / (2 * h)
+    assert float(div.abs().max()) < 1e-7
+    for yw in (-1.0, 1.0):
+        uw = W.channel_velocity(x, torch.full_like(x, yw), z, seed=5, scale=scale)[:3]
+        assert max(float(c.abs().max()) for c in uw) < 1e-14
+    ux = W.channel_velocity(x + 2 * np.pi, y, z + np.pi, seed=5, scale=scale)[:3]
+    u0 = W.channel_velocity(x, y, z, seed=5, scale=scale)[:3]
+    assert max(float((a - b).abs().max()) for a, b in zip(ux, u0)) < 1e-12
