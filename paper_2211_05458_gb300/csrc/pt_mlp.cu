@@ -445,7 +445,7 @@ static pt_status export_bf16(pt_ctx* c) {
   MCK(cudaMemcpyAsync(th.data(), s->theta, NPAR * 4, cudaMemcpyDeviceToHost, c->stream));
   MCK(cudaMemcpyAsync(s->norm, s->hnorm, NNORM * 4, cudaMemcpyHostToDevice, c->stream));
   MCK(cudaStreamSynchronize(c->stream));
-  const float* mean = s->hnorm;
+  // the input means are folded into the per-element layer-1 table (k_mlp_pre)
   const float* sd = s->hnorm + 51;
   const float* osc = s->hnorm + 102;
   std::vector<uint16_t> w2(4096), w3(4096);
