@@ -203,3 +203,36 @@ def test_channel_flow_generator_properties():
     ux = W.channel_velocity(x + 2 * np.pi, y, z + np.pi, seed=5, scale=scale)[:3]
     u0 = W.channel_velocity(x, y, z, seed=5, scale=scale)[:3]
     assert max(float((a - b).abs().max()) for a, b in zip(ux, u0)) < 1e-12
+
+
+def test_ctypes_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the sizes and field offsets that a
+    C compiler gives the structs of include/pt.h."""
+    import shutil
+    import subprocess
+    from paper_2211_05458_gb300 import pt
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = [("pt_config", pt.Config), ("pt_mesh_desc", pt.MeshDesc),
+             ("pt_particles", pt.CParticles), ("pt_stats", pt.Stats)]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "pt.h"', "int main(void) {"]
+    for cname, cls in pairs:
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                               text=True).stdout.splitlines():
+        *key, val = line.split()
+        got[tuple(key)] = int(val)
+    for cname, cls in pairs:
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
