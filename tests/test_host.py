@@ -61,6 +61,42 @@ def test_box_mesh_connectivity_is_symmetric(periodic):
             assert np.array_equal(xg[e, :, :, g - 1], xg[nb, :, :, 0])
 
 
+@pytest.mark.parametrize("split", ["st", "s", "t"])
+def test_mortar_box_connectivity(split):
+    """Conforming faces point back; every big face names one mortar row whose
+    small faces name the big face back; small faces cover the big face once."""
+    m = W.mortar_box(3, 2, split)
+    seen = np.zeros(len(m.mortar), int)
+    for e in range(m.nelem):
+        for f in range(6):
+            nb, nf, bc = m.neighbor[e, f], m.nbr_face[e, f], m.bc[e, f]
+            if bc == W.BC_MORTAR:
+                seen[nb] += 1
+                row = m.mortar[nb]
+                ns = 4 if row[0] == W.MORTAR_FOUR else 2
+                assert np.all(row[1 + ns:5] == -1) and np.all(row[5 + ns:9] == -1)
+                for q in range(ns):
+                    es, fs = row[1 + q], row[5 + q]
+                    assert m.bc[es, fs] == W.BC_INTERNAL
+                    assert m.neighbor[es, fs] == e and m.nbr_face[es, fs] == f
+            elif bc == W.BC_INTERNAL and m.bc[nb, nf] == W.BC_MORTAR:
+                row = m.mortar[m.neighbor[nb, nf]]
+                assert any(row[1 + q] == e and row[5 + q] == f for q in range(4))
+            elif bc == W.BC_INTERNAL:
+                assert m.neighbor[nb, nf] == e and m.nbr_face[nb, nf] == f
+            else:
+                assert nb == -1
+    assert np.all(seen == 1)
+    # every small face is listed exactly once: 4 or 2 per row
+    ns = 4 if split == "st" else 2
+    n_small = sum(1 for e in range(m.nelem) for f in range(6)
+                  if m.bc[e, f] == W.BC_INTERNAL
+                  and m.bc[m.neighbor[e, f], m.nbr_face[e, f]] == W.BC_MORTAR)
+    assert n_small == len(m.mortar) * ns
+    listed = m.mortar[:, 1:1 + ns].ravel()
+    assert len(np.unique(listed)) == len(listed)
+
+
 def test_workloads_are_seeded():
     a = W.curved_channel((4, 4, 4), 2, 3, P=100, nsteps=1, seed=3)
     b = W.curved_channel((4, 4, 4), 2, 3, P=100, nsteps=1, seed=3)
