@@ -1673,6 +1673,14 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
 #pragma unroll
       for (int r = 0; r < 3; ++r) n1[r] *= in1;
       cross3d(td, n1, n2);
+      // and so do the FP32 copies that the slab test and the screen use
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        tdf[r] = (float)td[r];
+        n1f[r] = (float)n1[r];
+        n2f[r] = (float)n2[r];
+      }
+      Lf = (float)L;
       if (!(L > 0.0)) break;
     } else {
 #pragma unroll
