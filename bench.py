@@ -48,6 +48,9 @@ def parse():
                     help="c3 (default): the learned-start 64^3 channel; c1: 8^3 TGV box FP64; "
                          "c2: 32^3 NGeo=2 channel FP64; c4: 128 batched boxes FP32; "
                          "c5: 128x64x64 N=7 two-way channel FP32 with deposition")
+    ap.add_argument("--shard", action="store_true",
+                    help="c4 on several GPUs: split the same 128 boxes over the ranks by cost "
+                         "(strong scaling) instead of giving every rank its own 128 (weak)")
     return ap.parse_args()
 
 
@@ -60,6 +63,32 @@ def reduce_time_ms(ms: float, world: int, device=None) -> float:
     t = torch.tensor([ms], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int, device=None) -> float:
+    """Sum of a per-rank value over all ranks (the particles they advanced)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def shard_by_cost(costs, world: int):
+    """Greedy longest-processing-time split of independent units over ranks:
+    units in decreasing cost (lower index first on ties) go to the least
+    loaded rank (lowest rank on ties).  Returns one sorted index list per rank;
+    the largest load exceeds the smallest by at most one unit's cost."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0.0] * world
+    out = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        out[r].append(i)
+        load[r] += costs[i]
+    return [sorted(o) for o in out]
 
 
 def throughput(particles_per_rank: int, inner: int, steps: int, world: int, ms: float) -> float:
@@ -219,9 +248,16 @@ def fp64_peak_tflops(clk_max_mhz=2070.0, sms=152, dfma_per_clk=2):
     return sms * dfma_per_clk * 2 * clk_max_mhz * 1e6 / 1e12
 
 
-def config_workloads(cfg, dev, seed):
-    """The workloads other than the default one (seeded, synthetic)."""
+def config_workloads(cfg, dev, seed, shard=None):
+    """The workloads other than the default one (seeded, synthetic).  shard =
+    (rank, world): the 128 batched boxes (c4) split over the ranks by cost
+    P (N+1)^3, every rank drawing the same boxes."""
     from paper_2211_05458_gb300 import workloads as W
+    if cfg == "c4" and shard is not None:
+        rank, world = shard
+        prm = W.batched_box_params(nbox=128, seed=1)
+        mine = shard_by_cost([P * (N + 1) ** 3 for _, N, P in prm], world)[rank]
+        return W.batched_boxes(nbox=128, seed=1, device=dev, nsteps=50, select=mine)
     if cfg == "c1":
         return [W.tgv_box(8, 3, P=10_000, nsteps=100, seed=seed, device=dev)]
     if cfg == "c2":
@@ -248,7 +284,8 @@ def run_config(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     cfg = args.config
-    wls = config_workloads(cfg, dev, rank)
+    sharded = cfg == "c4" and args.shard and world > 1
+    wls = config_workloads(cfg, dev, rank, shard=(rank, world) if sharded else None)
     f64 = cfg in ("c1", "c2")
     prec = pt.FP64 if f64 else pt.FP32
     dt_ = torch.float64 if f64 else torch.float32
@@ -300,7 +337,8 @@ def run_config(args):
         if world > 1:
             dist.barrier()
     ms = reduce_time_ms(ev0.elapsed_time(ev1), world, dev)
-    value = P * inner * args.steps * world / (ms / 1e3)
+    P_all = sum_over_ranks(P, world, dev)  # ranks may hold different particle counts (c4)
+    value = P_all * inner * args.steps / (ms / 1e3)
     wl0 = wls[0]
     G, NP = wl0.mesh.ngeo + 1, wl0.N + 1
     # measured Newton iterations per particle-stage, from one more step with counters
@@ -328,16 +366,19 @@ def run_config(args):
     achieved = flops * 5 * value / world / 1e12
     names = {"c1": "TGV box 8^3 NGeo=1 N=3 Gauss, 10^4 particles, Stokes, FP64",
              "c2": "curved channel 32^3 NGeo=2 N=5 Gauss, 10^6 particles, Schiller-Naumann, FP64",
-             "c4": f"128 periodic TGV boxes (sides 8..40, N 3..7, {P} particles), FP32, "
+             "c4": f"128 periodic TGV boxes (sides 8..40, N 3..7, {int(P_all)} particles"
+                   + (" split over the GPUs by cost" if sharded else "") + "), FP32, "
                    "graph of 50 steps",
              "c5": "two-way channel 128x64x64 NGeo=2 N=7, 2x10^7 particles, FP32, push of "
                    f"{inner} steps + segmented deposition"}
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": warm, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong" if sharded else "weak",
+            "vs_baseline": None,
             "dtype": "f64" if f64 else "f32", "data": "synthetic",
             "config": {"workload": names[cfg], "inner_steps_per_call": inner,
-                       "parallelism": f"weak, {world} independent GPU(s)"},
+                       "parallelism": (f"{world} GPU(s), boxes split by cost P (N+1)^3"
+                                       if sharded else f"weak, {world} independent GPU(s)")},
             "gpu_launches": None, "clocks": clk.summary(),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "whole step",

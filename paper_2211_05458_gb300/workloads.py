@@ -497,17 +497,29 @@ def mortar_tgv(n=3, ngeo=2, split="st", N=4, P=400, nsteps=40, seed=0, device="c
                     precision)
 
 
-def batched_boxes(nbox=128, seed=1, device="cpu", side_range=(8, 40), N_set=(3, 4, 5, 6, 7),
-                  P_range=(1_000, 1_000_000), nsteps=50, dt=1e-3, scale_P=1.0):
-    """Independent periodic TGV boxes of uneven size: side log-uniform in
-    side_range, N uniform in N_set, particle count log-uniform in P_range."""
+def batched_box_params(nbox=128, seed=1, side_range=(8, 40), N_set=(3, 4, 5, 6, 7),
+                       P_range=(1_000, 1_000_000), scale_P=1.0):
+    """(side, N, P) of each box of batched_boxes, in order, without building them."""
     rng = np.random.default_rng(seed)
     out = []
-    for b in range(nbox):
+    for _ in range(nbox):
         side = int(round(math.exp(rng.uniform(math.log(side_range[0]), math.log(side_range[1])))))
         N = int(rng.choice(N_set))
         P = int(round(math.exp(rng.uniform(math.log(P_range[0]), math.log(P_range[1])))))
-        P = max(1, int(P * scale_P))
+        out.append((side, N, max(1, int(P * scale_P))))
+    return out
+
+
+def batched_boxes(nbox=128, seed=1, device="cpu", side_range=(8, 40), N_set=(3, 4, 5, 6, 7),
+                  P_range=(1_000, 1_000_000), nsteps=50, dt=1e-3, scale_P=1.0, select=None):
+    """Independent periodic TGV boxes of uneven size: side log-uniform in
+    side_range, N uniform in N_set, particle count log-uniform in P_range.
+    select: indices of the boxes to build (all if None); a box is the same
+    whichever others are built."""
+    params = batched_box_params(nbox, seed, side_range, N_set, P_range, scale_P)
+    out = []
+    for b in (range(nbox) if select is None else select):
+        side, N, P = params[b]
         wl = tgv_box(side, N, P, nsteps, seed=seed * 100003 + b, device=device,
                      precision="fp32", dt=dt)
         wl.name = f"box{b}"

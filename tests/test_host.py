@@ -124,7 +124,8 @@ def _rank_main(rank, world, port, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     ms = bench.reduce_time_ms(100.0 + 50.0 * rank, world)
     v = bench.throughput(1000, 10, 5, world, ms)
-    q.put((rank, ms, v))
+    p_all = bench.sum_over_ranks(1000.0 + 2000.0 * rank, world)
+    q.put((rank, ms, v, p_all))
     dist.destroy_process_group()
 
 
@@ -140,9 +141,30 @@ def test_weak_scaling_aggregation_two_ranks_gloo():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    for rank, ms, v in out:
+    for rank, ms, v, p_all in out:
         assert ms == 150.0  # max over ranks
         assert abs(v - 1000 * 10 * 5 * 2 / 0.15) < 1e-6 * v
+        assert p_all == 4000.0  # particles of both ranks (uneven, as with the batched boxes)
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 8])
+def test_batched_boxes_shard_by_cost(world):
+    """The 128 boxes split over ranks: each box once, loads within one box's
+    cost of each other, the same split on every rank, and a rank's boxes the
+    same as in the unsplit set."""
+    import bench
+    prm = W.batched_box_params(nbox=128, seed=1)
+    costs = [P * (N + 1) ** 3 for _, N, P in prm]
+    parts = bench.shard_by_cost(costs, world)
+    assert sorted(i for p in parts for i in p) == list(range(128))
+    loads = [sum(costs[i] for i in p) for p in parts]
+    assert max(loads) - min(loads) <= max(costs)
+    assert parts == bench.shard_by_cost(costs, world)
+    sel = parts[-1][:2]
+    a = W.batched_boxes(nbox=128, seed=1, select=sel, scale_P=1e-3)
+    for b, wl in zip(sel, a):
+        side, N, P = W.batched_box_params(nbox=128, seed=1, scale_P=1e-3)[b]
+        assert wl.mesh.dims == (side,) * 3 and wl.N == N and wl.x.shape[0] == P
 
 
 def test_particle_set_never_aliases_its_inputs():
