@@ -180,8 +180,10 @@ def test_particle_set_never_aliases_its_inputs():
 
 
 def _init_rc(md):
-    """pt_init_mesh on a mesh description; returns (status, message).  Only
-    malformed meshes are passed: they are rejected before any device call."""
+    """pt_init_mesh on a mesh description; returns (status, message).
+    Malformed meshes are rejected before any device call; a well-formed one
+    gets as far as the device allocation (PT_ERR_CUDA without a GPU; with one
+    the context is created and destroyed again)."""
     from paper_2211_05458_gb300 import build, pt
     build.build()
     L = pt.lib()
@@ -197,8 +199,11 @@ def _init_rc(md):
     cfg = pt.default_config()
     h = ctypes.c_void_p()
     rc = L.pt_init_mesh(ctypes.byref(h), ctypes.byref(d), ctypes.byref(cfg), None)
-    assert not h.value
-    return rc, L.pt_last_error(None).decode()
+    msg = L.pt_last_error(None).decode()
+    if h.value:
+        assert rc == pt.PT_OK
+        L.pt_destroy(h)
+    return rc, msg
 
 
 def _edit(md, key, idx, val):
@@ -234,6 +239,10 @@ def test_mesh_validation_rejects_malformed_connectivity():
         rc, err = _init_rc(mdx)
         assert rc == pt.PT_ERR_ARG, (msg, rc, err)
         assert msg in err, (msg, err)
+    # the well-formed meshes pass every host check
+    for mdx in (md, box, W.mortar_box(2, 3, "s").as_dict(), W.mortar_box(2, 1, "t").as_dict()):
+        rc, err = _init_rc(mdx)
+        assert rc in (pt.PT_OK, pt.PT_ERR_CUDA), (rc, err)
 
 
 def test_channel_flow_generator_properties():
