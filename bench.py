@@ -2,8 +2,10 @@
 
 Workload (default): the learned-guess curved channel -- 64^3 curved hexahedra
 (NGeo = 3) of [0,2pi]x[-1,1]x[0,pi], N = 5 on Gauss nodes, synthetic channel
-turbulence, 10^7 particles, Schiller-Naumann drag, FP32 push with FP64 final
-Newton iterations and FP64 face intersection, dt = 1e-3.
+turbulence, 10^7 particles, Schiller-Naumann drag, dt = 1e-3; FP32 push: FP32
+interpolation, drag and RK update, the final Newton iterations in double-float
+(FP32 pairs) to |dxi| < 1e-12, FP64 face intersection where FP32 cannot decide
+the crossing.
 A bench step is one pt_push call advancing every particle by --inner time
 steps (one element re-binning, then --inner x 5 RK stages).
 
@@ -29,6 +31,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s"
+# bounded oracle sample (particles, time steps) of the cpu_baseline leg and of
+# every step of --impl reference: about 10 s of work on a 16-core host
+REF_SAMPLE = (100_000, 2)
 
 
 def parse():
@@ -198,7 +203,19 @@ def algorithmic_flops_per_particle_stage(G=4, NP=6, ntri=2, it_full=2.0, it_resi
 
 
 def fp32_peak_tflops(clk_max_mhz=2070.0, sms=152, lanes=128):
+    """FP32 FMA rate from the unit counts and the maximum clock (context only;
+    the roofline uses the measured rate)."""
     return sms * lanes * 2 * clk_max_mhz * 1e6 / 1e12
+
+
+def alu_peaks(stream):
+    """Measured FP32 and FP64 FMA throughput (TFLOP/s) of this GPU from libpt's
+    probe kernels, with the SM count read from the device."""
+    import torch
+
+    from paper_2211_05458_gb300 import pt
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return {"fp32": pt.measure_peak(0, stream), "fp64": pt.measure_peak(1, stream), "sms": sms}
 
 
 def measured_peaks():
@@ -223,7 +240,7 @@ class OracleSample:
         self.d, self.el = H.np64(wl.d), H.np64(wl.elem).astype(np.int32)
         self.prm = H.oracle_params(wl)
         self.dt = wl.dt
-        self.threads = max_threads or min(os.cpu_count() or 1, 16)
+        self.threads = max_threads or (os.cpu_count() or 1)
         self.rng = np.random.default_rng(123)
 
     def run(self, sample_particles, sample_steps):
@@ -323,6 +340,8 @@ def run_config(args):
         step()
     torch.cuda.synchronize()
     dep_ev.clear()
+    for c in ctxs:
+        c.launch_count()  # clear
     with ClockSampler(local) as clk:
         if world > 1:
             dist.barrier()
@@ -337,6 +356,8 @@ def run_config(args):
         if world > 1:
             dist.barrier()
     ms = reduce_time_ms(ev0.elapsed_time(ev1), world, dev)
+    launches = sum(c.launch_count() for c in ctxs)
+    peaks_alu = alu_peaks(stream)
     P_all = sum_over_ranks(P, world, dev)  # ranks may hold different particle counts (c4)
     value = P_all * inner * args.steps / (ms / 1e3)
     wl0 = wls[0]
@@ -358,11 +379,11 @@ def run_config(args):
                                                      it_full=it32, it_resid=it64)
     if f64:
         # FP64 mode: the same operation count in FP64, against the FP64 rate
-        peak = fp64_peak_tflops()
-        peak_kind = "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz"
+        peak = peaks_alu["fp64"]
+        peak_kind = "measured: libpt FP64 FMA probe (pt_measure_peak)"
     else:
-        peak = fp32_peak_tflops()
-        peak_kind = "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+        peak = peaks_alu["fp32"]
+        peak_kind = "measured: libpt FP32 FMA probe (pt_measure_peak)"
     achieved = flops * 5 * value / world / 1e12
     names = {"c1": "TGV box 8^3 NGeo=1 N=3 Gauss, 10^4 particles, Stokes, FP64",
              "c2": "curved channel 32^3 NGeo=2 N=5 Gauss, 10^6 particles, Schiller-Naumann, FP64",
@@ -379,7 +400,7 @@ def run_config(args):
             "config": {"workload": names[cfg], "inner_steps_per_call": inner,
                        "parallelism": (f"{world} GPU(s), boxes split by cost P (N+1)^3"
                                        if sharded else f"weak, {world} independent GPU(s)")},
-            "gpu_launches": None, "clocks": clk.summary(),
+            "gpu_launches": launches, "clocks": clk.summary(),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "whole step",
                          "peak_kind": peak_kind, "flops_per_particle_stage": flops,
@@ -421,15 +442,16 @@ def run_reference(args):
     wl = make_workload(args, "cuda" if torch.cuda.is_available() else "cpu", 0, "fp64")
     wl.U = wl.U.cpu()
     wl.x, wl.v, wl.d, wl.elem = wl.x.cpu(), wl.v.cpu(), wl.d.cpu(), wl.elem.cpu()
-    sample = 2000
+    sample, ssteps = REF_SAMPLE
     times = []
     osmp = OracleSample(wl)
-    for i in range(args.warmup + args.steps):
-        rate, threads, dt = osmp.run(sample, 1)
-        if i >= args.warmup:
+    warm = args.warmup
+    for i in range(warm + args.steps):
+        rate, threads, dt = osmp.run(sample, ssteps)
+        if i >= warm:
             times.append(dt)
     tot = sum(times)
-    value = sample * len(times) / tot
+    value = sample * ssteps * len(times) / tot
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -438,7 +460,8 @@ def run_reference(args):
                        f"{args.particles} particles, Schiller-Naumann, dt=1e-3",
                        "inputs_vs_l2": "inputs larger than L2"},
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": threads, "kind": "oracle",
-                             "sample": f"{sample} particles x 1 time step per bench step"},
+                             "sample": f"{sample} particles x {ssteps} time steps per bench "
+                                       "step (the cpu_baseline sample of the default run)"},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -494,6 +517,7 @@ def main():
     torch.cuda.synchronize()
     ctx.profile(True)
     ctx.profile_read()  # clear
+    ctx.launch_count()  # clear
     with ClockSampler(local) as clk:
         if world > 1:
             dist.barrier()
@@ -509,7 +533,9 @@ def main():
             dist.barrier()
     ms = ev0.elapsed_time(ev1)
     kern_ms, launches = ctx.profile_read()
+    gpu_launches = ctx.launch_count()
     ctx.profile(False)
+    peaks_alu = alu_peaks(stream)
     ms = reduce_time_ms(ms, world, dev)
     value = throughput(P, args.inner, args.steps, world, ms)
     stats = ctx.push(parts, 1, wl.dt, stats=True)  # one more step with counters
@@ -523,13 +549,16 @@ def main():
     avg_launch_s = (kern_ms / 1e3) / max(launches, 1)
     flops_launch = flops_stage * 5 * args.inner * P
     achieved = flops_launch / avg_launch_s / 1e12
-    fp32_peak = fp32_peak_tflops(clk_max_mhz=2070.0)
+    fp32_peak = peaks_alu["fp32"]
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak,
                 "traffic": (TRAFFIC_BYTES_PER_PARTICLE_STEP * P * args.inner
                             if TRAFFIC_BYTES_PER_PARTICLE_STEP else None),
                 "kernel": "k_push<4,6,fp32,%s>" % ("learned" if guess else "trilinear"),
-                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "peak_kind": "measured: libpt FP32 FMA probe (pt_measure_peak), "
+                             f"{peaks_alu['sms']} SMs; from unit counts: "
+                             f"{fp32_peak_tflops(sms=peaks_alu['sms']):.1f}",
+                "fp64_peak_measured": peaks_alu["fp64"],
                 "flops_per_particle_stage": flops_stage,
                 "newton_iterations_per_stage": {"full": it32, "residual_only": it64},
                 "launch_ms": avg_launch_s * 1e3,
@@ -552,17 +581,16 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"curved channel {args.dims}^3 NGeo=3 N=5 Gauss, "
-                       f"{P} particles/GPU, Schiller-Naumann, dt=1e-3, FP32 + FP64 final Newton",
+                       f"{P} particles/GPU, Schiller-Naumann, dt=1e-3; FP32 interpolation, "
+                       "drag and RK; double-float final Newton to |dxi| < 1e-12; FP64 "
+                       "intersection where FP32 is ambiguous",
                        "inner_steps_per_call": args.inner, "guess": "mlp" if guess else "trilinear",
                        "inputs_vs_l2": inputs_vs_l2(P, wl),
                        "parallelism": f"weak, {world} independent GPU(s)"},
-            "gpu_launches": None, "clocks": clk.summary(), "roofline": roofline,
+            "gpu_launches": gpu_launches, "clocks": clk.summary(), "roofline": roofline,
             "stats_one_step": {k: stats[k] for k in ("particle_steps", "crossings", "wall_hits",
                                                      "newton_it_fp32", "newton_it_fp64",
                                                      "slow_track", "near_face")}}
-    # launches per bench step: binning (hist, scan x3, scatter) + push per chunk, memset
-    chunks = math.ceil(args.inner / args.inner)
-    line["gpu_launches"] = args.steps * chunks * 6
     if mlp_info:
         line["mlp"] = mlp_info
 
@@ -649,13 +677,23 @@ def main():
             wl.U = wl.U.cpu()
             wl.x, wl.v, wl.d, wl.elem = wl.x.cpu(), wl.v.cpu(), wl.d.cpu(), wl.elem.cpu()
             osamp = OracleSample(wl)
-            rate, threads, dt = osamp.run(100_000, 2)
+            rate, threads, dt = osamp.run(REF_SAMPLE[0], REF_SAMPLE[1])
             osamp.threads = 1
             rate1, _, _ = osamp.run(2000, 2)
             line["cpu_baseline"] = {"value": rate, "unit": METRIC, "cores": threads,
                                     "kind": "oracle", "single_thread": rate1,
-                                    "sample": "100000 particles x 2 time steps of the same "
-                                              "workload (single thread: 2000 x 2)"}
+                                    "sample": f"{REF_SAMPLE[0]} particles x {REF_SAMPLE[1]} time "
+                                              "steps of the same workload (single thread: "
+                                              "2000 x 2)"}
+            # per-result error of the FP32 arithmetic against the FP64 oracle
+            # (first-stage terms of 2000 sampled particles with a slip velocity)
+            from tests import helpers as H
+            err = H.stage_term_errors(wl, ctx, osamp.orc, 2000, seed=0)
+            line["precision_split_error"] = {
+                "xi_abs": err["xi"], "rho_rhou_rel": err["U"], "accel_rel": err["acc"],
+                "dx_rel": err["dx"], "dv_rel": err["dv"],
+                "note": "max over 2000 sampled (x, element) of the first RK stage, FP32 mode "
+                        "vs the FP64 oracle at its own xi; rel = normwise per component"}
         except Exception as e:  # pragma: no cover
             line["cpu_baseline"] = {"unavailable": str(e)[:200]}
     if rank == 0:

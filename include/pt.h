@@ -48,7 +48,11 @@ enum {
   PT_ST_CROSS_CAP = 1u << 2,   /* crossing cap reached: particle frozen    */
   PT_ST_NEAR_FACE = 1u << 3,   /* came within the near-face band           */
   PT_ST_REP800 = 1u << 4,      /* Re_p >= 800 seen (drag law out of range)  */
-  PT_ST_OPEN = 1u << 5         /* left through an open boundary: frozen    */
+  PT_ST_OPEN = 1u << 5,        /* left through an open boundary: frozen    */
+  PT_ST_NEAR_WALL = 1u << 6    /* came within the near-face band of a wall
+                                  or open face (a subset of PT_ST_NEAR_FACE):
+                                  the wall-hit count and the reflected path
+                                  may then depend on rounding               */
 };
 
 /* boundary kinds (pt_mesh_desc.bc); PT_BC_MORTAR marks the big side of a
@@ -184,7 +188,8 @@ typedef struct {
   int64_t open;
   int64_t rep800;
   int64_t dt_warn;          /* particles with dt > 2.75 tau_p                */
-  int64_t reserved[3];
+  int64_t near_wall;        /* particles with PT_ST_NEAR_WALL set at the end */
+  int64_t reserved[2];
 } pt_stats;
 
 /* Fills *cfg with the defaults listed in pt_config. */
@@ -246,26 +251,49 @@ pt_status pt_push_host(pt_ctx* ctx, const pt_particles* p_host, int32_t nsteps, 
  * of the element volume (the paper's projection operator).  Summation:
  * PT_DEPOSIT_ATOMIC adds with FP32 atomics (order-dependent rounding);
  * PT_DEPOSIT_SEGMENTED sums each element's particles in index order (bitwise
- * reproducible); it first computes every particle's source into a library-
- * owned device buffer of 32 bytes per particle (grown on demand, released by
- * pt_destroy), then reduces per element.  Other mode bits: PT_ERR_ARG. */
+ * reproducible): it sorts each element's particles by index (O(m log^2 m)
+ * for m particles in an element), computes every particle's source into a
+ * library-owned device buffer of 36 bytes per particle (grown on demand,
+ * released by pt_destroy), then reduces per element.  Other mode bits: PT_ERR_ARG. */
 pt_status pt_deposit(pt_ctx* ctx, const pt_particles* p, int32_t mode, float* S_dev);
 
 /* pt_deposit without any device allocation (the paper has no counterpart).
  * Some callers cannot call cudaMalloc: a flow solver that has handed the
  * device memory to its own pool allocator, or a time loop that must not
  * allocate once it runs (a device allocation can synchronise the device and
- * fragment such a pool).  This entry point computes exactly what pt_deposit
- * computes (same modes, same S_dev layout and ownership) but keeps its
- * scratch -- the element binning counters and the particle permutation -- in
- * one fixed array of about 5.8 MB of device memory that the library reserves
- * on every GPU that loads it, until the process exits.  Limits: at most
- * 131072 elements and 1048576 particles; larger problems return PT_ERR_ARG
- * (use pt_deposit).  The first call on a device looks up the array's device
- * address, so make that first call before any stream capture.  Every call
- * reuses the same array and clears what must start at zero; calls whose work
- * overlaps on the GPU (other streams, other contexts) race on it. */
+ * fragment such a pool).  This entry point takes the same modes, S_dev layout
+ * and ownership as pt_deposit, but keeps its scratch -- the element binning
+ * counters and two particle orders -- in one fixed array of about 9.9 MB of
+ * device memory that the library reserves on every GPU that loads it, until
+ * the process exits.  The segmented mode computes each particle's source
+ * inside the per-element reduction (one pass, no 32-byte-per-particle buffer)
+ * with the same factors and order as pt_deposit: in PT_FP32 mode the result is
+ * bitwise that of pt_deposit; in PT_FP64 mode it agrees to FP32 rounding of
+ * the weights; either way it is bitwise reproducible from call to call.  The
+ * atomic mode is pt_deposit's atomic mode.  Limits: at most 131072 elements
+ * and 1048576 particles; larger problems return PT_ERR_ARG (use pt_deposit).
+ * The array's device address differs per CUDA context; every call outside a
+ * stream capture looks it up again in the current context, and a call being
+ * captured into a graph uses the address of the last call outside capture on
+ * that device (PT_ERR_CUDA if there was none): make one call outside capture
+ * first.  Every call reuses the same array and clears what must start at
+ * zero; calls whose work overlaps on the GPU (other streams, other contexts)
+ * race on it. */
 pt_status pt_deposit_noalloc(pt_ctx* ctx, const pt_particles* p, int32_t mode, float* S_dev);
+
+/* The terms of the first RK stage of each particle, evaluated by the push's
+ * own code but without tracking, so that each result of the precision split
+ * (Sec. 3.2.1 inverse map, Eq. part_interpolation, Sec. 2.2 drag, Sec. 3.1
+ * RK update) can be compared with FP64 values: xi_dev double [3][n] the
+ * inverse map of x in elem (trilinear start, the context's precision);
+ * U_dev real [4][n] rho, rho u1, rho u2, rho u3 at xi; acc_dev real [3][n]
+ * the particle's acceleration (drag, gravity, lift as configured); dx_dev and
+ * dv_dev real [3][n] the stage increments B_1 dt v and B_1 dt a ("real" is
+ * the context's precision).  p->status receives PT_ST_NEWTON_FAIL or
+ * PT_ST_LOST where no terms could be formed (outputs then unchanged), else
+ * 0 or PT_ST_REP800; x, v, elem are not changed.  All device, caller-owned. */
+pt_status pt_stage_terms(pt_ctx* ctx, const pt_particles* p, double dt, double* xi_dev,
+                         void* U_dev, void* acc_dev, void* dx_dev, void* dv_dev);
 
 /* Point location without a known element (Sec. 3.2.3, localisation in
  * reference space): for each x the candidates are the elements listed in x's
@@ -340,6 +368,18 @@ pt_status pt_push_batch(pt_ctx* const* ctxs, const pt_particles* parts, int32_t 
  * record.  pt_profile(ctx, 0) stops recording. */
 pt_status pt_profile(pt_ctx* ctx, int32_t enable);
 pt_status pt_profile_read(pt_ctx* ctx, double* kernel_ms, int64_t* launches);
+
+/* Kernel launches this context queued (every kernel of every call) since the
+ * last pt_launch_count; *n receives the count, which is then cleared. */
+pt_status pt_launch_count(pt_ctx* ctx, int64_t* n);
+
+/* Measured arithmetic throughput of the current device (diagnostics, no
+ * counterpart in the paper): kind 0 FP32, 1 FP64 fused multiply-adds on every
+ * SM (eight independent chains per thread), best of three timed launches after
+ * a warm-up; *tflops receives TFLOP/s (2 flops per multiply-add).  Queued on
+ * stream (a cudaStream_t, NULL = default) and synchronised.  The ALU roofline
+ * of the push is reported against it. */
+pt_status pt_measure_peak(int32_t kind, void* stream, double* tflops);
 
 /* Releases the context and its device memory (not the caller's arrays). */
 pt_status pt_destroy(pt_ctx* ctx);

@@ -33,6 +33,7 @@ ST_CROSS_CAP = 1 << 2
 ST_NEAR_FACE = 1 << 3
 ST_REP800 = 1 << 4
 ST_OPEN = 1 << 5
+ST_NEAR_WALL = 1 << 6
 ST_FROZEN = ST_NEWTON_FAIL | ST_LOST | ST_CROSS_CAP | ST_OPEN
 
 
@@ -112,6 +113,9 @@ def lib():
                                                _I, ctypes.c_int]
             L.or_push.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_int64, _D, _D, _D, _I, _I,
                                   _U, ctypes.c_int, ctypes.c_double]
+            L.or_stage1.restype = ctypes.c_int
+            L.or_stage1.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_int, _D, _D,
+                                    ctypes.c_double, ctypes.c_double, _D]
             L.or_deposit.argtypes = [vp, ctypes.POINTER(Params), ctypes.c_int64, _D, _D, _D, _I,
                                      _U, _D]
             L.or_lserk_coeffs.argtypes = [_D, _D, _D]
@@ -301,6 +305,16 @@ class Oracle:
         lib().or_push(self.h, ctypes.byref(params), n, _dp(x), _dp(v), _dp(d), _ip(elem),
                       _ip(hits), _up(status), int(nsteps), float(dt))
         return dict(x=x, v=v, elem=elem, hits=hits, status=status)
+
+    def stage1(self, params: Params, e, x, v, d, dt):
+        """First RK stage without tracking: dict of xi, U (5), acc, dx, dv, or
+        None if the inverse map fails."""
+        out = np.zeros(17)
+        ok = lib().or_stage1(self.h, ctypes.byref(params), int(e), _dp(_f64(x)), _dp(_f64(v)),
+                             float(d), float(dt), _dp(out))
+        if not ok:
+            return None
+        return dict(xi=out[0:3], U=out[3:8], acc=out[8:11], dx=out[11:14], dv=out[14:17])
 
     def deposit(self, params: Params, x, v, d, elem, status=None):
         n = len(d)

@@ -671,6 +671,29 @@ static void reflect(double* a, const double* n) {
   for (int r = 0; r < 3; ++r) a[r] -= s * n[r];
 }
 
+/* 1 if local face f of element e is a wall or an open boundary: a near-face
+ * event there can change the wall-hit count or the particle's fate, while one
+ * on an internal or periodic face changes only the stage at which the owner
+ * changes (Sec. 3.2.3 follows the same straight segment either way). */
+static int is_wall_or_open(const or_ctx* c, int e, int f) {
+  int b = c->bc[e * 6 + f];
+  return b == 1 || b == 3;
+}
+
+/* Near-face band at a stage start (R8): max |xi_d| > 1 - band_ref sets the
+ * near-face bit; when the face of such a component (2d + (xi_d > 0)) is a wall
+ * or open face the near-wall bit as well. */
+static uint32_t near_bits(const or_ctx* c, const or_params* p, int e, const double xi[3]) {
+  uint32_t b = 0;
+  for (int d = 0; d < 3; ++d) {
+    if (fabs(xi[d]) > 1.0 - p->band_ref) {
+      b |= OR_ST_NEAR_FACE;
+      if (is_wall_or_open(c, e, 2 * d + (xi[d] > 0.0))) b |= OR_ST_NEAR_WALL;
+    }
+  }
+  return b;
+}
+
 /* Moves the particle along x -> xe.  The ray x(alpha) = xs + alpha*td,
  * alpha in (a0, L] (Eq. parttrajectory) is tested against every face of the
  * current element except the one it came in by; the smallest accepted alpha
@@ -701,8 +724,10 @@ static void track(const or_ctx* c, const or_params* p, int32_t* elem, double x[3
         double al = hl.h[i].alpha, s = hl.h[i].s, t = hl.h[i].t;
         double m = fabs(s) > fabs(t) ? fabs(s) : fabs(t);
         if (al < a0 - p->band_x || al > L + p->band_x) continue;
-        if (fabs(m - 1.0) < p->band_ref || fabs(al - a0) < p->band_x || fabs(L - al) < p->band_x)
+        if (fabs(m - 1.0) < p->band_ref || fabs(al - a0) < p->band_x || fabs(L - al) < p->band_x) {
           *status |= OR_ST_NEAR_FACE;
+          if (is_wall_or_open(c, e, f)) *status |= OR_ST_NEAR_WALL;
+        }
         if (m <= 1.0 && al > a0 && al <= L && al < best) {
           best = al;
           bf = f;
@@ -899,6 +924,31 @@ static void particle_accel(const or_ctx* c, const or_params* p, int e, const dou
   }
 }
 
+/* First RK stage of one particle without tracking (Sec. 3.2.1, Eq.
+ * part_interpolation, Sec. 2.2, Sec. 3.1): xi of x in e by Newton, the fluid
+ * state U(xi), the particle's acceleration, and the stage's increments of
+ * position and velocity, B_1 k_x and B_1 k_v with k_x = dt v and k_v = dt a
+ * (A_1 = 0).  out = [xi (3), U (5), a (3), dx (3), dv (3)]; returns 0 if the
+ * inverse map fails. */
+int or_stage1(const or_ctx* c, const or_params* p, int e, const double x[3], const double v[3],
+              double d, double dt, double out[17]) {
+  double A[5], B[5], C[5], xi[3], U[5], acc[3], F[3];
+  int it;
+  or_lserk_coeffs(A, B, C);
+  if (!or_newton(c, p, e, x, xi, &it)) return 0;
+  or_interp(c, e, xi, U);
+  particle_accel(c, p, e, xi, v, d, NULL, acc, F);
+  for (int r = 0; r < 3; ++r) out[r] = xi[r];
+  for (int q = 0; q < 5; ++q) out[3 + q] = U[q];
+  for (int r = 0; r < 3; ++r) {
+    double kx = dt * v[r], kv = dt * acc[r]; /* registers start at 0 in a step */
+    out[8 + r] = acc[r];
+    out[11 + r] = B[0] * kx;
+    out[14 + r] = B[0] * kv;
+  }
+  return 1;
+}
+
 void or_push(const or_ctx* c, const or_params* p, int64_t np, double* x, double* v,
              const double* d, int32_t* elem, int32_t* hits, uint32_t* status, int nsteps,
              double dt) {
@@ -922,7 +972,7 @@ void or_push(const or_ctx* c, const or_params* p, int64_t np, double* x, double*
           status[ip] |= OR_ST_LOST;
           break;
         }
-        if (m > 1.0 - p->band_ref) status[ip] |= OR_ST_NEAR_FACE;
+        status[ip] |= near_bits(c, p, e, xi);
         particle_accel(c, p, e, xi, vp, d[ip], &status[ip], acc, Ff);
         for (int r = 0; r < 3; ++r) {
           kx[r] = A[st] * kx[r] + dt * vp[r];

@@ -36,7 +36,8 @@ enum {
   OR_ST_CROSS_CAP   = 1u << 2,
   OR_ST_NEAR_FACE   = 1u << 3,
   OR_ST_REP800      = 1u << 4,
-  OR_ST_OPEN        = 1u << 5
+  OR_ST_OPEN        = 1u << 5,
+  OR_ST_NEAR_WALL   = 1u << 6  /* a near-face event on a wall or open face */
 };
 #define OR_ST_FROZEN (OR_ST_NEWTON_FAIL | OR_ST_LOST | OR_ST_CROSS_CAP | OR_ST_OPEN)
 
@@ -102,6 +103,8 @@ int     or_locate_bruteforce(const or_ctx* c, const or_params* p, const double x
 void    or_push(const or_ctx* c, const or_params* p, int64_t np, double* x, double* v,
                 const double* d, int32_t* elem, int32_t* hits, uint32_t* status,
                 int nsteps, double dt);
+int     or_stage1(const or_ctx* c, const or_params* p, int e, const double x[3],
+                  const double v[3], double d, double dt, double out[17]);
 void    or_deposit(const or_ctx* c, const or_params* p, int64_t np, const double* x,
                    const double* v, const double* d, const int32_t* elem,
                    const uint32_t* status, double* S);

@@ -50,6 +50,14 @@ int fam_g4_fp64_loc(const LocateArgs&, int, int, void*);
 int fam_g4_fp32_loc(const LocateArgs&, int, int, void*);
 int fam_g5_fp64_loc(const LocateArgs&, int, int, void*);
 int fam_g5_fp32_loc(const LocateArgs&, int, int, void*);
+int fam_g2_fp64_terms(int, const TermsArgs&, int, int, void*);
+int fam_g2_fp32_terms(int, const TermsArgs&, int, int, void*);
+int fam_g3_fp64_terms(int, const TermsArgs&, int, int, void*);
+int fam_g3_fp32_terms(int, const TermsArgs&, int, int, void*);
+int fam_g4_fp64_terms(int, const TermsArgs&, int, int, void*);
+int fam_g4_fp32_terms(int, const TermsArgs&, int, int, void*);
+int fam_g5_fp64_terms(int, const TermsArgs&, int, int, void*);
+int fam_g5_fp32_terms(int, const TermsArgs&, int, int, void*);
 int fam_g2_fp64_find(const FindArgs&, int, int, void*);
 int fam_g2_fp32_find(const FindArgs&, int, int, void*);
 int fam_g3_fp64_find(const FindArgs&, int, int, void*);
@@ -77,6 +85,9 @@ int max_active_push(int g, bool f64, int np, int block) {
 }
 int launch_find(int g, bool f64, const FindArgs& a, int grid, int block, void* s) {
   return PT_DISPATCH(g, f64, find, a, grid, block, s);
+}
+int launch_terms(int g, bool f64, int np, const TermsArgs& a, int grid, int block, void* s) {
+  return PT_DISPATCH(g, f64, terms, np, a, grid, block, s);
 }
 int launch_locate(int g, bool f64, int np, const LocateArgs& a, int grid, int block, void* s) {
   (void)np;
@@ -792,7 +803,7 @@ static int grid_for(pt_ctx* c, int64_t n, int block, int occ) {
 }
 
 __global__ void k_status_counts(const unsigned* st, int64_t n, unsigned long long* stats) {
-  unsigned long long a[6] = {0, 0, 0, 0, 0, 0};
+  unsigned long long a[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     unsigned s = st[i];
@@ -802,11 +813,13 @@ __global__ void k_status_counts(const unsigned* st, int64_t n, unsigned long lon
     a[3] += (s & PT_ST_CROSS_CAP) != 0;
     a[4] += (s & PT_ST_OPEN) != 0;
     a[5] += (s & PT_ST_REP800) != 0;
+    a[6] += (s & PT_ST_NEAR_WALL) != 0;
   }
-  for (int q = 0; q < 6; ++q) {
+  for (int q = 0; q < 7; ++q) {
     unsigned long long v = a[q];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && v) atomicAdd(stats + PT_C_NEAR + q, v);
+    if ((threadIdx.x & 31) == 0 && v)
+      atomicAdd(stats + (q < 6 ? PT_C_NEAR + q : PT_C_NEARWALL), v);
   }
 }
 
@@ -830,6 +843,10 @@ static pt_status validate_particles(pt_ctx* c, const pt_particles* p) {
   if (p->n > 0 && (!p->x || !p->v || !p->d || !p->elem || !p->hits || !p->status))
     return fail(c, PT_ERR_ARG, "a particle array is NULL");
   return PT_OK;
+}
+
+pt_status pt_validate_particles(pt_ctx* c, const pt_particles* p) {
+  return validate_particles(c, p);
 }
 
 static pt_status read_stats(pt_ctx* c, const pt_particles* p, double dt, pt_stats* out) {
@@ -861,6 +878,7 @@ static pt_status read_stats(pt_ctx* c, const pt_particles* p, double dt, pt_stat
   out->open = (int64_t)h[PT_C_OPEN];
   out->rep800 = (int64_t)h[PT_C_REP];
   out->dt_warn = (int64_t)h[PT_C_DTWARN];
+  out->near_wall = (int64_t)h[PT_C_NEARWALL];
   if (out->newton_fail) return fail(c, PT_ERR_NEWTON, "%lld particles failed the inverse map",
                                     (long long)out->newton_fail);
   if (out->lost) return fail(c, PT_ERR_LOST, "%lld particles lost", (long long)out->lost);
@@ -907,6 +925,7 @@ pt_status pt_push_impl(pt_ctx* c, const pt_particles* p, int32_t nsteps, double 
       int rc = bin_by_element(p->elem, n, c->nelem, c->d_scratch, c->d_perm, nullptr, c->nsm,
                               c->stream);
       if (rc) return fail(c, PT_ERR_CUDA, "binning: %s", cudaGetErrorString((cudaError_t)rc));
+      c->launches += 5;  // histogram, three scan kernels, scatter
       a.perm = c->d_perm;
       a.nsteps = std::min(chunk, nsteps - s0);
       cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -916,6 +935,7 @@ pt_status pt_push_impl(pt_ctx* c, const pt_particles* p, int32_t nsteps, double 
         if (e0) cudaEventRecord(e0, c->stream);
       }
       rc = launch_push(c->g, f64, np, a, grid, block, c->stream);
+      c->launches += 1;
       if (e1) cudaEventRecord(e1, c->stream);
       if (rc) return fail(c, PT_ERR_CUDA, "push launch: %s", cudaGetErrorString((cudaError_t)rc));
     }
@@ -950,7 +970,6 @@ pt_status pt_push_host(pt_ctx* c, const pt_particles* h, int32_t nsteps, double 
   const size_t bytes = n * (24 + 3 * rs + rs + 12);
   if (c->stage_bytes < bytes) {
     if (c->d_stage) cudaFree(c->d_stage);
-  if (c->d_src) cudaFree(c->d_src);
     c->d_stage = nullptr;
     CK(cudaMalloc(&c->d_stage, std::max<size_t>(bytes, 64) + 256));
     c->stage_bytes = bytes;
@@ -1014,6 +1033,33 @@ pt_status pt_locate(pt_ctx* c, int64_t n, const double* x, const int32_t* elem, 
   return PT_OK;
 }
 
+pt_status pt_stage_terms(pt_ctx* c, const pt_particles* p, double dt, double* xi, void* U,
+                         void* acc, void* dx, void* dv) {
+  if (!c) return fail(nullptr, PT_ERR_ARG, "ctx is NULL");
+  if (c->N < 0 || !c->U) return fail(c, PT_ERR_STATE, "pt_set_fluid was not called");
+  pt_status s = validate_particles(c, p);
+  if (s) return s;
+  const int64_t n = p->n;
+  if (n > 0 && (!xi || !U || !acc || !dx || !dv)) return fail(c, PT_ERR_ARG, "NULL output");
+  if (n == 0) return PT_OK;
+  TermsArgs a;
+  a.m = dev_mesh(c);
+  fill_consts(c, a.k);
+  a.p = {n, p->x, p->v, p->d, p->elem, p->hits, p->status};
+  a.U = c->U;
+  a.dt = dt;
+  a.xi = xi;
+  a.Uo = U;
+  a.acc = acc;
+  a.dx = dx;
+  a.dv = dv;
+  const int grid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)c->nsm * 16);
+  const int rc = launch_terms(c->g, c->cfg.precision == PT_FP64, c->N + 1, a, grid, 128,
+                              c->stream);
+  if (rc) return fail(c, PT_ERR_CUDA, "terms launch: %s", cudaGetErrorString((cudaError_t)rc));
+  return PT_OK;
+}
+
 pt_status pt_deposit(pt_ctx* c, const pt_particles* p, int32_t mode, float* S) {
   if (!c) return fail(nullptr, PT_ERR_ARG, "ctx is NULL");
   if (c->N < 0 || !c->U) return fail(c, PT_ERR_STATE, "pt_set_fluid was not called");
@@ -1043,15 +1089,22 @@ pt_status pt_deposit(pt_ctx* c, const pt_particles* p, int32_t mode, float* S) {
   a.src = nullptr;
   const bool f64 = c->cfg.precision == PT_FP64;
   if (mode & PT_DEPOSIT_SEGMENTED) {
-    // two passes: the sources of all particles, then the per-element sums
+    // two passes: the sources of all particles, then the per-element sums,
+    // each element's particles in index order
     if (c->src_cap < n) {
       if (c->d_src) cudaFree(c->d_src);
+      if (c->d_perm2) cudaFree(c->d_perm2);
       c->d_src = nullptr;
+      c->d_perm2 = nullptr;
       c->src_cap = 0;
       CK(cudaMalloc(&c->d_src, sizeof(float4) * 2 * std::max<int64_t>(n, 1)));
+      CK(cudaMalloc(&c->d_perm2, sizeof(int) * std::max<int64_t>(n, 1)));
       c->src_cap = n;
     }
     a.src = c->d_src;
+    rc = sort_segments(c->d_perm, offs, c->nelem, c->d_perm2, c->nsm, c->stream);
+    if (rc) return fail(c, PT_ERR_CUDA, "segment sort: %s", cudaGetErrorString((cudaError_t)rc));
+    a.perm = c->d_perm2;
   }
   if (!(mode & PT_DEPOSIT_SEGMENTED)) {
     CK(cudaMemsetAsync(S, 0, sizeof(float) * 4 * n3 * c->nelem, c->stream));
@@ -1224,6 +1277,13 @@ pt_status pt_profile_read(pt_ctx* c, double* ms, int64_t* launches) {
   return PT_OK;
 }
 
+pt_status pt_launch_count(pt_ctx* c, int64_t* n) {
+  if (!c || !n) return fail(c, PT_ERR_ARG, "NULL argument");
+  *n = c->launches;
+  c->launches = 0;
+  return PT_OK;
+}
+
 pt_status pt_destroy(pt_ctx* c) {
   if (!c) return PT_OK;
   for (cudaEvent_t e : c->ev_used) cudaEventDestroy(e);
@@ -1233,6 +1293,7 @@ pt_status pt_destroy(pt_ctx* c) {
   if (c->d_perm) cudaFree(c->d_perm);
   if (c->d_stage) cudaFree(c->d_stage);
   if (c->d_src) cudaFree(c->d_src);
+  if (c->d_perm2) cudaFree(c->d_perm2);
   pt_mlp_release(c);
   pt_batch_release(c);
   delete c;

@@ -125,6 +125,7 @@ __global__ void k_status_counts_batch(const BatchArgs a) {
     if (s & PT_ST_CROSS_CAP) atomicAdd(st + PT_C_CCAP, 1ull);
     if (s & PT_ST_OPEN) atomicAdd(st + PT_C_OPEN, 1ull);
     if (s & PT_ST_REP800) atomicAdd(st + PT_C_REP, 1ull);
+    if (s & PT_ST_NEAR_WALL) atomicAdd(st + PT_C_NEARWALL, 1ull);
   }
 }
 
@@ -310,6 +311,7 @@ extern "C" pt_status pt_push_batch(pt_ctx* const* ctxs, const pt_particles* part
         cudaEventCreate(&e1);
         cudaEventRecord(e0, s);
         enqueue_chunk(P, a, block, s);
+        c0->launches += 6;  // histogram, three scan kernels, scatter, push
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -355,6 +357,7 @@ extern "C" pt_status pt_push_batch(pt_ctx* const* ctxs, const pt_particles* part
         P->graph_block = P->block;
       }
       cudaError_t e = cudaGraphLaunch(P->graph, s);
+      c0->launches += 6 * (int64_t)((nsteps + kChunk - 1) / kChunk);
       if (e != cudaSuccess) {
         c0->err = std::string("pt_push_batch: graph launch: ") + cudaGetErrorString(e);
         return PT_ERR_CUDA;
@@ -397,6 +400,7 @@ extern "C" pt_status pt_push_batch(pt_ctx* const* ctxs, const pt_particles* part
     o.cross_cap = (int64_t)q[PT_C_CCAP];
     o.open = (int64_t)q[PT_C_OPEN];
     o.rep800 = (int64_t)q[PT_C_REP];
+    o.near_wall = (int64_t)q[PT_C_NEARWALL];
     if (ret == PT_OK) {
       if (o.newton_fail) ret = PT_ERR_NEWTON;
       else if (o.lost) ret = PT_ERR_LOST;

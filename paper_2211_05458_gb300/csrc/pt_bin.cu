@@ -106,6 +106,65 @@ __global__ void k_scatter(const int* __restrict__ elem, int64_t n, int nelem, in
   }
 }
 
+// Sorts a[0..m) ascending in place by a bitonic network in its "flip" form:
+// for each block size k, element i is compared with i ^ (k - 1) and then with
+// i ^ j for j = k/4 .. 1, the smaller value always going to the lower index.
+// Missing elements beyond m act as +infinity, so pairs reaching past m are
+// skipped and m need not be a power of two.  Called by a whole block.
+__device__ void block_bitonic(int* a, unsigned m) {
+  unsigned M = 1;
+  while (M < m) M <<= 1;
+  for (unsigned k = 2; k <= M && k != 0; k <<= 1) {
+    for (unsigned j = k >> 1; j > 0; j >>= 1) {
+      const unsigned mask = (j == (k >> 1)) ? k - 1 : j;
+      for (unsigned i = threadIdx.x; i < M; i += blockDim.x) {
+        const unsigned l = i ^ mask;
+        if (l > i && l < m) {
+          const int x = a[i], y = a[l];
+          if (x > y) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+constexpr int kSortSmem = 4096;  // segments up to this size are sorted in shared memory
+
+__global__ void __launch_bounds__(256) k_sort_segments(const int* __restrict__ perm,
+                                                       const int* __restrict__ offs, int nbins,
+                                                       int* out) {
+  __shared__ int sh[kSortSmem];
+  for (int e = blockIdx.x; e < nbins; e += gridDim.x) {
+    const int beg = offs[e], m = offs[e + 1] - beg;
+    if (m <= 0) continue;
+    if (m <= kSortSmem) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) sh[i] = perm[beg + i];
+      __syncthreads();
+      block_bitonic(sh, (unsigned)m);
+      for (int i = threadIdx.x; i < m; i += blockDim.x) out[beg + i] = sh[i];
+    } else {
+      // large segment: the same network on the output in global memory (the
+      // block's writes are visible to its threads after __syncthreads)
+      for (int i = threadIdx.x; i < m; i += blockDim.x) out[beg + i] = perm[beg + i];
+      __syncthreads();
+      block_bitonic(out + beg, (unsigned)m);
+    }
+    __syncthreads();
+  }
+}
+
+int sort_segments(const int* perm, const int* offs, int nelem, int* out, int nsm,
+                  cudaStream_t s) {
+  const int nbins = nelem + 1;
+  const int g = nbins < nsm * 8 ? nbins : nsm * 8;
+  k_sort_segments<<<g > 0 ? g : 1, 256, 0, s>>>(perm, offs, nbins, out);
+  return (int)cudaGetLastError();
+}
+
 size_t bin_scratch_ints(int nelem) {
   const int nbins = nelem + 1;
   const int nb = (nbins + 1023) / 1024;

@@ -20,4 +20,9 @@ size_t bin_scratch_ints(int nelem);
 // particles are perm[offs[e] .. offs[e+1]); bin nelem holds invalid owners.
 int bin_by_element(const int* elem, int64_t n, int nelem, int* scratch, int* perm, int** offs_out,
                    int nsm, cudaStream_t s);
+// out[offs[e] .. offs[e+1]) = perm[offs[e] .. offs[e+1]) in increasing order,
+// for every element e < nelem (and the trailing bin): the element-sorted order
+// with each element's particles in index order.  O(m log^2 m) work per
+// segment of m particles (one block per segment); perm and out must differ.
+int sort_segments(const int* perm, const int* offs, int nelem, int* out, int nsm, cudaStream_t s);
 }  // namespace pt

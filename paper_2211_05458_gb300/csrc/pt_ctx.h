@@ -46,9 +46,11 @@ struct pt_ctx {
   int64_t perm_cap = 0;
   void* d_stage = nullptr;
   size_t stage_bytes = 0;
-  // per-particle sources of the two-pass segmented deposition
+  // per-particle sources of the two-pass segmented deposition, and the
+  // element-sorted order with each element's particles in index order
   float4* d_src = nullptr;
   int64_t src_cap = 0;
+  int* d_perm2 = nullptr;
   // learned guess
   pt_mlp_state* mlp = nullptr;
   bool mlp_ready = false;
@@ -61,6 +63,8 @@ struct pt_ctx {
   int grid_dims[3] = {0, 0, 0};
   // batched push plan (pt_push_batch called with this context first)
   pt_batch_plan* batch = nullptr;
+  // kernels queued since the last pt_launch_count
+  int64_t launches = 0;
   // kernel timing (pt_profile)
   bool profile = false;
   std::vector<cudaEvent_t> ev_free, ev_used;

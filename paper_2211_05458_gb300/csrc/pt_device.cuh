@@ -1587,8 +1587,12 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
           double mm = fmax(fabs(s), fabs(t));
           if (mm > 1.0 + k.band_ref) continue;
           if (al < a0 - k.band_x || al > L + k.band_x) continue;
-          if (fabs(mm - 1.0) < k.band_ref || fabs(al - a0) < k.band_x || fabs(L - al) < k.band_x)
-            st |= PT_ST_NEAR_FACE;
+          if (fabs(mm - 1.0) < k.band_ref || fabs(al - a0) < k.band_x ||
+              fabs(L - al) < k.band_x) {
+            const int bcf = finfo_bc(info);
+            st |= PT_ST_NEAR_FACE |
+                  ((bcf == PT_BC_WALL || bcf == PT_BC_OPEN) ? (unsigned)PT_ST_NEAR_WALL : 0u);
+          }
           if (mm <= 1.0 && al > a0 && al <= L && al < best) {
             best = al;
             bf = f;

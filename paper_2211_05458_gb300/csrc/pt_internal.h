@@ -23,7 +23,7 @@ __host__ __device__ __forceinline__ int finfo_nf(int info) { return (info >> 5) 
 // stats counter slots (device uint64 array)
 enum {
   PT_C_STEPS = 0, PT_C_CROSS, PT_C_HITS, PT_C_IT32, PT_C_IT64, PT_C_SLOW,
-  PT_C_NEAR, PT_C_NFAIL, PT_C_LOST, PT_C_CCAP, PT_C_OPEN, PT_C_REP, PT_C_DTWARN,
+  PT_C_NEAR, PT_C_NFAIL, PT_C_LOST, PT_C_CCAP, PT_C_OPEN, PT_C_REP, PT_C_DTWARN, PT_C_NEARWALL,
   PT_C_COUNT = 16
 };
 
@@ -142,6 +142,21 @@ struct DepositArgs {
   float4* src;            // [2 n] per-particle sources of the two-pass segmented mode
 };
 
+// first-stage terms of each particle (pt_stage_terms): p.status receives the
+// status bits, the other outputs are [q][n] arrays in the mode's precision
+struct TermsArgs {
+  DevMesh m;
+  DevConsts k;
+  DevParticles p;
+  const void* U;
+  double dt;
+  double* xi;             // [3][n]
+  void* Uo;               // [4][n] rho, rho u1, rho u2, rho u3 at xi
+  void* acc;              // [3][n]
+  void* dx;               // [3][n] B_1 dt v
+  void* dv;               // [3][n] B_1 dt a
+};
+
 // kernel entry points, one family per (g, mode) translation unit
 namespace pt {
 int launch_push(int g, bool fp64, int np, const PushArgs& a, int grid, int block, void* stream);
@@ -151,4 +166,5 @@ int launch_locate(int g, bool fp64, int np, const LocateArgs& a, int grid, int b
 int launch_deposit(int g, bool fp64, int np, int mode, const DepositArgs& a, int grid, int block,
                    void* stream);
 int max_active_push(int g, bool fp64, int np, int block);
+int launch_terms(int g, bool fp64, int np, const TermsArgs& a, int grid, int block, void* stream);
 }  // namespace pt

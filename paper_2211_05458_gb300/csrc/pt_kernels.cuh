@@ -199,6 +199,87 @@ __device__ __noinline__ void saffman_force(const DevMesh& m, const DevConsts& k,
   F[2] = kf * (rel[0] * w[1] - rel[1] * w[0]);
 }
 
+// Near-face band at a stage start (R8): max |xi_d| > 1 - band_ref sets
+// PT_ST_NEAR_FACE; where the face of such a component (2d + (xi_d > 0)) is a
+// wall or open face, PT_ST_NEAR_WALL as well.
+template <typename T>
+__device__ __forceinline__ unsigned near_bits(const DevMesh& m, int e, const T* xi, double band) {
+  unsigned b = 0u;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (fabs((double)xi[d]) > 1.0 - band) {
+      b |= PT_ST_NEAR_FACE;
+      const int bc = finfo_bc(__ldg(m.finfo + 6 * (size_t)e + 2 * d + (xi[d] > T(0) ? 1 : 0)));
+      if (bc == PT_BC_WALL || bc == PT_BC_OPEN) b |= PT_ST_NEAR_WALL;
+    }
+  }
+  return b;
+}
+
+// Acceleration of a particle (Sec. 2.2, Eqs. dragforce, dragfactor, Eq.
+// theory:maxey): a = m_d f_D (u - v) / tau_p + g (1 - rho / rho_p with
+// buoyancy) + F_S / m_p with the lift; m_d the per-axis drag mask.  Uv holds
+// rho, rho u at xi (interpolated by the caller).  Sets PT_ST_REP800 for the
+// Schiller-Naumann law beyond its range.
+template <int G, int NP, typename R>
+__device__ __forceinline__ void particle_accel(const DevMesh& m, const DevConsts& k,
+                                               const R* __restrict__ Ue, int e, const double* xi,
+                                               const R* Uv, const R* v, R d, R tau, unsigned& st,
+                                               R* acc) {
+  const R mu = (R)k.mu;
+  R irho = R(1) / Uv[0], rel[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) rel[r] = Uv[1 + r] * irho - v[r];
+  R fD = R(1);
+  if (k.drag_law) {
+    R re = Uv[0] * sqrt(rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2]) * d / mu;
+    if (k.drag_law == 1 && re >= R(800)) st |= PT_ST_REP800;
+    fD = drag_factor<R>(k, re);
+  }
+  const R coef = fD / tau;
+  R al[3] = {R(0), R(0), R(0)};
+  if (k.lift) {
+    saffman_force<G, NP, R>(m, k, Ue, e, xi, v, d, al);
+    const R imp = R(6) / (R(3.14159265358979323846) * (R)k.rho_p * d * d * d);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) al[r] *= imp;
+  }
+  const R gf = k.buoyancy ? R(1) - Uv[0] / (R)k.rho_p : R(1);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) acc[r] = (R)k.mask[r] * coef * rel[r] + (R)k.g[r] * gf + al[r];
+}
+
+// FP32 mode: as particle_accel, xi as a double-float (used by the lift only)
+template <int G, int NP>
+__device__ __forceinline__ void particle_accel_f32(const DevMesh& m, const DevConsts& k,
+                                                   const float* __restrict__ Ue, int e,
+                                                   const df* zd, const float* Uv, const float* v,
+                                                   float d, float tau, unsigned& st, float* acc) {
+  const float mu = (float)k.mu;
+  float irho = 1.f / Uv[0], rel[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) rel[r] = Uv[1 + r] * irho - v[r];
+  float fD = 1.f;
+  if (k.drag_law) {
+    float re = Uv[0] * sqrtf(rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2]) * d / mu;
+    if (k.drag_law == 1 && re >= 800.f) st |= PT_ST_REP800;
+    fD = drag_factor<float>(k, re);
+  }
+  const float coef = fD / tau;
+  float al[3] = {0.f, 0.f, 0.f};
+  if (k.lift) {
+    const double xid[3] = {df_to_double(zd[0]), df_to_double(zd[1]), df_to_double(zd[2])};
+    saffman_force<G, NP, float>(m, k, Ue, e, xid, v, d, al);
+    const float imp = 6.f / (3.14159265358979323846f * (float)k.rho_p * d * d * d);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) al[r] *= imp;
+  }
+  const float gf = k.buoyancy ? 1.f - Uv[0] / (float)k.rho_p : 1.f;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    acc[r] = (float)k.mask[r] * coef * rel[r] + (float)k.g[r] * gf + al[r];
+}
+
 struct PushCounters {
   unsigned long long steps, it32, it64;
   TrackCounters tc;
@@ -407,7 +488,7 @@ __device__ __forceinline__ void push_particle(const DevMesh& m, const DevConsts&
         }
       }
       pending = false;
-      if (mx > 1.0 - k.band_ref) st |= PT_ST_NEAR_FACE;
+      if (mx > 1.0 - k.band_ref) st |= near_bits(m, e, xi, k.band_ref);
       // interpolation of rho, rho u at xi
       R l1[NP], l2[NP], l3[NP], Uv[4];
       lagr<NP, R>((R)xi[0], Nodes<R>::sol(k), Nodes<R>::solw(k), l1);
@@ -415,31 +496,14 @@ __device__ __forceinline__ void push_particle(const DevMesh& m, const DevConsts&
       lagr<NP, R>((R)xi[2], Nodes<R>::sol(k), Nodes<R>::solw(k), l3);
       interp4<NP, R>(U + (size_t)e * 5 * N3, l1, l2, l3, Uv);
       // drag + gravity
-      R irho = R(1) / Uv[0], rel[3];
-#pragma unroll
-      for (int r = 0; r < 3; ++r) rel[r] = Uv[1 + r] * irho - v[r];
-      R fD = R(1);
-      if (k.drag_law) {
-        R re = Uv[0] * sqrt(rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2]) * d / mu;
-        if (k.drag_law == 1 && re >= R(800)) st |= PT_ST_REP800;
-        fD = drag_factor<R>(k, re);
-      }
-      const R coef = fD / tau;
-      R al[3] = {R(0), R(0), R(0)};
-      if (k.lift) {
-        saffman_force<G, NP, R>(m, k, U + (size_t)e * 5 * N3, e, xi, v, d, al);
-        const R imp = R(6) / (R(3.14159265358979323846) * (R)k.rho_p * d * d * d);
-#pragma unroll
-        for (int r = 0; r < 3; ++r) al[r] *= imp;
-      }
+      R acc[3];
+      particle_accel<G, NP, R>(m, k, U + (size_t)e * 5 * N3, e, xi, Uv, v, d, tau, st, acc);
       double xe[3];
       float bf[3];
-      const R gf = k.buoyancy ? R(1) - Uv[0] / (R)k.rho_p : R(1);
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        R acc = (R)k.mask[r] * coef * rel[r] + (R)k.g[r] * gf + al[r];
         kx[r] = As * kx[r] + dt * v[r];
-        kv[r] = As * kv[r] + dt * acc;
+        kv[r] = As * kv[r] + dt * acc[r];
         const R dx = Bs * kx[r];
         xe[r] = x[r] + (double)dx;
         bf[r] = F64 ? (float)(xl[r] + (double)dx) : xf[r] + (float)dx;
@@ -549,7 +613,7 @@ __device__ __forceinline__ void push_particle_f32(const DevMesh& m, const DevCon
       }
       float xi[3] = {zd[0].hi + zd[0].lo, zd[1].hi + zd[1].lo, zd[2].hi + zd[2].lo};
       const float mx = tmax3(xi[0], xi[1], xi[2]);
-      if (mx > 1.f - 1e-5f) {  // decide the bands exactly (rare)
+      if (mx > 1.f - fmaxf(1e-5f, (float)k.band_ref)) {  // decide the bands exactly (rare)
         double md = fmax(fmax(fabs(df_to_double(zd[0])), fabs(df_to_double(zd[1]))),
                          fabs(df_to_double(zd[2])));
         if (md > 1.0 + k.lost_tol && !pending) {  // outside without having moved: lost
@@ -576,7 +640,10 @@ __device__ __forceinline__ void push_particle_f32(const DevMesh& m, const DevCon
           md = fmax(fmax(fabs(df_to_double(zd[0])), fabs(df_to_double(zd[1]))),
                     fabs(df_to_double(zd[2])));
         }
-        if (md > 1.0 - k.band_ref) st |= PT_ST_NEAR_FACE;
+        if (md > 1.0 - k.band_ref) {
+          const double z[3] = {df_to_double(zd[0]), df_to_double(zd[1]), df_to_double(zd[2])};
+          st |= near_bits(m, e, z, k.band_ref);
+        }
       }
       pending = false;
       // interpolation of rho, rho u at xi
@@ -586,32 +653,14 @@ __device__ __forceinline__ void push_particle_f32(const DevMesh& m, const DevCon
       lagr<NP, float>(xi[2], k.sn32, k.sw32, l3);
       interp4<NP, float>(U + (size_t)e * 5 * N3, l1, l2, l3, Uv);
       // drag + gravity
-      float irho = 1.f / Uv[0], rel[3];
-#pragma unroll
-      for (int r = 0; r < 3; ++r) rel[r] = Uv[1 + r] * irho - v[r];
-      float fD = 1.f;
-      if (k.drag_law) {
-        float re = Uv[0] * sqrtf(rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2]) * d / mu;
-        if (k.drag_law == 1 && re >= 800.f) st |= PT_ST_REP800;
-        fD = drag_factor<float>(k, re);
-      }
-      const float coef = fD / tau;
-      float al[3] = {0.f, 0.f, 0.f};
-      if (k.lift) {
-        const double xid[3] = {df_to_double(zd[0]), df_to_double(zd[1]), df_to_double(zd[2])};
-        saffman_force<G, NP, float>(m, k, U + (size_t)e * 5 * N3, e, xid, v, d, al);
-        const float imp = 6.f / (3.14159265358979323846f * (float)k.rho_p * d * d * d);
-#pragma unroll
-        for (int r = 0; r < 3; ++r) al[r] *= imp;
-      }
+      float acc[3];
+      particle_accel_f32<G, NP>(m, k, U + (size_t)e * 5 * N3, e, zd, Uv, v, d, tau, st, acc);
       df xe[3];
       float bf[3];
-      const float gf = k.buoyancy ? 1.f - Uv[0] / (float)k.rho_p : 1.f;
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        float acc = (float)k.mask[r] * coef * rel[r] + (float)k.g[r] * gf + al[r];
         kx[r] = As * kx[r] + dt * v[r];
-        kv[r] = As * kv[r] + dt * acc;
+        kv[r] = As * kv[r] + dt * acc[r];
         xe[r] = df_add(xd[r], df_from(Bs * kx[r]));
         bf[r] = xe[r].hi;
         v[r] = v[r] + Bs * kv[r];
@@ -942,52 +991,43 @@ __global__ void __launch_bounds__(256) k_deposit_atomic(const DepositArgs a) {
   }
 }
 
-// Deterministic segmented reduction: one block per element; the element's
-// particles (a segment of the element-sorted order) are put in index order,
-// their sources staged in shared memory, and every output node sums them in
-// that fixed order -- S_e[q][ijk] = sum_p f_q(p) l_i(p) l_j(p) l_k(p).
-constexpr int SEG_TILE = 128;
+// Deterministic segmented reduction in one pass: one block per element; the
+// element's particles (a segment of the element-sorted order, each segment in
+// particle-index order) are taken CH at a time, their sources computed by one
+// thread each and staged as the two factors of
+//   S_e[q][i,j,k] = sum_p (f_q l3_k)(p) (l1_i l2_j)(p),
+// and every output node sums them in that fixed order -- bitwise reproducible,
+// and in FP32 mode bitwise equal to the two-pass form below (same factors,
+// same order).
 template <int G, int NP, bool F64, bool NEAR>
 __global__ void __launch_bounds__(256) k_deposit_segmented(const DepositArgs a) {
   constexpr int N3 = NP * NP * NP;
-  __shared__ int idx[SEG_TILE];
-  __shared__ float sf[SEG_TILE][4];
-  __shared__ float sl[SEG_TILE][3][NP];
-  __shared__ int sok[SEG_TILE];
+  constexpr int CH = 64;
+  constexpr int NO = (4 * N3 + 255) / 256;
+  __shared__ float sA[CH][4 * NP];
+  __shared__ float sB[CH][NP * NP];
   for (int e = blockIdx.x; e < a.m.nelem; e += gridDim.x) {
     const int beg = a.offs[e], end = a.offs[e + 1];
-    // outputs owned by this thread: o = threadIdx.x + 256 * r, r < ceil(4 N3 / 256)
-    constexpr int NO = (4 * N3 + 255) / 256;
+    const int total = end - beg;
     float acc[NO];
 #pragma unroll
     for (int r = 0; r < NO; ++r) acc[r] = 0.f;
-    const int total = end - beg;
-    for (int base = 0; base < total; base += SEG_TILE) {
-      const int cnt = min(SEG_TILE, total - base);
-      __syncthreads();
-      // the segment's particles in index order, SEG_TILE at a time (the order
-      // left by the atomic scatter is arbitrary; index order makes the sum
-      // reproducible): the particle of rank r goes to idx[r - base]
-      for (int j = threadIdx.x; j < total; j += blockDim.x) {
-        const int my = a.perm[beg + j];
-        int rank = 0;
-        for (int q = 0; q < total; ++q) rank += a.perm[beg + q] < my;
-        if (rank >= base && rank < base + SEG_TILE) idx[rank - base] = my;
-      }
+    for (int base = 0; base < total; base += CH) {
+      const int cnt = min(CH, total - base);
       __syncthreads();
       if (threadIdx.x < cnt) {
         int ee, node;
         float f[4], l1[NP], l2[NP], l3[NP];
-        bool ok = particle_source<G, NP, F64, NEAR>(a, idx[threadIdx.x], ee, f, l1, l2, l3, &node);
-        sok[threadIdx.x] = ok;
+        const bool ok = particle_source<G, NP, F64, NEAR>(a, a.perm[beg + base + threadIdx.x],
+                                                          ee, f, l1, l2, l3, &node);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) sf[threadIdx.x][q] = ok ? f[q] : 0.f;
+        for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int i = 0; i < NP; ++i) {
-          sl[threadIdx.x][0][i] = l1[i];
-          sl[threadIdx.x][1][i] = l2[i];
-          sl[threadIdx.x][2][i] = l3[i];
-        }
+          for (int k = 0; k < NP; ++k) sA[threadIdx.x][q * NP + k] = ok ? f[q] * l3[k] : 0.f;
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+#pragma unroll
+          for (int i = 0; i < NP; ++i) sB[threadIdx.x][i + NP * j] = ok ? l1[i] * l2[j] : 0.f;
       }
       __syncthreads();
 #pragma unroll
@@ -995,10 +1035,9 @@ __global__ void __launch_bounds__(256) k_deposit_segmented(const DepositArgs a) 
         const int o = threadIdx.x + 256 * r;
         if (o < 4 * N3) {
           const int q = o / N3, node = o - q * N3;
-          const int i = node % NP, j = (node / NP) % NP, kk = node / (NP * NP);
+          const int row = q * NP + node / (NP * NP), col = node % (NP * NP);
           float s = acc[r];
-          for (int p = 0; p < cnt; ++p)
-            if (sok[p]) s = fmaf(sf[p][q] * sl[p][0][i], sl[p][1][j] * sl[p][2][kk], s);
+          for (int p = 0; p < cnt; ++p) s = fmaf(sA[p][row], sB[p][col], s);
           acc[r] = s;
         }
       }
@@ -1038,7 +1077,8 @@ __global__ void __launch_bounds__(128) k_deposit_src(const DepositArgs a) {
 }
 
 // Pass 2: one block per element.  The element's particles are taken in index
-// order (so the sums are bitwise reproducible), CH at a time; each particle's
+// order (the segments of the sorted order are in index order, so the sums are
+// bitwise reproducible), CH at a time; each particle's
 // weights are staged as the two factors of S[q][i,j,k] = sum_p (f_q l_k)(l_i l_j):
 // A[p][q NP + k] = f_q l3_k and B[p][i + NP j] = l1_i l2_j, so every output
 // needs two shared loads and one FMA per particle.  Nearest-node projection:
@@ -1048,7 +1088,6 @@ __global__ void __launch_bounds__(256) k_deposit_seg2(const DepositArgs a) {
   constexpr int N3 = NP * NP * NP;
   constexpr int CH = 64;
   constexpr int NO = (4 * N3 + 255) / 256;
-  __shared__ int idx[CH];
   __shared__ float sA[CH][4 * NP];
   __shared__ float sB[CH][NP * NP];
   __shared__ int snode[CH];
@@ -1061,15 +1100,8 @@ __global__ void __launch_bounds__(256) k_deposit_seg2(const DepositArgs a) {
     for (int base = 0; base < total; base += CH) {
       const int cnt = min(CH, total - base);
       __syncthreads();
-      for (int j = threadIdx.x; j < total; j += blockDim.x) {
-        const int my = a.perm[beg + j];
-        int rank = 0;
-        for (int q = 0; q < total; ++q) rank += a.perm[beg + q] < my;
-        if (rank >= base && rank < base + CH) idx[rank - base] = beg + j;
-      }
-      __syncthreads();
       if (threadIdx.x < cnt) {
-        const int t = idx[threadIdx.x];
+        const int t = beg + base + threadIdx.x;
         const float4 w0 = a.src[2 * (int64_t)t], w1 = a.src[2 * (int64_t)t + 1];
         const float f[4] = {w0.x, w0.y, w0.z, w0.w};
         if (NEAR) {
@@ -1116,6 +1148,97 @@ __global__ void __launch_bounds__(256) k_deposit_seg2(const DepositArgs a) {
       const int o = threadIdx.x + 256 * r;
       if (o < 4 * N3) Se[o] = acc[r];
     }
+  }
+}
+
+// First RK stage of each particle without tracking, by the push's own code:
+// inverse map (trilinear start, the mode's Newton), interpolation of rho and
+// rho u, the acceleration, and the stage increments B_1 k_x, B_1 k_v with
+// k_x = dt v, k_v = dt a (the registers start at zero in a step).  Reports each
+// result of the precision split separately, for comparison with FP64 values.
+template <int G, int NP, bool F64>
+__global__ void __launch_bounds__(128) k_terms(const __grid_constant__ TermsArgs a) {
+  using R = typename RealOf<F64>::type;
+  constexpr int N3 = NP * NP * NP;
+  const int64_t n = a.p.n;
+  const R* vg = reinterpret_cast<const R*>(a.p.v);
+  const R* dg = reinterpret_cast<const R*>(a.p.d);
+  const R* U = reinterpret_cast<const R*>(a.U);
+  R* Uo = reinterpret_cast<R*>(a.Uo);
+  R* ao = reinterpret_cast<R*>(a.acc);
+  R* xo = reinterpret_cast<R*>(a.dx);
+  R* vo = reinterpret_cast<R*>(a.dv);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int e = a.p.elem[i];
+    unsigned st = 0u;
+    if (e < 0 || e >= a.m.nelem) {
+      a.p.status[i] = PT_ST_LOST;
+      continue;
+    }
+    const R v[3] = {vg[i], vg[n + i], vg[2 * n + i]};
+    const R d = dg[i];
+    const double* ce = a.m.ce + 3 * (size_t)e;
+    const double xl[3] = {a.p.x[i] - __ldg(ce), a.p.x[n + i] - __ldg(ce + 1),
+                          a.p.x[2 * n + i] - __ldg(ce + 2)};
+    double xi[3];
+    R Uv[4], acc[3];
+    int i32 = 0, i64 = 0;
+    const R tau = (R)a.k.rho_p * d * d / (R(18) * (R)a.k.mu);
+    if constexpr (F64) {
+      const float xf[3] = {(float)xl[0], (float)xl[1], (float)xl[2]};
+      float guess[3];
+      trilinear_guess(a.m, e, xf, guess);
+      if (!locate_local<G, true>(a.m, a.k, e, xl, guess, xi, i32, i64)) {
+        a.p.status[i] = PT_ST_NEWTON_FAIL;
+        continue;
+      }
+      R l1[NP], l2[NP], l3[NP];
+      lagr<NP, R>((R)xi[0], Nodes<R>::sol(a.k), Nodes<R>::solw(a.k), l1);
+      lagr<NP, R>((R)xi[1], Nodes<R>::sol(a.k), Nodes<R>::solw(a.k), l2);
+      lagr<NP, R>((R)xi[2], Nodes<R>::sol(a.k), Nodes<R>::solw(a.k), l3);
+      interp4<NP, R>(U + (size_t)e * 5 * N3, l1, l2, l3, Uv);
+      particle_accel<G, NP, R>(a.m, a.k, U + (size_t)e * 5 * N3, e, xi, Uv, v, d, tau, st, acc);
+    } else {
+      df xd[3], zd[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) xd[r] = df_from_double(xl[r]);
+      const float xf[3] = {xd[0].hi, xd[1].hi, xd[2].hi};
+      float guess[3];
+      trilinear_guess(a.m, e, xf, guess);
+      if (!newton_df<G>(a.m, a.k, e, xd, guess, zd, i32, i64)) {
+        a.p.status[i] = PT_ST_NEWTON_FAIL;
+        continue;
+      }
+      const float xs[3] = {zd[0].hi + zd[0].lo, zd[1].hi + zd[1].lo, zd[2].hi + zd[2].lo};
+      float l1[NP], l2[NP], l3[NP];
+      lagr<NP, float>(xs[0], a.k.sn32, a.k.sw32, l1);
+      lagr<NP, float>(xs[1], a.k.sn32, a.k.sw32, l2);
+      lagr<NP, float>(xs[2], a.k.sn32, a.k.sw32, l3);
+      interp4<NP, float>(reinterpret_cast<const float*>(U) + (size_t)e * 5 * N3, l1, l2, l3,
+                         reinterpret_cast<float*>(Uv));
+      particle_accel_f32<G, NP>(a.m, a.k, reinterpret_cast<const float*>(U) + (size_t)e * 5 * N3,
+                                e, zd, reinterpret_cast<const float*>(Uv),
+                                reinterpret_cast<const float*>(v), (float)d, (float)tau, st,
+                                reinterpret_cast<float*>(acc));
+#pragma unroll
+      for (int r = 0; r < 3; ++r) xi[r] = df_to_double(zd[r]);
+    }
+    const R dt = (R)a.dt;
+    const R B1 = F64 ? (R)a.k.B[0] : (R)a.k.B32[0];
+    const R A1 = F64 ? (R)a.k.A[0] : (R)a.k.A32[0];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      a.xi[r * n + i] = xi[r];
+      ao[r * n + i] = acc[r];
+      // the push's register update with the registers at zero (first stage)
+      const R kx = A1 * R(0) + dt * v[r], kv = A1 * R(0) + dt * acc[r];
+      xo[r * n + i] = B1 * kx;
+      vo[r * n + i] = B1 * kv;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Uo[q * n + i] = Uv[q];
+    a.p.status[i] = st;
   }
 }
 
@@ -1211,6 +1334,19 @@ struct Family {
     }
     return 0;
   }
+  static int terms_np(int np, const TermsArgs& a, int grid, int block, cudaStream_t s) {
+    switch (np) {
+      case 2: k_terms<G, 2, F64><<<grid, block, 0, s>>>(a); break;
+      case 3: k_terms<G, 3, F64><<<grid, block, 0, s>>>(a); break;
+      case 4: k_terms<G, 4, F64><<<grid, block, 0, s>>>(a); break;
+      case 5: k_terms<G, 5, F64><<<grid, block, 0, s>>>(a); break;
+      case 6: k_terms<G, 6, F64><<<grid, block, 0, s>>>(a); break;
+      case 7: k_terms<G, 7, F64><<<grid, block, 0, s>>>(a); break;
+      case 8: k_terms<G, 8, F64><<<grid, block, 0, s>>>(a); break;
+      default: return (int)cudaErrorInvalidValue;
+    }
+    return (int)cudaGetLastError();
+  }
   static int find(const FindArgs& a, int grid, int block, cudaStream_t s) {
     k_find<G, F64><<<grid, block, 0, s>>>(a);
     return (int)cudaGetLastError();
@@ -1240,5 +1376,8 @@ struct Family {
   }                                                                                          \
   int NAME##_find(const FindArgs& a, int grid, int block, void* s) {                         \
     return Family<G, F64>::find(a, grid, block, (cudaStream_t)s);                            \
+  }                                                                                          \
+  int NAME##_terms(int np, const TermsArgs& a, int grid, int block, void* s) {              \
+    return Family<G, F64>::terms_np(np, a, grid, block, (cudaStream_t)s);                    \
   }                                                                                          \
   }

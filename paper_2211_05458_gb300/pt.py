@@ -17,6 +17,7 @@ from . import build as _build
 PT_OK, PT_ERR_ARG, PT_ERR_CUDA, PT_ERR_NEWTON, PT_ERR_LOST, PT_ERR_CROSS = 0, 1, 2, 3, 4, 5
 PT_ERR_TIMEOUT, PT_ERR_STATE, PT_WARN_DT = 6, 7, 16
 ST_NEWTON_FAIL, ST_LOST, ST_CROSS_CAP, ST_NEAR_FACE, ST_REP800, ST_OPEN = 1, 2, 4, 8, 16, 32
+ST_NEAR_WALL = 64
 ST_FROZEN = ST_NEWTON_FAIL | ST_LOST | ST_CROSS_CAP | ST_OPEN
 FP64, FP32 = 0, 1
 STOKES, SCHILLER_NAUMANN = 0, 1
@@ -54,11 +55,11 @@ class CParticles(ctypes.Structure):
 
 STAT_FIELDS = ["particle_steps", "crossings", "wall_hits", "newton_it_fp32", "newton_it_fp64",
                "slow_track", "near_face", "newton_fail", "lost", "cross_cap", "open", "rep800",
-               "dt_warn"]
+               "dt_warn", "near_wall"]
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [(f, ctypes.c_int64) for f in STAT_FIELDS] + [("reserved", ctypes.c_int64 * 3)]
+    _fields_ = [(f, ctypes.c_int64) for f in STAT_FIELDS] + [("reserved", ctypes.c_int64 * 2)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f in STAT_FIELDS}
@@ -71,7 +72,8 @@ EXPORTS = ["pt_config_default", "pt_init_mesh", "pt_set_config", "pt_set_fluid",
            "pt_push_host", "pt_deposit", "pt_locate", "pt_mlp_make_pairs", "pt_mlp_train",
            "pt_mlp_features", "pt_mlp_nparams", "pt_mlp_set", "pt_mlp_get", "pt_mlp_forward",
            "pt_mlp_grad", "pt_push_batch", "pt_profile", "pt_profile_read", "pt_destroy",
-           "pt_last_error", "pt_deposit_noalloc", "pt_find_element"]
+           "pt_last_error", "pt_deposit_noalloc", "pt_find_element", "pt_stage_terms",
+           "pt_launch_count", "pt_measure_peak"]
 
 
 def library_path() -> str:
@@ -115,9 +117,13 @@ def lib():
                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                         ctypes.POINTER(Stats)]
             L.pt_find_element.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp]
+            L.pt_stage_terms.argtypes = [_vp, ctypes.POINTER(CParticles), ctypes.c_double, _vp,
+                                         _vp, _vp, _vp, _vp]
             L.pt_profile.argtypes = [_vp, ctypes.c_int32]
             L.pt_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int64)]
+            L.pt_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+            L.pt_measure_peak.argtypes = [ctypes.c_int32, _vp, ctypes.POINTER(ctypes.c_double)]
             L.pt_destroy.argtypes = [_vp]
             L.pt_last_error.argtypes = [_vp]
             L.pt_last_error.restype = ctypes.c_char_p
@@ -290,6 +296,23 @@ class Context:
         self._check(lib().pt_deposit(self.h, ctypes.byref(p), int(mode), _ptr(S)))
         return S
 
+    def stage_terms(self, parts: ParticleSet, dt: float):
+        """First-stage terms by the push's code (no tracking): dict of xi [3][n]
+        float64, U [4][n], acc, dx, dv [3][n] in the particle precision; the
+        particles' status receives the per-particle status bits."""
+        n = parts.n
+        dev, rd = parts.x.device, parts.v.dtype
+        out = dict(xi=torch.zeros((3, n), dtype=torch.float64, device=dev),
+                   U=torch.zeros((4, n), dtype=rd, device=dev),
+                   acc=torch.zeros((3, n), dtype=rd, device=dev),
+                   dx=torch.zeros((3, n), dtype=rd, device=dev),
+                   dv=torch.zeros((3, n), dtype=rd, device=dev))
+        p = parts.struct()
+        self._check(lib().pt_stage_terms(self.h, ctypes.byref(p), float(dt), _ptr(out["xi"]),
+                                          _ptr(out["U"]), _ptr(out["acc"]), _ptr(out["dx"]),
+                                          _ptr(out["dv"])))
+        return out
+
     def find_element(self, x: torch.Tensor):
         """x: [3][n] float64 cuda -> (elem [n] int32, -1 if outside; xi [3][n]; status)."""
         n = x.shape[1]
@@ -360,6 +383,12 @@ class Context:
         self._check(lib().pt_profile_read(self.h, ctypes.byref(ms), ctypes.byref(k)))
         return float(ms.value), int(k.value)
 
+    def launch_count(self):
+        """Kernel launches this context queued since the last call (then cleared)."""
+        k = ctypes.c_int64(0)
+        self._check(lib().pt_launch_count(self.h, ctypes.byref(k)))
+        return int(k.value)
+
     def close(self):
         if getattr(self, "h", None):
             lib().pt_destroy(self.h)
@@ -381,3 +410,14 @@ def push_batch(ctxs, parts, nsteps: int, dt: float, stats: bool = True):
     if rc not in (PT_OK, PT_WARN_DT, PT_ERR_NEWTON, PT_ERR_LOST, PT_ERR_CROSS):
         raise PtError(rc, lib().pt_last_error(ctxs[0].h).decode())
     return [s.as_dict() for s in st] if st is not None else None
+
+
+def measure_peak(kind: int, stream=None) -> float:
+    """Measured FMA throughput of the current device in TFLOP/s (kind 0 FP32,
+    1 FP64), from libpt's own probe kernel."""
+    t = ctypes.c_double(0.0)
+    s = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    rc = lib().pt_measure_peak(int(kind), s, ctypes.byref(t))
+    if rc != 0:
+        raise PtError(rc, "pt_measure_peak failed")
+    return float(t.value)

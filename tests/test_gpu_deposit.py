@@ -127,3 +127,25 @@ def test_two_way_time_step_guard_counts_like_oracle(precision):
     assert st["dt_warn"] == expect
     errors = st["newton_fail"] + st["lost"] + st["cross_cap"]
     assert st["status_code"] == pt.PT_WARN_DT or errors > 0
+
+
+@pytest.mark.parametrize("mode", [pt.DEPOSIT_SEGMENTED, pt.DEPOSIT_SEGMENTED | pt.DEPOSIT_NEAREST])
+def test_segmented_with_large_segments_matches_oracle_and_is_reproducible(mode):
+    """8 elements holding ~5000 particles each: every segment is longer than
+    the shared-memory sort, so the index order is made in global memory."""
+    wl = W.tgv_box(2, 3, P=40_000, nsteps=1, seed=3, precision="fp32")
+    ctx = H.gpu_context(wl, "fp32")
+    parts = H.gpu_particles(wl, ctx)
+    counts = np.bincount(H.np64(wl.elem).astype(np.int64), minlength=8)
+    assert counts.min() > 4096
+    a = ctx.deposit(parts, mode).clone()
+    b = ctx.deposit(parts, mode).clone()
+    assert torch.equal(a, b)
+    orc = H.make_oracle(wl)
+    args = (H.oracle_params(wl), H.np64(wl.x), H.np64(wl.v), H.np64(wl.d),
+            H.np64(wl.elem).astype(np.int32))
+    So = orc.deposit_nearest(*args) if mode & pt.DEPOSIT_NEAREST else orc.deposit(*args)
+    S = a.double().cpu().numpy()
+    assert np.max(np.abs(S - So)) <= 1e-5 * np.abs(So).max()
+    es, eo = S.sum(axis=2), So.sum(axis=2)
+    assert np.max(np.abs(es - eo) / np.abs(eo).max(axis=0, keepdims=True)) < 1e-5

@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 EA = 27  # elements of the coarse block (n = 3)
 
 
-def _run(wl, precision, tol, band=None, min_checked=0.9, **cfg):
+def _run(wl, precision, tol, band=None, **cfg):
     ctx = H.gpu_context(wl, precision, **cfg)
     parts = H.gpu_particles(wl, ctx)
     st = ctx.push(parts, wl.nsteps, wl.dt)
@@ -23,7 +23,7 @@ def _run(wl, precision, tol, band=None, min_checked=0.9, **cfg):
     g = H.gpu_result(parts)
     band_ref, band_x = (1e-10, 1e-10) if band is None else band
     o = H.run_oracle(wl, band_ref=band_ref, band_x=band_x)
-    res = H.compare(g, o, tol, min_checked=min_checked)
+    res = H.compare(g, o, tol)
     start = H.np64(wl.elem) < EA
     # both directions through the mortars were taken
     assert np.sum(start & (g["elem"] >= EA)) >= 5 and np.sum(~start & (g["elem"] < EA)) >= 5
@@ -42,8 +42,7 @@ def test_mortar_fp64_matches_oracle(split, ngeo):
 def test_mortar_fp32_matches_oracle(split, ngeo):
     wl = W.mortar_tgv(3, ngeo, split, N=4, P=400, nsteps=40)
     h = 1.0 / 6
-    res, st = _run(wl, "fp32", 2e-5, band=(2e-4, 1e-4 * h), band_ref=2e-4, band_x=1e-4 * h,
-                   min_checked=0.85)
+    res, st = _run(wl, "fp32", 2e-5, band=(2e-4, 1e-4 * h), band_ref=2e-4, band_x=1e-4 * h)
     assert st["crossings"] > 100
 
 
@@ -53,11 +52,11 @@ def test_mortar_reference_space_localisation(precision):
     element whose part of the big face holds the point."""
     wl = W.mortar_tgv(3, 2, "st", N=4, P=400, nsteps=40)
     if precision == "fp64":
-        _run(wl, "fp64", 1e-12, track=pt.TRACK_REFERENCE, min_checked=0.85)
+        _run(wl, "fp64", 1e-12, track=pt.TRACK_REFERENCE)
     else:
         h = 1.0 / 6
         _run(wl, "fp32", 2e-5, band=(2e-4, 1e-4 * h), band_ref=2e-4, band_x=1e-4 * h,
-             track=pt.TRACK_REFERENCE, min_checked=0.85)
+             track=pt.TRACK_REFERENCE)
 
 
 def test_mortar_bezier_clipping_fp64():

@@ -21,7 +21,7 @@ def _speed_up(wl, seed=0):
     wl.v = wl.v * 4.0 + torch.as_tensor(rng.normal(size=tuple(wl.v.shape)) * 1.5)
 
 
-def _push_and_compare(wl, precision, tol, band=None, idx=None, min_checked=0.9, **cfg):
+def _push_and_compare(wl, precision, tol, band=None, idx=None, **cfg):
     ctx = H.gpu_context(wl, precision, **cfg)
     parts = H.gpu_particles(wl, ctx, idx)
     st = ctx.push(parts, wl.nsteps, wl.dt)
@@ -29,7 +29,7 @@ def _push_and_compare(wl, precision, tol, band=None, idx=None, min_checked=0.9, 
     g = H.gpu_result(parts)
     band_ref, band_x = (1e-10, 1e-10) if band is None else band
     o = H.run_oracle(wl, idx, band_ref=band_ref, band_x=band_x)
-    res = H.compare(g, o, tol, min_checked=min_checked)
+    res = H.compare(g, o, tol)
     res["stats"] = st
     return res, g, o
 
@@ -160,8 +160,7 @@ def test_reference_space_localisation_matches_physical_oracle(precision, tol, ng
     wl = W.curved_channel((6, 6, 6), ngeo, N, P=400, nsteps=40, dt=2e-3, st=(0.1, 100.0))
     _speed_up(wl)
     band = None if precision == "fp64" else (2e-4, 1e-4 * 2.0 / 6)
-    res, g, o = _push_and_compare(wl, precision, tol, band=band, track=pt.TRACK_REFERENCE,
-                                  min_checked=0.85)
+    res, g, o = _push_and_compare(wl, precision, tol, band=band, track=pt.TRACK_REFERENCE)
     assert res["stats"]["crossings"] > 50 and res["stats"]["wall_hits"] >= 1
 
 
@@ -187,7 +186,7 @@ def test_bezier_clipping_fp32():
     _speed_up(wl)
     h = 2.0 / 6
     res, g, o = _push_and_compare(wl, "fp32", 2e-5, band=(2e-4, 1e-4 * h), band_ref=2e-4,
-                                  band_x=1e-4 * h, curved_faces=1, min_checked=0.85)
+                                  band_x=1e-4 * h, curved_faces=1)
     assert res["stats"]["crossings"] > 50
 
 
@@ -204,3 +203,39 @@ def test_bezier_clipping_on_curved_walls_fp64():
     wl.d = torch.full((300,), 4e-3, dtype=torch.float64)
     res, g, o = _push_and_compare(wl, "fp64", 1e-12, curved_faces=1)
     assert res["stats"]["wall_hits"] > 20
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_split_call_resume(precision):
+    """A push of 10 steps equals a push of 5 steps followed by another of 5
+    (the particle state between calls is x, v, elem, hits, status: restartable
+    as the paper's restart files are).  FP64 mode: bitwise.  FP32 mode: inside a
+    call the position is a double-float offset from the element centre; at a
+    call boundary it becomes an FP64 position and back, a rounding of ~1e-16
+    relative that can change the FP32 rounding of a later xi; owners and hits
+    stay exact, x and v agree far inside the FP32 tolerance."""
+    wl = W.curved_channel((6, 6, 6), 2, 5, P=2000, nsteps=10, dt=2e-3, seed=7)
+    _speed_up(wl, seed=7)
+    h = 2.0 / 6
+    band = dict(band_ref=2e-4, band_x=1e-4 * h) if precision == "fp32" else {}
+    ctx = H.gpu_context(wl, precision, **band)
+    one = H.gpu_particles(wl, ctx)
+    two = H.gpu_particles(wl, ctx)
+    st1 = ctx.push(one, 10, wl.dt)
+    ctx.push(two, 5, wl.dt)
+    ctx.push(two, 5, wl.dt)
+    torch.cuda.synchronize()
+    assert st1["crossings"] > 100 and st1["wall_hits"] > 5
+    a, b = H.gpu_result(one), H.gpu_result(two)
+    if precision == "fp64":
+        for k in ("x", "v", "elem", "hits", "status"):
+            assert np.array_equal(a[k], b[k]), k
+    else:
+        near = ((a["status"] | b["status"]) & (pt.ST_NEAR_WALL | pt.ST_FROZEN)) != 0
+        assert near.mean() < 0.05
+        assert np.array_equal(a["elem"][~near], b["elem"][~near])
+        assert np.array_equal(a["hits"][~near], b["hits"][~near])
+        ex = np.abs(a["x"] - b["x"]) / np.maximum(np.abs(a["x"]), 1.0)
+        ev = np.abs(a["v"] - b["v"]) / np.maximum(np.abs(a["v"]), 1.0)
+        print("FP32 call boundary: max rel dx %.2e dv %.2e" % (ex[~near].max(), ev[~near].max()))
+        assert ex[~near].max() <= 1e-9 and ev[~near].max() <= 1e-6
