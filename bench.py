@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--particles", type=int, default=10_000_000)
     ap.add_argument("--dims", type=int, default=64)
     ap.add_argument("--guess", default="auto", choices=["auto", "trilinear", "mlp"])
+    ap.add_argument("--schedule", default="auto", choices=["auto", "resident", "staged"],
+                    help="pt_push kernel schedule (results do not depend on it)")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / fp64 / cpu legs")
     ap.add_argument("--extras", default="trilinear,reference,e2e,fp64,cpu",
                     help="comma list of extra legs to run (trilinear, reference, e2e, fp64, cpu)")
@@ -487,8 +489,10 @@ def main():
     wl = make_workload(args, dev, seed=rank, precision="fp32")
     stream = torch.cuda.current_stream()
     guess = pt.GUESS_TRILINEAR
+    sched = {"auto": pt.SCHEDULE_AUTO, "resident": pt.SCHEDULE_RESIDENT,
+             "staged": pt.SCHEDULE_STAGED}[args.schedule]
     ctx = pt.Context(wl.mesh, stream=stream, precision=pt.FP32, mu=wl.mu, rho_p=wl.rho_p,
-                     drag_law=wl.drag_law, rebin_every=args.inner)
+                     drag_law=wl.drag_law, rebin_every=args.inner, schedule=sched)
     mlp_info = None
     if args.guess in ("auto", "mlp"):
         try:

@@ -76,6 +76,16 @@ typedef enum { PT_GUESS_TRILINEAR = 0, PT_GUESS_MLP = 1 } pt_guess;
  * periodic face) and mapping again (the paper's "localisation in reference
  * space" with face neighbours instead of a background mesh). */
 typedef enum { PT_TRACK_PHYSICAL = 0, PT_TRACK_REFERENCE = 1 } pt_track;
+/* Kernel schedule of pt_push.  RESIDENT: one kernel per pt_push chunk keeps
+ * every particle in registers for all its stages.  STAGED: one kernel per RK
+ * stage over the particle state in element-sorted order (held in library-
+ * owned device buffers of about 116 bytes per particle in PT_FP32 mode, 144 in
+ * PT_FP64 mode), the stage segments that may cross a face collected in a
+ * compacted list and intersected by a second kernel on full warps.  AUTO:
+ * STAGED from 2^18 particles on, RESIDENT below (launch latency dominates
+ * small pushes).  Both run the same arithmetic in the same order per
+ * particle. */
+typedef enum { PT_SCHEDULE_AUTO = 0, PT_SCHEDULE_RESIDENT = 1, PT_SCHEDULE_STAGED = 2 } pt_schedule;
 typedef enum {
   PT_DEPOSIT_ATOMIC = 0,     /* FP32 atomics                                   */
   PT_DEPOSIT_SEGMENTED = 1,  /* element-sorted, fixed summation order          */
@@ -150,7 +160,9 @@ typedef struct {
                            the roots of the face's bilinear patch (default; a
                            crossing it misses is found by the walk after the
                            stage); 1 Bezier clipping of the face's control net   */
-  int32_t reserved[3];
+  int32_t schedule;     /* pt_schedule: how pt_push maps the stages to kernels
+                           (default PT_SCHEDULE_AUTO); results do not depend on it */
+  int32_t reserved[2];
 } pt_config;
 
 /* Particles, structure of arrays, all device memory, caller-owned, updated in

@@ -58,6 +58,22 @@ int fam_g4_fp64_terms(int, const TermsArgs&, int, int, void*);
 int fam_g4_fp32_terms(int, const TermsArgs&, int, int, void*);
 int fam_g5_fp64_terms(int, const TermsArgs&, int, int, void*);
 int fam_g5_fp32_terms(int, const TermsArgs&, int, int, void*);
+int fam_g2_fp64_staged(int, int, const StageArgs&, const DevParticles&, const int*, int, int, void*);
+int fam_g2_fp64_occs(int, int);
+int fam_g2_fp32_staged(int, int, const StageArgs&, const DevParticles&, const int*, int, int, void*);
+int fam_g2_fp32_occs(int, int);
+int fam_g3_fp64_staged(int, int, const StageArgs&, const DevParticles&, const int*, int, int, void*);
+int fam_g3_fp64_occs(int, int);
+int fam_g3_fp32_staged(int, int, const StageArgs&, const DevParticles&, const int*, int, int, void*);
+int fam_g3_fp32_occs(int, int);
+int fam_g4_fp64_staged(int, int, const StageArgs&, const DevParticles&, const int*, int, int, void*);
+int fam_g4_fp64_occs(int, int);
+int fam_g4_fp32_staged(int, int, const StageArgs&, const DevParticles&, const int*, int, int, void*);
+int fam_g4_fp32_occs(int, int);
+int fam_g5_fp64_staged(int, int, const StageArgs&, const DevParticles&, const int*, int, int, void*);
+int fam_g5_fp64_occs(int, int);
+int fam_g5_fp32_staged(int, int, const StageArgs&, const DevParticles&, const int*, int, int, void*);
+int fam_g5_fp32_occs(int, int);
 int fam_g2_fp64_find(const FindArgs&, int, int, void*);
 int fam_g2_fp32_find(const FindArgs&, int, int, void*);
 int fam_g3_fp64_find(const FindArgs&, int, int, void*);
@@ -85,6 +101,13 @@ int max_active_push(int g, bool f64, int np, int block) {
 }
 int launch_find(int g, bool f64, const FindArgs& a, int grid, int block, void* s) {
   return PT_DISPATCH(g, f64, find, a, grid, block, s);
+}
+int launch_staged(int g, bool f64, int np, int op, const StageArgs& a, const DevParticles& p,
+                  const int* perm, int grid, int block, void* s) {
+  return PT_DISPATCH(g, f64, staged, np, op, a, p, perm, grid, block, s);
+}
+int max_active_stage(int g, bool f64, int np, int block) {
+  return PT_DISPATCH(g, f64, occs, np, block);
 }
 int launch_terms(int g, bool f64, int np, const TermsArgs& a, int grid, int block, void* s) {
   return PT_DISPATCH(g, f64, terms, np, a, grid, block, s);
@@ -682,6 +705,8 @@ static pt_status check_config(const pt_config* cfg) {
   if (cfg->lift != 0 && cfg->lift != 1) return fail(nullptr, PT_ERR_ARG, "lift must be 0 or 1");
   if (cfg->curved_faces != 0 && cfg->curved_faces != 1)
     return fail(nullptr, PT_ERR_ARG, "curved_faces must be 0 or 1");
+  if (cfg->schedule < PT_SCHEDULE_AUTO || cfg->schedule > PT_SCHEDULE_STAGED)
+    return fail(nullptr, PT_ERR_ARG, "schedule must be a pt_schedule value");
   if (cfg->buoyancy != 0 && cfg->buoyancy != 1)
     return fail(nullptr, PT_ERR_ARG, "buoyancy must be 0 or 1");
   if (cfg->track != PT_TRACK_PHYSICAL && cfg->track != PT_TRACK_REFERENCE)
@@ -900,11 +925,145 @@ static cudaEvent_t take_event(pt_ctx* c) {
   return e;
 }
 
+// particles from which PT_SCHEDULE_AUTO takes the staged schedule
+static const int64_t kStagedMin = (int64_t)1 << 18;
+
+static bool use_staged(const pt_ctx* c, int64_t n) {
+  if (c->cfg.schedule == PT_SCHEDULE_STAGED) return true;
+  if (c->cfg.schedule == PT_SCHEDULE_RESIDENT) return false;
+  return n >= kStagedMin;
+}
+
+// Carves the staged schedule's state buffers for n particles out of one
+// allocation (grown on demand).
+static pt_status stage_args(pt_ctx* c, int64_t n, StageArgs& a) {
+  const bool f64 = c->cfg.precision == PT_FP64;
+  const size_t rs = f64 ? 8 : 4;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t nn = (size_t)std::max<int64_t>(n, 1);
+  size_t bytes = 0;
+  if (f64) bytes += al(24 * nn);                      // x
+  else bytes += 2 * al(12 * nn);                      // xh, xl
+  bytes += 3 * al(3 * rs * nn) + al(rs * nn);         // v, kx, kv, d
+  bytes += al((f64 ? 24 : 24) * nn);                  // xe
+  bytes += f64 ? 0 : al(12 * nn);                     // guess
+  bytes += 4 * al(4 * nn) + 256;                      // e, hits, st, list, counters
+  if (c->state_cap < n || !c->d_state) {
+    if (c->d_state) cudaFree(c->d_state);
+    c->d_state = nullptr;
+    c->state_cap = 0;
+    CK(cudaMalloc(&c->d_state, bytes));
+    c->state_cap = n;
+  }
+  char* b = (char*)c->d_state;
+  auto take = [&](size_t sz) {
+    char* q = b;
+    b += al(sz);
+    return (void*)q;
+  };
+  a.x = nullptr;
+  a.xh = a.xl = nullptr;
+  a.guess = nullptr;
+  if (f64) {
+    a.x = (double*)take(24 * nn);
+  } else {
+    a.xh = (float*)take(12 * nn);
+    a.xl = (float*)take(12 * nn);
+  }
+  a.v = take(3 * rs * nn);
+  a.kx = take(3 * rs * nn);
+  a.kv = take(3 * rs * nn);
+  a.d = take(rs * nn);
+  a.xe = take(24 * nn);
+  if (!f64) a.guess = (float*)take(12 * nn);
+  a.e = (int*)take(4 * nn);
+  a.hits = (int*)take(4 * nn);
+  a.st = (unsigned*)take(4 * nn);
+  a.list = (unsigned*)take(4 * nn);
+  a.count = (unsigned*)b;
+  a.count_next = a.count + 1;
+  return PT_OK;
+}
+
+// The staged schedule: per chunk of rebin_every steps, binning, the sorted
+// copy of the particle state, per RK stage (the learned start,) the stage
+// kernel and the exact-tracking kernel over its list, and the copy back.
+static pt_status push_staged(pt_ctx* c, const pt_particles* p, int32_t nsteps, double dt) {
+  const int64_t n = p->n;
+  const bool f64 = c->cfg.precision == PT_FP64;
+  const bool mlp = !f64 && c->cfg.guess == PT_GUESS_MLP;
+  const int np = c->N + 1;
+  StageArgs a;
+  pt_status s = stage_args(c, n, a);
+  if (s) return s;
+  a.m = dev_mesh(c);
+  fill_consts(c, a.k);
+  a.mlp = pt_dev_mlp(c);
+  a.U = c->U;
+  a.n = n;
+  a.dt = dt;
+  a.stats = c->d_stats;
+  const DevParticles dp = {n, p->x, p->v, p->d, p->elem, p->hits, p->status};
+  const int block = 128;
+  const int occ = max_active_stage(c->g, f64, np, block);
+  const int grid = grid_for(c, n, block, occ);
+  const int gmove = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)c->nsm * 8));
+  const int gtrack = c->nsm * 4;
+  const int gguess = (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, (int64_t)c->nsm * 8));
+  unsigned* const ctr = a.count;  // two list counters, used by alternate stages
+  CK(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), c->stream));
+  const int chunk = c->cfg.rebin_every > 0 ? c->cfg.rebin_every : 10;
+  int k = 0;
+  for (int s0 = 0; s0 < nsteps; s0 += chunk) {
+    int rc = bin_by_element(p->elem, n, c->nelem, c->d_scratch, c->d_perm, nullptr, c->nsm,
+                            c->stream);
+    if (rc) return fail(c, PT_ERR_CUDA, "binning: %s", cudaGetErrorString((cudaError_t)rc));
+    c->launches += 5;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->profile) {
+      e0 = take_event(c);
+      e1 = take_event(c);
+      if (e0) cudaEventRecord(e0, c->stream);
+    }
+    rc = launch_staged(c->g, f64, np, PT_SOP_GATHER, a, dp, c->d_perm, gmove, 256, c->stream);
+    const int ns = std::min(chunk, nsteps - s0);
+    for (int step = 0; step < ns && !rc; ++step) {
+      for (int st = 0; st < 5 && !rc; ++st, ++k) {
+        a.stage = st;
+        a.count = ctr + (k & 1);
+        a.count_next = ctr + ((k + 1) & 1);
+        if (mlp) {
+          rc = launch_staged(c->g, f64, np, PT_SOP_GUESS, a, dp, c->d_perm, gguess, 128,
+                             c->stream);
+          c->launches += 1;
+        }
+        if (!rc) rc = launch_staged(c->g, f64, np, PT_SOP_STAGE, a, dp, c->d_perm, grid, block,
+                                    c->stream);
+        if (!rc) rc = launch_staged(c->g, f64, np, PT_SOP_TRACK, a, dp, c->d_perm, gtrack, 128,
+                                    c->stream);
+        c->launches += 2;
+      }
+    }
+    if (!rc) rc = launch_staged(c->g, f64, np, PT_SOP_SCATTER, a, dp, c->d_perm, gmove, 256,
+                                c->stream);
+    c->launches += 2;
+    if (e1) cudaEventRecord(e1, c->stream);
+    if (rc) return fail(c, PT_ERR_CUDA, "staged push launch: %s",
+                        cudaGetErrorString((cudaError_t)rc));
+  }
+  return PT_OK;
+}
+
 pt_status pt_push_impl(pt_ctx* c, const pt_particles* p, int32_t nsteps, double dt,
                        pt_stats* out) {
   const int64_t n = p->n;
   CK(cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * PT_C_COUNT, c->stream));
-  if (n > 0 && nsteps > 0) {
+  if (n > 0 && nsteps > 0 && use_staged(c, n)) {
+    pt_status s = ensure_scratch(c, n);
+    if (s) return s;
+    s = push_staged(c, p, nsteps, dt);
+    if (s) return s;
+  } else if (n > 0 && nsteps > 0) {
     pt_status s = ensure_scratch(c, n);
     if (s) return s;
     const bool f64 = c->cfg.precision == PT_FP64;
@@ -1294,6 +1453,7 @@ pt_status pt_destroy(pt_ctx* c) {
   if (c->d_stage) cudaFree(c->d_stage);
   if (c->d_src) cudaFree(c->d_src);
   if (c->d_perm2) cudaFree(c->d_perm2);
+  if (c->d_state) cudaFree(c->d_state);
   pt_mlp_release(c);
   pt_batch_release(c);
   delete c;

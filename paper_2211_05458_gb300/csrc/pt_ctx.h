@@ -63,6 +63,9 @@ struct pt_ctx {
   int grid_dims[3] = {0, 0, 0};
   // batched push plan (pt_push_batch called with this context first)
   pt_batch_plan* batch = nullptr;
+  // particle state of the staged schedule (sorted order), grown on demand
+  void* d_state = nullptr;
+  int64_t state_cap = 0;
   // kernels queued since the last pt_launch_count
   int64_t launches = 0;
   // kernel timing (pt_profile)

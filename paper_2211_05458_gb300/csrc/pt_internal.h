@@ -142,6 +142,35 @@ struct DepositArgs {
   float4* src;            // [2 n] per-particle sources of the two-pass segmented mode
 };
 
+// One RK stage of the staged schedule: the particle state in element-sorted
+// order (library-owned structure-of-arrays, index t), the list of stage
+// segments that need exact tracking or the walk, and the counters.
+struct StageArgs {
+  DevMesh m;
+  DevConsts k;
+  DevMLP mlp;
+  const void* U;          // fluid state
+  int64_t n;
+  double* x;              // FP64 mode: [3][n] positions
+  float* xh;              // FP32 mode: [3][n] double-float offset from the owner's
+  float* xl;              //            centre, high and low parts
+  void* v;                // [3][n] velocity, mode precision
+  void* kx;               // [3][n] RK registers of x and v
+  void* kv;
+  const void* d;          // [n] diameters
+  void* xe;               // stage end of listed particles: FP64 [3][n]; FP32 [6][n] hi, lo
+  int* e;                 // [n] owner
+  int* hits;              // [n]
+  unsigned* st;           // [n] status bits
+  float* guess;           // [3][n] learned start (MLP) or null
+  unsigned* list;         // [n] listed positions (| 1 << 31: walk only)
+  unsigned* count;        // entries in list
+  unsigned* count_next;   // the next stage's counter (cleared by this stage)
+  int stage;              // 0..4
+  double dt;
+  unsigned long long* stats;
+};
+
 // first-stage terms of each particle (pt_stage_terms): p.status receives the
 // status bits, the other outputs are [q][n] arrays in the mode's precision
 struct TermsArgs {
@@ -167,4 +196,9 @@ int launch_deposit(int g, bool fp64, int np, int mode, const DepositArgs& a, int
                    void* stream);
 int max_active_push(int g, bool fp64, int np, int block);
 int launch_terms(int g, bool fp64, int np, const TermsArgs& a, int grid, int block, void* stream);
+// staged schedule: op 0 gather, 1 stage, 2 track, 3 learned start, 4 scatter back
+enum { PT_SOP_GATHER = 0, PT_SOP_STAGE = 1, PT_SOP_TRACK = 2, PT_SOP_GUESS = 3, PT_SOP_SCATTER = 4 };
+int launch_staged(int g, bool fp64, int np, int op, const StageArgs& a, const DevParticles& p,
+                  const int* perm, int grid, int block, void* stream);
+int max_active_stage(int g, bool fp64, int np, int block);
 }  // namespace pt

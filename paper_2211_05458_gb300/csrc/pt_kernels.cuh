@@ -1242,6 +1242,10 @@ __global__ void __launch_bounds__(128) k_terms(const __grid_constant__ TermsArgs
   }
 }
 
+}  // namespace pt
+#include "pt_staged.cuh"
+namespace pt {
+
 // launch helpers for one (G, mode) family
 template <int G, bool F64>
 struct Family {
@@ -1347,6 +1351,81 @@ struct Family {
     }
     return (int)cudaGetLastError();
   }
+  template <int NP>
+  static int staged(int op, const StageArgs& a, const DevParticles& p, const int* perm, int grid,
+                    int block, cudaStream_t s) {
+    const bool clip = a.k.curved_clip != 0;
+    switch (op) {
+      case PT_SOP_GATHER: k_gather<F64><<<grid, block, 0, s>>>(a, p, perm); break;
+      case PT_SOP_SCATTER: k_scatter_back<F64><<<grid, block, 0, s>>>(a, p, perm); break;
+      case PT_SOP_STAGE:
+        if constexpr (F64) {
+          k_stage_f64<G, NP><<<grid, block, 0, s>>>(a);
+        } else {
+          if (kMlp && a.k.guess == PT_GUESS_MLP)
+            k_stage_f32<G, NP, kMlp><<<grid, block, 0, s>>>(a);
+          else
+            k_stage_f32<G, NP, false><<<grid, block, 0, s>>>(a);
+        }
+        break;
+      case PT_SOP_TRACK:
+        if constexpr (F64) {
+          if (clip)
+            k_track_f64<G, true><<<grid, block, 0, s>>>(a);
+          else
+            k_track_f64<G, false><<<grid, block, 0, s>>>(a);
+        } else {
+          if (clip)
+            k_track_f32<G, true><<<grid, block, 0, s>>>(a);
+          else
+            k_track_f32<G, false><<<grid, block, 0, s>>>(a);
+        }
+        break;
+      case PT_SOP_GUESS:
+        if constexpr (kMlp) {
+          k_guess_mlp<G><<<grid, block, 0, s>>>(a);
+          break;
+        } else {
+          return (int)cudaErrorInvalidValue;
+        }
+      default: return (int)cudaErrorInvalidValue;
+    }
+    return (int)cudaGetLastError();
+  }
+  template <int NP>
+  static int occ_stage(int block) {
+    int nb = 0;
+    if constexpr (F64)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage_f64<G, NP>, block, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage_f32<G, NP, false>, block, 0);
+    return nb;
+  }
+  static int staged_np(int np, int op, const StageArgs& a, const DevParticles& p, const int* perm,
+                       int grid, int block, cudaStream_t s) {
+    switch (np) {
+      case 2: return staged<2>(op, a, p, perm, grid, block, s);
+      case 3: return staged<3>(op, a, p, perm, grid, block, s);
+      case 4: return staged<4>(op, a, p, perm, grid, block, s);
+      case 5: return staged<5>(op, a, p, perm, grid, block, s);
+      case 6: return staged<6>(op, a, p, perm, grid, block, s);
+      case 7: return staged<7>(op, a, p, perm, grid, block, s);
+      case 8: return staged<8>(op, a, p, perm, grid, block, s);
+    }
+    return (int)cudaErrorInvalidValue;
+  }
+  static int occ_stage_np(int np, int block) {
+    switch (np) {
+      case 2: return occ_stage<2>(block);
+      case 3: return occ_stage<3>(block);
+      case 4: return occ_stage<4>(block);
+      case 5: return occ_stage<5>(block);
+      case 6: return occ_stage<6>(block);
+      case 7: return occ_stage<7>(block);
+      case 8: return occ_stage<8>(block);
+    }
+    return 0;
+  }
   static int find(const FindArgs& a, int grid, int block, cudaStream_t s) {
     k_find<G, F64><<<grid, block, 0, s>>>(a);
     return (int)cudaGetLastError();
@@ -1380,4 +1459,9 @@ struct Family {
   int NAME##_terms(int np, const TermsArgs& a, int grid, int block, void* s) {              \
     return Family<G, F64>::terms_np(np, a, grid, block, (cudaStream_t)s);                    \
   }                                                                                          \
+  int NAME##_staged(int np, int op, const StageArgs& a, const DevParticles& p, const int* perm,\
+                    int grid, int block, void* s) {                                         \
+    return Family<G, F64>::staged_np(np, op, a, p, perm, grid, block, (cudaStream_t)s);     \
+  }                                                                                         \
+  int NAME##_occs(int np, int block) { return Family<G, F64>::occ_stage_np(np, block); }    \
   }

@@ -1,0 +1,516 @@
+// pt_staged.cuh -- the push as one kernel per RK stage (the "staged" schedule).
+//
+// The resident push (k_push) keeps every particle in registers for all
+// nsteps x 5 stages of a call; its one kernel carries the inverse map, the
+// interpolation, the drag, the RK update, the exact face intersection, the
+// walk and (optionally) the learned start, so that its register budget and
+// instruction footprint are those of the largest path, and a warp in which one
+// lane intersects faces stalls the other 31.  The staged schedule splits a
+// stage into
+//   k_stage_*   every live particle: start guess, inverse map, interpolation,
+//               drag, RK update and the FP32 slab test; a particle whose stage
+//               segment may touch a face (~0.5 % at the 64^3 workload) is
+//               appended to a compacted list instead of being intersected;
+//   k_track_*   the listed particles on full warps: exact tracking through
+//               the faces (Secs. 3.2.3, 3.2.4, 2.4) and the walk that checks
+//               the new owner (the missed-crossing repair of the resident
+//               push, run at once instead of at the next stage's start);
+// and, with the learned start, k_guess_mlp before k_stage_*.  Between stages
+// the particle state goes through HBM in element-sorted order: k_gather
+// copies it from the caller's arrays into library-owned structure-of-arrays
+// buffers (coalesced in the visiting order), k_scatter copies it back.  Every
+// arithmetic step is the resident push's own device code, in the same order.
+#pragma once
+#include "pt_kernels.cuh"
+
+#ifndef PT_STAGE_MINB
+#define PT_STAGE_MINB 3
+#endif
+
+namespace pt {
+
+// list entry: position t in the sorted state; the high bit marks a stage end
+// that needs only the walk (reference-space localisation without a wall)
+constexpr unsigned kSettleOnly = 0x80000000u;
+
+// Appends t (| flag) for every lane with want != 0; warp-collective (all 32
+// lanes must call it).
+__device__ __forceinline__ void list_append(const StageArgs& a, int64_t t, unsigned want) {
+  const unsigned m = __ballot_sync(0xffffffffu, want != 0u);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  unsigned base = 0u;
+  if (lane == leader) base = atomicAdd(a.count, (unsigned)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (want) a.list[base + __popc(m & ((1u << lane) - 1u))] = (unsigned)t | (want == 2u ? kSettleOnly : 0u);
+}
+
+__device__ __forceinline__ void stage_counters(const StageArgs& a, const PushCounters& c) {
+  count_add(a.stats, PT_C_STEPS, c.steps);
+  count_add(a.stats, PT_C_IT32, c.it32);
+  count_add(a.stats, PT_C_IT64, c.it64);
+  count_add(a.stats, PT_C_CROSS, (unsigned long long)c.tc.cross);
+  count_add(a.stats, PT_C_HITS, (unsigned long long)c.tc.hits);
+  count_add(a.stats, PT_C_SLOW, (unsigned long long)c.tc.slow);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 mode: position as a double-float offset from the owner's centre
+// ---------------------------------------------------------------------------
+
+// Returns 0 (stage end committed), 1 (listed for exact tracking) or 2 (listed
+// for the walk only).
+template <int G, int NP, bool MLP>
+__device__ __forceinline__ unsigned stage_one_f32(const StageArgs& a, int64_t t,
+                                                  PushCounters& c) {
+  constexpr int N3 = NP * NP * NP;
+  const int64_t n = a.n;
+  const int s = a.stage;
+  unsigned st = a.st[t];
+  if (st & PT_ST_FROZEN) return 0u;
+  const int e = a.e[t];
+  float* vg = reinterpret_cast<float*>(a.v);
+  float* kxg = reinterpret_cast<float*>(a.kx);
+  float* kvg = reinterpret_cast<float*>(a.kv);
+  const float d = reinterpret_cast<const float*>(a.d)[t];
+  df xd[3];
+  float v[3], kx[3] = {0.f, 0.f, 0.f}, kv[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    xd[r] = df{a.xh[r * n + t], a.xl[r * n + t]};
+    v[r] = vg[r * n + t];
+    if (s > 0) {
+      kx[r] = kxg[r * n + t];
+      kv[r] = kvg[r * n + t];
+    }
+  }
+  const float mu = (float)a.k.mu;
+  const float tau = (float)a.k.rho_p * d * d / (18.f * mu);
+  float xf[3] = {xd[0].hi, xd[1].hi, xd[2].hi};
+  float guess[3];
+  if constexpr (MLP) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) guess[r] = a.guess[r * n + t];
+  } else {
+    trilinear_guess(a.m, e, xf, guess);
+  }
+  df zd[3];
+  int i32 = 0, i64 = 0;
+  const bool ok = newton_df<G>(a.m, a.k, e, xd, guess, zd, i32, i64);
+  c.it32 += i32;
+  c.it64 += i64;
+  if (!ok) {
+    a.st[t] = st | PT_ST_NEWTON_FAIL;
+    return 0u;
+  }
+  const float xi[3] = {zd[0].hi + zd[0].lo, zd[1].hi + zd[1].lo, zd[2].hi + zd[2].lo};
+  const float mx = tmax3(xi[0], xi[1], xi[2]);
+  if (mx > 1.f - fmaxf(1e-5f, (float)a.k.band_ref)) {  // decide the bands exactly (rare)
+    const double z[3] = {df_to_double(zd[0]), df_to_double(zd[1]), df_to_double(zd[2])};
+    const double md = tmax3(z[0], z[1], z[2]);
+    if (md > 1.0 + a.k.lost_tol) {  // outside: the walk after the last crossing ran already
+      a.st[t] = st | PT_ST_LOST;
+      return 0u;
+    }
+    if (md > 1.0 - a.k.band_ref) st |= near_bits(a.m, e, z, a.k.band_ref);
+  }
+  // interpolation of rho, rho u at xi, drag + gravity
+  const float* Ue = reinterpret_cast<const float*>(a.U) + (size_t)e * 5 * N3;
+  float l1[NP], l2[NP], l3[NP], Uv[4], acc[3];
+  lagr<NP, float>(xi[0], a.k.sn32, a.k.sw32, l1);
+  lagr<NP, float>(xi[1], a.k.sn32, a.k.sw32, l2);
+  lagr<NP, float>(xi[2], a.k.sn32, a.k.sw32, l3);
+  interp4<NP, float>(Ue, l1, l2, l3, Uv);
+  particle_accel_f32<G, NP>(a.m, a.k, Ue, e, zd, Uv, v, d, tau, st, acc);
+  const float As = a.k.A32[s], Bs = a.k.B32[s], dt = (float)a.dt;
+  df xe[3];
+  float bf[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    kx[r] = As * kx[r] + dt * v[r];
+    kv[r] = As * kv[r] + dt * acc[r];
+    xe[r] = df_add(xd[r], df_from(Bs * kx[r]));
+    bf[r] = xe[r].hi;
+    v[r] = v[r] + Bs * kv[r];
+  }
+  const int touch = slab_touch(a.m, e, xf, bf);
+  unsigned list = 0u;
+  if (!(touch & (a.k.track == PT_TRACK_REFERENCE ? 2 : 1))) {
+    // no face reachable, or (localisation) no wall or open face: with a touch
+    // the end point's owner is checked by the walk
+#pragma unroll
+    for (int r = 0; r < 3; ++r) xd[r] = xe[r];
+    if (touch) list = 2u;
+  } else {
+    float* xeg = reinterpret_cast<float*>(a.xe);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      xeg[r * n + t] = xe[r].hi;
+      xeg[(3 + r) * n + t] = xe[r].lo;
+    }
+    list = 1u;
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    a.xh[r * n + t] = xd[r].hi;
+    a.xl[r * n + t] = xd[r].lo;
+    vg[r * n + t] = v[r];
+    if (s < 4) {
+      kxg[r * n + t] = kx[r];
+      kvg[r * n + t] = kv[r];
+    }
+  }
+  a.st[t] = st;
+  if (s == 4 && !list) ++c.steps;
+  return list;
+}
+
+template <int G, int NP, bool MLP>
+__global__ void __launch_bounds__(128, PT_STAGE_MINB) k_stage_f32(const __grid_constant__ StageArgs a) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.count_next = 0u;
+  PushCounters c = {0, 0, 0, {0, 0, 0}};
+  const int64_t n = a.n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nround = (n + stride - 1) / stride * stride;  // uniform trip count per warp
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nround; t += stride) {
+    const unsigned want = t < n ? stage_one_f32<G, NP, MLP>(a, t, c) : 0u;
+    list_append(a, t, want);
+  }
+  stage_counters(a, c);
+}
+
+// Exact tracking of the listed stage segments, then the walk that checks the
+// new owner; FP64 on global positions, back to the double-float offset.
+template <int G, bool CLIP>
+__global__ void __launch_bounds__(128) k_track_f32(const __grid_constant__ StageArgs a) {
+  PushCounters c = {0, 0, 0, {0, 0, 0}};
+  const int64_t n = a.n;
+  const int s = a.stage;
+  const unsigned cnt = *a.count;
+  float* vg = reinterpret_cast<float*>(a.v);
+  float* kxg = reinterpret_cast<float*>(a.kx);
+  float* kvg = reinterpret_cast<float*>(a.kv);
+  const float* xeg = reinterpret_cast<const float*>(a.xe);
+  const unsigned stride = gridDim.x * blockDim.x;
+  const unsigned cround = (cnt + stride - 1) / stride * stride;
+  for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < cround; j += stride) {
+    if (j >= cnt) continue;
+    const unsigned ent = a.list[j];
+    const int64_t t = ent & ~kSettleOnly;
+    unsigned st = a.st[t];
+    int e = a.e[t], hits = a.hits[t];
+    df xd[3];
+    float v[3], kx[3], kv[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      xd[r] = df{a.xh[r * n + t], a.xl[r * n + t]};
+      v[r] = vg[r * n + t];
+      kx[r] = kxg[r * n + t];  // stale at the last stage of a step: not used after it
+      kv[r] = kvg[r * n + t];
+    }
+    bool frozen = false;
+    if (!(ent & kSettleOnly)) {
+      const double* ce = a.m.ce + 3 * (size_t)e;
+      double xs[3], xg[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const double cr = __ldg(ce + r);
+        xs[r] = cr + df_to_double(xd[r]);
+        xg[r] = cr + df_to_double(df{xeg[r * n + t], xeg[(3 + r) * n + t]});
+      }
+      track_slow<G, float, CLIP>(a.m, a.k, e, xs, xg, v, kx, kv, hits, st, c.tc);
+      const double* cn = a.m.ce + 3 * (size_t)e;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) xd[r] = df_from_double(xs[r] - __ldg(cn + r));
+      frozen = (st & PT_ST_FROZEN) != 0;
+    }
+    if (!frozen) {
+      df zd[3];
+      int cr = 0, j32 = 0, j64 = 0;
+      const int rc = settle_f32<G>(a.m, a.k, e, xd, zd, false, j32, j64, cr);
+      c.it32 += j32;
+      c.it64 += j64;
+      c.tc.cross += cr;
+      if (rc) st |= rc == 1 ? PT_ST_NEWTON_FAIL : PT_ST_LOST;
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      a.xh[r * n + t] = xd[r].hi;
+      a.xl[r * n + t] = xd[r].lo;
+      vg[r * n + t] = v[r];
+      if (s < 4) {
+        kxg[r * n + t] = kx[r];
+        kvg[r * n + t] = kv[r];
+      }
+    }
+    a.e[t] = e;
+    a.hits[t] = hits;
+    a.st[t] = st;
+    if (s == 4 && !(st & PT_ST_FROZEN)) ++c.steps;
+  }
+  stage_counters(a, c);
+}
+
+// Learned start of every live particle at the current position (the network
+// is warp-collective: every lane takes part, dead lanes with live = false).
+template <int G>
+__global__ void __launch_bounds__(128) k_guess_mlp(const __grid_constant__ StageArgs a) {
+  PT_MLP_PROLOGUE(true, a.mlp);
+  const int64_t n = a.n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nround = (n + stride - 1) / stride * stride;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nround; t += stride) {
+    const bool inr = t < n;
+    const unsigned st = inr ? a.st[t] : (unsigned)PT_ST_FROZEN;
+    const bool live = !(st & PT_ST_FROZEN);
+    const int e = live ? a.e[t] : 0;
+    float xf[3] = {0.f, 0.f, 0.f};
+    if (live) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) xf[r] = a.xh[r * n + t];
+    }
+    float guess[3];
+    start_guess_local<G, true>(a.m, a.k, sm, &a.mlp, e, xf, live, guess);
+    if (live) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) a.guess[r * n + t] = guess[r];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 mode: global FP64 positions
+// ---------------------------------------------------------------------------
+
+template <int G, int NP>
+__device__ __forceinline__ unsigned stage_one_f64(const StageArgs& a, int64_t t,
+                                                  PushCounters& c) {
+  constexpr int N3 = NP * NP * NP;
+  const int64_t n = a.n;
+  const int s = a.stage;
+  unsigned st = a.st[t];
+  if (st & PT_ST_FROZEN) return 0u;
+  const int e = a.e[t];
+  double* vg = reinterpret_cast<double*>(a.v);
+  double* kxg = reinterpret_cast<double*>(a.kx);
+  double* kvg = reinterpret_cast<double*>(a.kv);
+  const double d = reinterpret_cast<const double*>(a.d)[t];
+  double x[3], v[3], kx[3] = {0, 0, 0}, kv[3] = {0, 0, 0};
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    x[r] = a.x[r * n + t];
+    v[r] = vg[r * n + t];
+    if (s > 0) {
+      kx[r] = kxg[r * n + t];
+      kv[r] = kvg[r * n + t];
+    }
+  }
+  const double tau = a.k.rho_p * d * d / (18.0 * a.k.mu);
+  const double* ce = a.m.ce + 3 * (size_t)e;
+  double xl[3] = {x[0] - __ldg(ce), x[1] - __ldg(ce + 1), x[2] - __ldg(ce + 2)};
+  const float xf[3] = {(float)xl[0], (float)xl[1], (float)xl[2]};
+  float guess[3];
+  trilinear_guess(a.m, e, xf, guess);
+  double xi[3];
+  int i32 = 0, i64 = 0;
+  const bool ok = locate_local<G, true>(a.m, a.k, e, xl, guess, xi, i32, i64);
+  c.it32 += i32;
+  c.it64 += i64;
+  if (!ok) {
+    a.st[t] = st | PT_ST_NEWTON_FAIL;
+    return 0u;
+  }
+  const double mx = tmax3(xi[0], xi[1], xi[2]);
+  if (mx > 1.0 + a.k.lost_tol) {
+    a.st[t] = st | PT_ST_LOST;
+    return 0u;
+  }
+  if (mx > 1.0 - a.k.band_ref) st |= near_bits(a.m, e, xi, a.k.band_ref);
+  const double* Ue = reinterpret_cast<const double*>(a.U) + (size_t)e * 5 * N3;
+  double l1[NP], l2[NP], l3[NP], Uv[4], acc[3];
+  lagr<NP, double>(xi[0], a.k.sn, a.k.sw, l1);
+  lagr<NP, double>(xi[1], a.k.sn, a.k.sw, l2);
+  lagr<NP, double>(xi[2], a.k.sn, a.k.sw, l3);
+  interp4<NP, double>(Ue, l1, l2, l3, Uv);
+  particle_accel<G, NP, double>(a.m, a.k, Ue, e, xi, Uv, v, d, tau, st, acc);
+  const double As = a.k.A[s], Bs = a.k.B[s], dt = a.dt;
+  double xe[3];
+  float bf[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    kx[r] = As * kx[r] + dt * v[r];
+    kv[r] = As * kv[r] + dt * acc[r];
+    const double dx = Bs * kx[r];
+    xe[r] = x[r] + dx;
+    bf[r] = (float)(xl[r] + dx);
+    v[r] = v[r] + Bs * kv[r];
+  }
+  const int touch = slab_touch(a.m, e, xf, bf);
+  unsigned list = 0u;
+  if (!(touch & (a.k.track == PT_TRACK_REFERENCE ? 2 : 1))) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) x[r] = xe[r];
+    if (touch) list = 2u;
+  } else {
+    double* xeg = reinterpret_cast<double*>(a.xe);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) xeg[r * n + t] = xe[r];
+    list = 1u;
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    a.x[r * n + t] = x[r];
+    vg[r * n + t] = v[r];
+    if (s < 4) {
+      kxg[r * n + t] = kx[r];
+      kvg[r * n + t] = kv[r];
+    }
+  }
+  a.st[t] = st;
+  if (s == 4 && !list) ++c.steps;
+  return list;
+}
+
+template <int G, int NP>
+__global__ void __launch_bounds__(128, PT_PUSH_MINB_F64) k_stage_f64(const __grid_constant__ StageArgs a) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.count_next = 0u;
+  PushCounters c = {0, 0, 0, {0, 0, 0}};
+  const int64_t n = a.n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nround = (n + stride - 1) / stride * stride;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nround; t += stride) {
+    const unsigned want = t < n ? stage_one_f64<G, NP>(a, t, c) : 0u;
+    list_append(a, t, want);
+  }
+  stage_counters(a, c);
+}
+
+template <int G, bool CLIP>
+__global__ void __launch_bounds__(128) k_track_f64(const __grid_constant__ StageArgs a) {
+  PushCounters c = {0, 0, 0, {0, 0, 0}};
+  const int64_t n = a.n;
+  const int s = a.stage;
+  const unsigned cnt = *a.count;
+  double* vg = reinterpret_cast<double*>(a.v);
+  double* kxg = reinterpret_cast<double*>(a.kx);
+  double* kvg = reinterpret_cast<double*>(a.kv);
+  const double* xeg = reinterpret_cast<const double*>(a.xe);
+  const unsigned stride = gridDim.x * blockDim.x;
+  const unsigned cround = (cnt + stride - 1) / stride * stride;
+  for (unsigned j = blockIdx.x * blockDim.x + threadIdx.x; j < cround; j += stride) {
+    if (j >= cnt) continue;
+    const unsigned ent = a.list[j];
+    const int64_t t = ent & ~kSettleOnly;
+    unsigned st = a.st[t];
+    int e = a.e[t], hits = a.hits[t];
+    double x[3], v[3], kx[3], kv[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      x[r] = a.x[r * n + t];
+      v[r] = vg[r * n + t];
+      kx[r] = kxg[r * n + t];  // stale at the last stage of a step: not used after it
+      kv[r] = kvg[r * n + t];
+    }
+    if (!(ent & kSettleOnly)) {
+      double xe[3] = {xeg[t], xeg[n + t], xeg[2 * n + t]};
+      track_slow<G, double, CLIP>(a.m, a.k, e, x, xe, v, kx, kv, hits, st, c.tc);
+    }
+    if (!(st & PT_ST_FROZEN)) {
+      double xi[3];
+      int cr = 0, j64 = 0;
+      const int rc = settle64<G>(a.m, a.k, e, x, xi, false, j64, cr);
+      c.it64 += j64;
+      c.tc.cross += cr;
+      if (rc) st |= rc == 1 ? PT_ST_NEWTON_FAIL : PT_ST_LOST;
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      a.x[r * n + t] = x[r];
+      vg[r * n + t] = v[r];
+      if (s < 4) {
+        kxg[r * n + t] = kx[r];
+        kvg[r * n + t] = kv[r];
+      }
+    }
+    a.e[t] = e;
+    a.hits[t] = hits;
+    a.st[t] = st;
+    if (s == 4 && !(st & PT_ST_FROZEN)) ++c.steps;
+  }
+  stage_counters(a, c);
+}
+
+// ---------------------------------------------------------------------------
+// the caller's arrays <-> the sorted state
+// ---------------------------------------------------------------------------
+
+// sorted[t] = caller[perm[t]]; an owner out of range freezes a live particle
+// (PT_ST_LOST), as in the resident push
+template <bool F64>
+__global__ void __launch_bounds__(256) k_gather(const __grid_constant__ StageArgs a,
+                                                const DevParticles p, const int* __restrict__ perm) {
+  using R = typename RealOf<F64>::type;
+  const int64_t n = a.n;
+  const R* vc = reinterpret_cast<const R*>(p.v);
+  const R* dc = reinterpret_cast<const R*>(p.d);
+  R* vs = reinterpret_cast<R*>(a.v);
+  R* ds = reinterpret_cast<R*>(const_cast<void*>(a.d));
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ip = perm[t];
+    unsigned st = p.status[ip];
+    const int e = p.elem[ip];
+    const bool valid = e >= 0 && e < a.m.nelem;
+    if (!valid && !(st & PT_ST_FROZEN)) st |= PT_ST_LOST;
+    const double* ce = a.m.ce + 3 * (size_t)(valid ? e : 0);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const double xr = p.x[r * n + ip];
+      if constexpr (F64) {
+        a.x[r * n + t] = xr;
+      } else {
+        const df o = df_from_double(valid ? xr - __ldg(ce + r) : 0.0);
+        a.xh[r * n + t] = o.hi;
+        a.xl[r * n + t] = o.lo;
+      }
+      vs[r * n + t] = vc[r * n + ip];
+    }
+    ds[t] = dc[ip];
+    a.e[t] = e;
+    a.hits[t] = p.hits[ip];
+    a.st[t] = st;
+  }
+}
+
+// caller[perm[t]] = sorted[t] for every particle that was not frozen on entry
+// (a particle whose owner was out of range keeps its position and velocity)
+template <bool F64>
+__global__ void __launch_bounds__(256) k_scatter_back(const __grid_constant__ StageArgs a,
+                                                      DevParticles p, const int* __restrict__ perm) {
+  using R = typename RealOf<F64>::type;
+  const int64_t n = a.n;
+  R* vc = reinterpret_cast<R*>(p.v);
+  const R* vs = reinterpret_cast<const R*>(a.v);
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ip = perm[t];
+    if (p.status[ip] & PT_ST_FROZEN) continue;
+    const int e = a.e[t];
+    p.status[ip] = a.st[t];
+    if (e < 0 || e >= a.m.nelem) continue;
+    const double* ce = a.m.ce + 3 * (size_t)e;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      if constexpr (F64)
+        p.x[r * n + ip] = a.x[r * n + t];
+      else
+        p.x[r * n + ip] = __ldg(ce + r) + df_to_double(df{a.xh[r * n + t], a.xl[r * n + t]});
+      vc[r * n + ip] = vs[r * n + t];
+    }
+    p.elem[ip] = e;
+    p.hits[ip] = a.hits[t];
+  }
+}
+
+}  // namespace pt

@@ -24,6 +24,7 @@ STOKES, SCHILLER_NAUMANN = 0, 1
 GUESS_TRILINEAR, GUESS_MLP = 0, 1
 DEPOSIT_ATOMIC, DEPOSIT_SEGMENTED, DEPOSIT_NEAREST = 0, 1, 2
 TRACK_PHYSICAL, TRACK_REFERENCE = 0, 1
+SCHEDULE_AUTO, SCHEDULE_RESIDENT, SCHEDULE_STAGED = 0, 1, 2
 
 _vp = ctypes.c_void_p
 
@@ -39,7 +40,7 @@ class Config(ctypes.Structure):
                 ("block", ctypes.c_int32), ("lift", ctypes.c_int32),
                 ("sphericity", ctypes.c_double), ("track", ctypes.c_int32),
                 ("buoyancy", ctypes.c_int32), ("curved_faces", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("schedule", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class MeshDesc(ctypes.Structure):

@@ -81,7 +81,7 @@ def _xi_max(orc_obj, params, e, x):
     return float(np.max(np.abs(xi))) if ok else math.inf
 
 
-def compare(gpu, orc, tol, xscale=1.0, vscale=1.0, min_checked=0.95, wall_tol=2e-3):
+def compare(gpu, orc, tol, xscale=1.0, vscale=1.0, min_checked=0.95, wall_tol=1e-4):
     """Particle-by-particle parity of a GPU push with the oracle.
 
     Strict set: every particle that is frozen on neither side, met the

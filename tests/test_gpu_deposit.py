@@ -134,6 +134,8 @@ def test_segmented_with_large_segments_matches_oracle_and_is_reproducible(mode):
     """8 elements holding ~5000 particles each: every segment is longer than
     the shared-memory sort, so the index order is made in global memory."""
     wl = W.tgv_box(2, 3, P=40_000, nsteps=1, seed=3, precision="fp32")
+    rng = np.random.default_rng(3)
+    wl.v = torch.as_tensor(rng.normal(size=(40_000, 3)) * 0.3)  # slip: non-zero energy source
     ctx = H.gpu_context(wl, "fp32")
     parts = H.gpu_particles(wl, ctx)
     counts = np.bincount(H.np64(wl.elem).astype(np.int64), minlength=8)
