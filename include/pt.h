@@ -358,6 +358,17 @@ pt_status pt_mlp_features(pt_ctx* ctx, int64_t n, const double* x_dev, const int
 int32_t pt_mlp_nparams(void);
 pt_status pt_mlp_set(pt_ctx* ctx, const float* theta_host, const float* norm_host);
 pt_status pt_mlp_get(pt_ctx* ctx, float* theta_host, float* norm_host);
+/* The learned Newton start of x_dev double [3][n] in elem_dev int32 [n]:
+ * guess_dev float [3][n] receives xi_tri + the network's correction, as the
+ * push uses it (an owner out of range leaves its column unchanged).  engine 1:
+ * the tensor-core form of the staged schedule (tcgen05, 128 particles per
+ * CTA, accumulators in tensor memory); 0: the warp-level mma.sync form of the
+ * resident schedule.  Needs ngeo = 3, PT_FP32 and a trained or set network
+ * (PT_ERR_STATE otherwise); PT_ERR_TIMEOUT if a tensor-core wait gave up.
+ * Synchronises. */
+pt_status pt_mlp_start(pt_ctx* ctx, int64_t n, const double* x_dev, const int32_t* elem_dev,
+                       float* guess_dev, int32_t engine);
+
 /* FP32 forward pass and loss gradient of the network on already-normalised
  * inputs (the kernels training uses): in_dev float [B][51], out_dev [B][3];
  * grad_dev float [11843] overwritten with d(mean squared error)/d theta for

@@ -904,6 +904,8 @@ static pt_status read_stats(pt_ctx* c, const pt_particles* p, double dt, pt_stat
   out->rep800 = (int64_t)h[PT_C_REP];
   out->dt_warn = (int64_t)h[PT_C_DTWARN];
   out->near_wall = (int64_t)h[PT_C_NEARWALL];
+  if (h[PT_C_TIMEOUT])
+    return fail(c, PT_ERR_TIMEOUT, "%llu tensor-core waits gave up", (unsigned long long)h[PT_C_TIMEOUT]);
   if (out->newton_fail) return fail(c, PT_ERR_NEWTON, "%lld particles failed the inverse map",
                                     (long long)out->newton_fail);
   if (out->lost) return fail(c, PT_ERR_LOST, "%lld particles lost", (long long)out->lost);
@@ -1009,7 +1011,7 @@ static pt_status push_staged(pt_ctx* c, const pt_particles* p, int32_t nsteps, d
   const int grid = grid_for(c, n, block, occ);
   const int gmove = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)c->nsm * 8));
   const int gtrack = c->nsm * 4;
-  const int gguess = (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, (int64_t)c->nsm * 8));
+  const int gguess = (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, (int64_t)c->nsm * 4));
   unsigned* const ctr = a.count;  // two list counters, used by alternate stages
   CK(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), c->stream));
   const int chunk = c->cfg.rebin_every > 0 ? c->cfg.rebin_every : 10;
@@ -1189,6 +1191,38 @@ pt_status pt_locate(pt_ctx* c, int64_t n, const double* x, const int32_t* elem, 
   int grid = (int)std::min<int64_t>((n + 127) / 128, (int64_t)c->nsm * 16);
   int rc = launch_locate(c->g, c->cfg.precision == PT_FP64, 0, a, grid, 128, c->stream);
   if (rc) return fail(c, PT_ERR_CUDA, "locate launch: %s", cudaGetErrorString((cudaError_t)rc));
+  return PT_OK;
+}
+
+pt_status pt_mlp_start(pt_ctx* c, int64_t n, const double* x, const int32_t* elem, float* guess,
+                       int32_t engine) {
+  if (!c) return fail(nullptr, PT_ERR_ARG, "ctx is NULL");
+  if (n < 0 || (n > 0 && (!x || !elem || !guess))) return fail(c, PT_ERR_ARG, "bad arrays");
+  if (engine != 0 && engine != 1) return fail(c, PT_ERR_ARG, "engine must be 0 or 1");
+  if (c->g != 4 || !c->mlp_ready || c->cfg.precision != PT_FP32)
+    return fail(c, PT_ERR_STATE, "learned start needs ngeo = 3, PT_FP32 and a trained network");
+  if (n == 0) return PT_OK;
+  StageArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.m = dev_mesh(c);
+  fill_consts(c, a.k);
+  a.mlp = pt_dev_mlp(c);
+  a.n = n;
+  a.x = const_cast<double*>(x);
+  a.e = const_cast<int*>(elem);
+  a.st = nullptr;
+  a.guess = guess;
+  a.stats = c->d_stats;
+  CK(cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * PT_C_COUNT, c->stream));
+  const DevParticles dp = {0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, (int64_t)c->nsm * 4));
+  const int rc = launch_staged(c->g, false, c->N + 1, engine ? PT_SOP_GUESS_X_TC : PT_SOP_GUESS_X_WARP,
+                               a, dp, nullptr, grid, 128, c->stream);
+  if (rc) return fail(c, PT_ERR_CUDA, "learned start launch: %s", cudaGetErrorString((cudaError_t)rc));
+  unsigned long long h[PT_C_COUNT];
+  CK(cudaMemcpyAsync(h, c->d_stats, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (h[PT_C_TIMEOUT]) return fail(c, PT_ERR_TIMEOUT, "tensor-core wait gave up");
   return PT_OK;
 }
 

@@ -24,6 +24,7 @@ __host__ __device__ __forceinline__ int finfo_nf(int info) { return (info >> 5) 
 enum {
   PT_C_STEPS = 0, PT_C_CROSS, PT_C_HITS, PT_C_IT32, PT_C_IT64, PT_C_SLOW,
   PT_C_NEAR, PT_C_NFAIL, PT_C_LOST, PT_C_CCAP, PT_C_OPEN, PT_C_REP, PT_C_DTWARN, PT_C_NEARWALL,
+  PT_C_TIMEOUT,
   PT_C_COUNT = 16
 };
 
@@ -197,7 +198,10 @@ int launch_deposit(int g, bool fp64, int np, int mode, const DepositArgs& a, int
 int max_active_push(int g, bool fp64, int np, int block);
 int launch_terms(int g, bool fp64, int np, const TermsArgs& a, int grid, int block, void* stream);
 // staged schedule: op 0 gather, 1 stage, 2 track, 3 learned start, 4 scatter back
-enum { PT_SOP_GATHER = 0, PT_SOP_STAGE = 1, PT_SOP_TRACK = 2, PT_SOP_GUESS = 3, PT_SOP_SCATTER = 4 };
+// (5, 6: the learned start of global positions a.x, tensor-core and warp-MMA
+// forms, for pt_mlp_start)
+enum { PT_SOP_GATHER = 0, PT_SOP_STAGE = 1, PT_SOP_TRACK = 2, PT_SOP_GUESS = 3, PT_SOP_SCATTER = 4,
+       PT_SOP_GUESS_X_TC = 5, PT_SOP_GUESS_X_WARP = 6 };
 int launch_staged(int g, bool fp64, int np, int op, const StageArgs& a, const DevParticles& p,
                   const int* perm, int grid, int block, void* stream);
 int max_active_stage(int g, bool fp64, int np, int block);

@@ -13,6 +13,11 @@
 #define PT_PUSH_MINB 2
 #endif
 #define PT_PUSH_MINB_F64 2
+// 1: the staged schedule evaluates the learned start on the tensor cores
+// (tcgen05, k_guess_tc); 0: with the warp-level mma.sync form (k_guess_mlp)
+#ifndef PT_MLP_TC
+#define PT_MLP_TC 1
+#endif
 
 namespace pt {
 
@@ -1382,8 +1387,28 @@ struct Family {
         }
         break;
       case PT_SOP_GUESS:
+      case PT_SOP_GUESS_X_TC:
+      case PT_SOP_GUESS_X_WARP:
         if constexpr (kMlp) {
-          k_guess_mlp<G><<<grid, block, 0, s>>>(a);
+          const bool tc = op == PT_SOP_GUESS_X_TC || (op == PT_SOP_GUESS && PT_MLP_TC);
+          if (tc) {
+            static bool attr = false;  // dynamic shared memory above 48 KB, set once
+            if (!attr) {
+              cudaFuncSetAttribute(k_guess_tc<G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   kMlpTcSmem);
+              cudaFuncSetAttribute(k_guess_tc<G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   kMlpTcSmem);
+              attr = true;
+            }
+            if (op == PT_SOP_GUESS)
+              k_guess_tc<G, false><<<grid, 128, kMlpTcSmem, s>>>(a);
+            else
+              k_guess_tc<G, true><<<grid, 128, kMlpTcSmem, s>>>(a);
+          } else if (op == PT_SOP_GUESS) {
+            k_guess_mlp<G, false><<<grid, block, 0, s>>>(a);
+          } else {
+            k_guess_mlp<G, true><<<grid, block, 0, s>>>(a);
+          }
           break;
         } else {
           return (int)cudaErrorInvalidValue;

@@ -22,6 +22,7 @@
 // arithmetic step is the resident push's own device code, in the same order.
 #pragma once
 #include "pt_kernels.cuh"
+#include "pt_mlp_tc.cuh"
 
 #ifndef PT_STAGE_MINB
 #define PT_STAGE_MINB 3
@@ -252,9 +253,26 @@ __global__ void __launch_bounds__(128) k_track_f32(const __grid_constant__ Stage
   stage_counters(a, c);
 }
 
-// Learned start of every live particle at the current position (the network
-// is warp-collective: every lane takes part, dead lanes with live = false).
-template <int G>
+// Position of particle t relative to its owner's centre, in FP32: from the
+// sorted state (the high part of the double-float offset), or (FROM_X) from
+// global FP64 positions a.x.
+template <bool FROM_X>
+__device__ __forceinline__ void start_pos(const StageArgs& a, int64_t t, int e, float* xf) {
+  const int64_t n = a.n;
+  if constexpr (FROM_X) {
+    const double* ce = a.m.ce + 3 * (size_t)e;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) xf[r] = (float)(a.x[r * n + t] - __ldg(ce + r));
+  } else {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) xf[r] = a.xh[r * n + t];
+  }
+}
+
+// Learned start of every live particle at the current position, warp-level
+// mma.sync form (the network is warp-collective: every lane takes part, dead
+// lanes with live = false).
+template <int G, bool FROM_X>
 __global__ void __launch_bounds__(128) k_guess_mlp(const __grid_constant__ StageArgs a) {
   PT_MLP_PROLOGUE(true, a.mlp);
   const int64_t n = a.n;
@@ -262,20 +280,77 @@ __global__ void __launch_bounds__(128) k_guess_mlp(const __grid_constant__ Stage
   const int64_t nround = (n + stride - 1) / stride * stride;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nround; t += stride) {
     const bool inr = t < n;
-    const unsigned st = inr ? a.st[t] : (unsigned)PT_ST_FROZEN;
-    const bool live = !(st & PT_ST_FROZEN);
-    const int e = live ? a.e[t] : 0;
+    // (a.st is null for pt_mlp_start: every particle with an owner in range)
+    const unsigned st = inr ? (a.st ? a.st[t] : 0u) : (unsigned)PT_ST_FROZEN;
+    const int e0 = inr ? a.e[t] : 0;
+    const bool live = !(st & PT_ST_FROZEN) && e0 >= 0 && e0 < a.m.nelem;
+    const int e = live ? e0 : 0;
     float xf[3] = {0.f, 0.f, 0.f};
-    if (live) {
-#pragma unroll
-      for (int r = 0; r < 3; ++r) xf[r] = a.xh[r * n + t];
-    }
+    if (live) start_pos<FROM_X>(a, t, e, xf);
     float guess[3];
     start_guess_local<G, true>(a.m, a.k, sm, &a.mlp, e, xf, live, guess);
     if (live) {
 #pragma unroll
       for (int r = 0; r < 3; ++r) a.guess[r * n + t] = guess[r];
     }
+  }
+}
+
+// Learned start of every live particle on the tensor cores (tcgen05): one
+// tile of 128 particles at a time per CTA, weights in shared memory,
+// accumulators in 128 columns of tensor memory.  An MMA that does not complete
+// within the wait limit counts in PT_C_TIMEOUT and ends the CTA's work.
+template <int G, bool FROM_X>
+__global__ void __launch_bounds__(128, 1) k_guess_tc(const __grid_constant__ StageArgs a) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  MlpTcSmem& s = *reinterpret_cast<MlpTcSmem*>(dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u));
+  const int tid = threadIdx.x;
+  mlp_tc_load(s, a.mlp);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&s.mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (tid < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(&s.tmem)),
+                 "r"(kMlpTcCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s.tmem;
+  uint32_t phase = 0u;
+  const int64_t n = a.n;
+  for (int64_t base = (int64_t)blockIdx.x * 128; base < n; base += (int64_t)gridDim.x * 128) {
+    const int64_t t = base + tid;
+    const bool inr = t < n;
+    // (a.st is null for pt_mlp_start: every particle with an owner in range)
+    const unsigned st = inr ? (a.st ? a.st[t] : 0u) : (unsigned)PT_ST_FROZEN;
+    const int e0 = inr ? a.e[t] : 0;
+    const bool live = !(st & PT_ST_FROZEN) && e0 >= 0 && e0 < a.m.nelem;
+    const int e = live ? e0 : 0;
+    float xf[3] = {0.f, 0.f, 0.f}, xi_tri[3], guess[3];
+    if (live) start_pos<FROM_X>(a, t, e, xf);
+    trilinear_guess(a.m, e, xf, xi_tri);
+    if (!mlp_tc_tile(s, a.mlp, a.m, tmem, e, xi_tri, guess, phase)) {
+      if (tid == 0) atomicAdd(a.stats + PT_C_TIMEOUT, 1ull);
+      break;
+    }
+    if (live) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) a.guess[r * n + t] = guess[r];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid < 32) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(kMlpTcCols)
+                 : "memory");
   }
 }
 

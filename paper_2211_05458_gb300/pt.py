@@ -74,7 +74,7 @@ EXPORTS = ["pt_config_default", "pt_init_mesh", "pt_set_config", "pt_set_fluid",
            "pt_mlp_features", "pt_mlp_nparams", "pt_mlp_set", "pt_mlp_get", "pt_mlp_forward",
            "pt_mlp_grad", "pt_push_batch", "pt_profile", "pt_profile_read", "pt_destroy",
            "pt_last_error", "pt_deposit_noalloc", "pt_find_element", "pt_stage_terms",
-           "pt_launch_count", "pt_measure_peak"]
+           "pt_launch_count", "pt_measure_peak", "pt_mlp_start"]
 
 
 def library_path() -> str:
@@ -124,6 +124,7 @@ def lib():
             L.pt_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int64)]
             L.pt_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+            L.pt_mlp_start.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_int32]
             L.pt_measure_peak.argtypes = [ctypes.c_int32, _vp, ctypes.POINTER(ctypes.c_double)]
             L.pt_destroy.argtypes = [_vp]
             L.pt_last_error.argtypes = [_vp]
@@ -344,6 +345,14 @@ class Context:
         self._check(lib().pt_mlp_train(self.h, inp.shape[0], _ptr(inp), _ptr(tgt), epochs, batch,
                                        ctypes.c_float(lr), seed, loss))
         return list(loss)[:epochs]
+
+    def mlp_start(self, x, elem, engine: int = 1):
+        """Learned Newton start of x [3][n] float64 cuda in elem [n] int32:
+        guess [3][n] float32 (engine 1 tensor cores, 0 warp mma.sync)."""
+        n = x.shape[1]
+        g = torch.zeros((3, n), dtype=torch.float32, device=x.device)
+        self._check(lib().pt_mlp_start(self.h, n, _ptr(x), _ptr(elem), _ptr(g), int(engine)))
+        return g
 
     def mlp_features(self, x, elem):
         n = x.shape[1]

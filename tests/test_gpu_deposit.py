@@ -149,5 +149,8 @@ def test_segmented_with_large_segments_matches_oracle_and_is_reproducible(mode):
     So = orc.deposit_nearest(*args) if mode & pt.DEPOSIT_NEAREST else orc.deposit(*args)
     S = a.double().cpu().numpy()
     assert np.max(np.abs(S - So)) <= 1e-5 * np.abs(So).max()
+    # per-element sums of ~5000 sources that largely cancel: relative to the
+    # sum of the nodal magnitudes (the sum's condition)
     es, eo = S.sum(axis=2), So.sum(axis=2)
-    assert np.max(np.abs(es - eo) / np.abs(eo).max(axis=0, keepdims=True)) < 1e-5
+    cond = np.abs(So).sum(axis=2).max(axis=0, keepdims=True)
+    assert np.max(np.abs(es - eo) / cond) < 1e-5

@@ -109,3 +109,34 @@ def test_push_with_learned_start_matches_oracle():
     o = H.run_oracle(wl, band_ref=2e-4, band_x=1e-4 * h)
     res = H.compare(g, o, 2e-5)
     assert res["checked"] > 300 and st["crossings"] > 50
+
+
+@pytest.mark.parametrize("engine", [1, 0])
+def test_learned_start_inference_matches_oracle_network(engine):
+    """The push-side BF16 network (engine 1: tcgen05 tensor-core kernel of the
+    staged schedule; 0: warp-level mma.sync of the resident one) against the
+    FP64 oracle network on the same weights: the start xi_tri + correction,
+    on a strongly curved mesh where the correction is large, for a particle
+    count that is not a multiple of the 128-particle tile."""
+    wl = W.curved_channel((8, 8, 8), 3, 4, P=100, nsteps=1, dt=2e-3)
+    wl.mesh = W.channel_mesh((8, 8, 8), 3, amp=0.25)
+    ctx = H.gpu_context(wl, "fp32")
+    inp, tgt = ctx.mlp_make_pairs(100_000, seed=5)
+    ctx.mlp_train(inp, tgt, epochs=4, batch=1024, lr=3e-3, seed=3)
+    theta, norm = ctx.mlp_get()
+    x, el = W.seed_particles(wl.mesh, 4001, seed=78, margin=0.0)
+    xd, ed = x.T.contiguous().cuda(), el.cuda()
+    g = ctx.mlp_start(xd, ed, engine).T.double().cpu().numpy()
+    orc = oracle.Oracle(wl.mesh.as_dict())
+    th = theta.double().numpy()
+    nm = norm.double().numpy()
+    mean, sd, osc = nm[:51], nm[51:102], nm[102:]
+    feats = np.array([orc.mlp_features(int(el[i]), H.np64(x[i])) for i in range(len(el))])
+    out = oracle.mlp_forward(th, (feats - mean) / sd) * osc
+    ref = feats[:, :3] + out
+    scale = np.sqrt(np.mean(out ** 2))
+    err = np.abs(g - ref)
+    print("engine", engine, "correction rms", scale, "max err", err.max(), "mean", err.mean())
+    assert scale > 1e-4
+    # BF16 operands through four layers (~3 significant digits per product)
+    assert err.max() <= 0.05 * scale and err.mean() <= 0.01 * scale
