@@ -49,8 +49,9 @@ def parse():
     ap.add_argument("--schedule", default="auto", choices=["auto", "resident", "staged"],
                     help="pt_push kernel schedule (results do not depend on it)")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / fp64 / cpu legs")
-    ap.add_argument("--extras", default="trilinear,reference,e2e,fp64,cpu",
-                    help="comma list of extra legs to run (trilinear, reference, e2e, fp64, cpu)")
+    ap.add_argument("--extras", default="trilinear,reference,coupled,e2e,fp64,cpu",
+                    help="comma list of extra legs to run (trilinear, reference, coupled, e2e, "
+                         "fp64, cpu)")
     ap.add_argument("--config", default="c3", choices=["c1", "c2", "c3", "c4", "c5"],
                     help="c3 (default): the learned-start 64^3 channel; c1: 8^3 TGV box FP64; "
                          "c2: 32^3 NGeo=2 channel FP64; c4: 128 batched boxes FP32; "
@@ -642,6 +643,24 @@ def main():
                 "note": "same FP32 push, owners found by inverse map + face walk (walls traced)"}
             ctx.set_config(track=pt.TRACK_PHYSICAL)
             del pref, pphy
+    if not args.no_extras and rank == 0 and "coupled" in legs:
+        # a coupled solver that updates the fluid state every time step calls
+        # pt_push with nsteps = 1: binning, sorted copy and copy back per step
+        pc = pt.ParticleSet.create(wl.x, wl.v, wl.d, wl.elem, pt.FP32, dev)
+        ctx.push(pc, 1, wl.dt, stats=False)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            ctx.push(pc, 1, wl.dt, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        line["coupled_one_step_calls"] = {
+            "value": P * 10 / (e0.elapsed_time(e1) / 1e3), "unit": METRIC,
+            "note": "same push, pt_push(nsteps = 1) per time step (fluid state updated by the "
+                    "caller between calls); the default run uses 10 steps per call"}
+        del pc
     if not args.no_extras and rank == 0 and "e2e" in legs:
         # e2e: same metric through pt_push_host with pinned host buffers
         hp = parts.to("cpu", pin=True)

@@ -204,6 +204,20 @@ typedef struct {
   int64_t reserved[2];
 } pt_stats;
 
+/* Histograms of the last pt_push (host struct), kept by the staged schedule
+ * (all zero after a push with the resident one):
+ *   newton_fp32[k]  particle-stages whose inverse map took k FP32 Newton
+ *                   iterations (k = 0..6; [7]: 7 or more)
+ *   newton_final[k] the same for the final iterations (double-float residuals
+ *                   in PT_FP32 mode; every FP64 iteration in PT_FP64 mode)
+ *   crossings[k]    exactly tracked stage segments with k face crossings
+ *                   (k = 0..2; [3]: 3 or more)                             */
+typedef struct {
+  int64_t newton_fp32[8];
+  int64_t newton_final[8];
+  int64_t crossings[4];
+} pt_histograms;
+
 /* Fills *cfg with the defaults listed in pt_config. */
 void pt_config_default(pt_config* cfg);
 
@@ -391,6 +405,9 @@ pt_status pt_push_batch(pt_ctx* const* ctxs, const pt_particles* parts, int32_t 
  * record.  pt_profile(ctx, 0) stops recording. */
 pt_status pt_profile(pt_ctx* ctx, int32_t enable);
 pt_status pt_profile_read(pt_ctx* ctx, double* kernel_ms, int64_t* launches);
+
+/* Reads the histograms of the last pt_push into *out (synchronises). */
+pt_status pt_read_histograms(pt_ctx* ctx, pt_histograms* out);
 
 /* Kernel launches this context queued (every kernel of every call) since the
  * last pt_launch_count; *n receives the count, which is then cleared. */

@@ -1470,6 +1470,19 @@ pt_status pt_profile_read(pt_ctx* c, double* ms, int64_t* launches) {
   return PT_OK;
 }
 
+pt_status pt_read_histograms(pt_ctx* c, pt_histograms* out) {
+  if (!c || !out) return fail(c, PT_ERR_ARG, "NULL argument");
+  unsigned long long h[PT_C_COUNT];
+  CK(cudaMemcpyAsync(h, c->d_stats, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < 8; ++k) {
+    out->newton_fp32[k] = (int64_t)h[PT_C_H32 + k];
+    out->newton_final[k] = (int64_t)h[PT_C_H64 + k];
+  }
+  for (int k = 0; k < 4; ++k) out->crossings[k] = (int64_t)h[PT_C_HCR + k];
+  return PT_OK;
+}
+
 pt_status pt_launch_count(pt_ctx* c, int64_t* n) {
   if (!c || !n) return fail(c, PT_ERR_ARG, "NULL argument");
   *n = c->launches;

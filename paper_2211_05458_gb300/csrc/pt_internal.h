@@ -25,7 +25,11 @@ enum {
   PT_C_STEPS = 0, PT_C_CROSS, PT_C_HITS, PT_C_IT32, PT_C_IT64, PT_C_SLOW,
   PT_C_NEAR, PT_C_NFAIL, PT_C_LOST, PT_C_CCAP, PT_C_OPEN, PT_C_REP, PT_C_DTWARN, PT_C_NEARWALL,
   PT_C_TIMEOUT,
-  PT_C_COUNT = 16
+  // histograms of the staged schedule: particle-stages by FP32 Newton
+  // iterations (0..6, 7+), by final iterations (0..6, 7+), exactly tracked
+  // segments by crossings (0, 1, 2, 3+)
+  PT_C_H32 = 16, PT_C_H64 = 24, PT_C_HCR = 32,
+  PT_C_COUNT = 40
 };
 
 #define PT_ST_FROZEN (PT_ST_NEWTON_FAIL | PT_ST_LOST | PT_ST_CROSS_CAP | PT_ST_OPEN)

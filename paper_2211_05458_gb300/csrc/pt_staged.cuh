@@ -27,6 +27,13 @@
 #ifndef PT_STAGE_MINB
 #define PT_STAGE_MINB 3
 #endif
+// 1: k_stage_f32 stages the nodal state (rho, rho u) of each element its tile
+// of 128 sorted particles needs in shared memory, one bulk copy per element
+// (cp.async.bulk, completion on an mbarrier), and interpolates from there;
+// 0: interpolation reads the state through L1
+#ifndef PT_STAGE_U
+#define PT_STAGE_U 0
+#endif
 
 namespace pt {
 
@@ -47,6 +54,20 @@ __device__ __forceinline__ void list_append(const StageArgs& a, int64_t t, unsig
   if (want) a.list[base + __popc(m & ((1u << lane) - 1u))] = (unsigned)t | (want == 2u ? kSettleOnly : 0u);
 }
 
+// Per-thread histogram of small counts: four 16-bit bins per word (a thread
+// sees far fewer than 65536 particles per launch).
+struct Hist8 {
+  unsigned long long w[2] = {0ull, 0ull};
+  __device__ __forceinline__ void add(int v) {
+    const int b = v < 7 ? (v > 0 ? v : 0) : 7;
+    w[b >> 2] += 1ull << (16 * (b & 3));
+  }
+  __device__ __forceinline__ void flush(unsigned long long* stats, int slot, int nbins) const {
+    for (int b = 0; b < nbins; ++b)
+      count_add(stats, slot + b, (w[b >> 2] >> (16 * (b & 3))) & 0xFFFFull);
+  }
+};
+
 __device__ __forceinline__ void stage_counters(const StageArgs& a, const PushCounters& c) {
   count_add(a.stats, PT_C_STEPS, c.steps);
   count_add(a.stats, PT_C_IT32, c.it32);
@@ -62,9 +83,40 @@ __device__ __forceinline__ void stage_counters(const StageArgs& a, const PushCou
 
 // Returns 0 (stage end committed), 1 (listed for exact tracking) or 2 (listed
 // for the walk only).
+// interp4 from a shared-memory copy of the element's first four variables
+template <int NP>
+__device__ __forceinline__ void interp4_sh(const float* Ue, const float* l1, const float* l2,
+                                           const float* l3, float* out) {
+  constexpr int N3 = NP * NP * NP;
+#pragma unroll 1
+  for (int v = 0; v < 4; ++v) {
+    const float* Uv = Ue + v * N3;
+    float acc = 0.f;
+#pragma unroll 1
+    for (int kk = 0; kk < NP; ++kk) {
+      float t2 = 0.f;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        const float* row = Uv + NP * (j + NP * kk);
+        float t1 = 0.f;
+#pragma unroll
+        for (int i = 0; i < NP; i += 2) {
+          const float2 q = *reinterpret_cast<const float2*>(row + i);
+          t1 = fmaf(q.x, l1[i], t1);
+          t1 = fmaf(q.y, l1[i + 1], t1);
+        }
+        t2 = fmaf(t1, l2[j], t2);
+      }
+      acc = fmaf(t2, l3[kk], acc);
+    }
+    out[v] = acc;
+  }
+}
+
 template <int G, int NP, bool MLP>
 __device__ __forceinline__ unsigned stage_one_f32(const StageArgs& a, int64_t t,
-                                                  PushCounters& c) {
+                                                  PushCounters& c, Hist8& h32, Hist8& h64,
+                                                  const float* Us = nullptr) {
   constexpr int N3 = NP * NP * NP;
   const int64_t n = a.n;
   const int s = a.stage;
@@ -101,6 +153,8 @@ __device__ __forceinline__ unsigned stage_one_f32(const StageArgs& a, int64_t t,
   const bool ok = newton_df<G>(a.m, a.k, e, xd, guess, zd, i32, i64);
   c.it32 += i32;
   c.it64 += i64;
+  h32.add(i32);
+  h64.add(i64);
   if (!ok) {
     a.st[t] = st | PT_ST_NEWTON_FAIL;
     return 0u;
@@ -122,7 +176,10 @@ __device__ __forceinline__ unsigned stage_one_f32(const StageArgs& a, int64_t t,
   lagr<NP, float>(xi[0], a.k.sn32, a.k.sw32, l1);
   lagr<NP, float>(xi[1], a.k.sn32, a.k.sw32, l2);
   lagr<NP, float>(xi[2], a.k.sn32, a.k.sw32, l3);
-  interp4<NP, float>(Ue, l1, l2, l3, Uv);
+  if (Us)
+    interp4_sh<NP>(Us, l1, l2, l3, Uv);
+  else
+    interp4<NP, float>(Ue, l1, l2, l3, Uv);
   particle_accel_f32<G, NP>(a.m, a.k, Ue, e, zd, Uv, v, d, tau, st, acc);
   const float As = a.k.A32[s], Bs = a.k.B32[s], dt = (float)a.dt;
   df xe[3];
@@ -167,18 +224,92 @@ __device__ __forceinline__ unsigned stage_one_f32(const StageArgs& a, int64_t t,
   return list;
 }
 
+// shared-memory slots of the element staging (at most 40 KB per block)
+template <int NP>
+struct UStage {
+  static constexpr int bytes = 16 * NP * NP * NP;  // rho, rho u1..u3 of one element
+  static constexpr int slots = (40960 / bytes) < 8 ? (40960 / bytes) : 8;
+  // a bulk copy needs 16-byte aligned element blocks: 20 NP^3 bytes apart
+  static constexpr bool ok = PT_STAGE_U && (NP % 2 == 0);
+};
+
 template <int G, int NP, bool MLP>
 __global__ void __launch_bounds__(128, PT_STAGE_MINB) k_stage_f32(const __grid_constant__ StageArgs a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.count_next = 0u;
   PushCounters c = {0, 0, 0, {0, 0, 0}};
+  Hist8 h32, h64;
   const int64_t n = a.n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t nround = (n + stride - 1) / stride * stride;  // uniform trip count per warp
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nround; t += stride) {
-    const unsigned want = t < n ? stage_one_f32<G, NP, MLP>(a, t, c) : 0u;
-    list_append(a, t, want);
+  if constexpr (!UStage<NP>::ok) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nround; t += stride) {
+      const unsigned want = t < n ? stage_one_f32<G, NP, MLP>(a, t, c, h32, h64) : 0u;
+      list_append(a, t, want);
+    }
+  } else {
+    // Per tile of 128 consecutive sorted particles: every run of equal owners
+    // gets a slot (the first UStage::slots runs), filled by one bulk copy of
+    // that element's rho, rho u; the tile's particles interpolate from the
+    // slot (from global memory beyond the slots).
+    constexpr int N3 = NP * NP * NP;
+    constexpr int SL = UStage<NP>::slots;
+    __shared__ __align__(128) float sU[SL][4 * N3];
+    __shared__ int se[128];
+    __shared__ int wcnt[4];
+    __shared__ unsigned long long mbar;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const uint32_t mb = smem_u32(&mbar);
+    if (tid == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t phase = 0u;
+    const float* Ug = reinterpret_cast<const float*>(a.U);
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + tid; t < nround; t += stride) {
+      const bool inr = t < n;
+      const unsigned st0 = inr ? a.st[t] : (unsigned)PT_ST_FROZEN;
+      const int e0 = (inr && !(st0 & PT_ST_FROZEN)) ? a.e[t] : -1;
+      fence_async_smem();  // this thread's reads of the previous tile's slots come first
+      se[tid] = e0;
+      __syncthreads();
+      const bool start = e0 >= 0 && (tid == 0 || se[tid - 1] != e0);
+      const unsigned bm = __ballot_sync(0xffffffffu, start);
+      if (lane == 0) wcnt[w] = __popc(bm);
+      __syncthreads();
+      int off = 0, total = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        off += j < w ? wcnt[j] : 0;
+        total += wcnt[j];
+      }
+      const int run = off + __popc(bm & ((2u << lane) - 1u)) - 1;  // run index of e0
+      const int nslot = total < SL ? total : SL;
+      if (tid == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mb),
+                     "r"(nslot * UStage<NP>::bytes)
+                     : "memory");
+      if (start && run < SL)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+            "[%3];\n" ::"r"(smem_u32(sU[run])),
+            "l"(Ug + (size_t)e0 * 5 * N3), "r"(UStage<NP>::bytes), "r"(mb)
+            : "memory");
+      const bool done = mbar_wait(mb, phase);
+      if (__syncthreads_or(!done)) {
+        if (!done) mbar_wait(mb, phase);
+        if (tid == 0) atomicAdd(a.stats + PT_C_TIMEOUT, 1ull);
+        break;
+      }
+      phase ^= 1u;
+      const float* Us = (e0 >= 0 && run < SL) ? sU[run] : nullptr;
+      const unsigned want = inr ? stage_one_f32<G, NP, MLP>(a, t, c, h32, h64, Us) : 0u;
+      list_append(a, t, want);
+    }
   }
   stage_counters(a, c);
+  h32.flush(a.stats, PT_C_H32, 8);
+  h64.flush(a.stats, PT_C_H64, 8);
 }
 
 // Exact tracking of the listed stage segments, then the walk that checks the
@@ -186,6 +317,7 @@ __global__ void __launch_bounds__(128, PT_STAGE_MINB) k_stage_f32(const __grid_c
 template <int G, bool CLIP>
 __global__ void __launch_bounds__(128) k_track_f32(const __grid_constant__ StageArgs a) {
   PushCounters c = {0, 0, 0, {0, 0, 0}};
+  Hist8 hcr;
   const int64_t n = a.n;
   const int s = a.stage;
   const unsigned cnt = *a.count;
@@ -220,7 +352,9 @@ __global__ void __launch_bounds__(128) k_track_f32(const __grid_constant__ Stage
         xs[r] = cr + df_to_double(xd[r]);
         xg[r] = cr + df_to_double(df{xeg[r * n + t], xeg[(3 + r) * n + t]});
       }
+      const int cr0 = c.tc.cross;
       track_slow<G, float, CLIP>(a.m, a.k, e, xs, xg, v, kx, kv, hits, st, c.tc);
+      hcr.add(c.tc.cross - cr0);
       const double* cn = a.m.ce + 3 * (size_t)e;
 #pragma unroll
       for (int r = 0; r < 3; ++r) xd[r] = df_from_double(xs[r] - __ldg(cn + r));
@@ -251,6 +385,7 @@ __global__ void __launch_bounds__(128) k_track_f32(const __grid_constant__ Stage
     if (s == 4 && !(st & PT_ST_FROZEN)) ++c.steps;
   }
   stage_counters(a, c);
+  hcr.flush(a.stats, PT_C_HCR, 4);
 }
 
 // Position of particle t relative to its owner's centre, in FP32: from the
@@ -360,7 +495,7 @@ __global__ void __launch_bounds__(128, 1) k_guess_tc(const __grid_constant__ Sta
 
 template <int G, int NP>
 __device__ __forceinline__ unsigned stage_one_f64(const StageArgs& a, int64_t t,
-                                                  PushCounters& c) {
+                                                  PushCounters& c, Hist8& h64) {
   constexpr int N3 = NP * NP * NP;
   const int64_t n = a.n;
   const int s = a.stage;
@@ -392,6 +527,7 @@ __device__ __forceinline__ unsigned stage_one_f64(const StageArgs& a, int64_t t,
   const bool ok = locate_local<G, true>(a.m, a.k, e, xl, guess, xi, i32, i64);
   c.it32 += i32;
   c.it64 += i64;
+  h64.add(i64);
   if (!ok) {
     a.st[t] = st | PT_ST_NEWTON_FAIL;
     return 0u;
@@ -451,19 +587,22 @@ template <int G, int NP>
 __global__ void __launch_bounds__(128, PT_PUSH_MINB_F64) k_stage_f64(const __grid_constant__ StageArgs a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.count_next = 0u;
   PushCounters c = {0, 0, 0, {0, 0, 0}};
+  Hist8 h64;
   const int64_t n = a.n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t nround = (n + stride - 1) / stride * stride;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nround; t += stride) {
-    const unsigned want = t < n ? stage_one_f64<G, NP>(a, t, c) : 0u;
+    const unsigned want = t < n ? stage_one_f64<G, NP>(a, t, c, h64) : 0u;
     list_append(a, t, want);
   }
   stage_counters(a, c);
+  h64.flush(a.stats, PT_C_H64, 8);
 }
 
 template <int G, bool CLIP>
 __global__ void __launch_bounds__(128) k_track_f64(const __grid_constant__ StageArgs a) {
   PushCounters c = {0, 0, 0, {0, 0, 0}};
+  Hist8 hcr;
   const int64_t n = a.n;
   const int s = a.stage;
   const unsigned cnt = *a.count;
@@ -489,7 +628,9 @@ __global__ void __launch_bounds__(128) k_track_f64(const __grid_constant__ Stage
     }
     if (!(ent & kSettleOnly)) {
       double xe[3] = {xeg[t], xeg[n + t], xeg[2 * n + t]};
+      const int cr0 = c.tc.cross;
       track_slow<G, double, CLIP>(a.m, a.k, e, x, xe, v, kx, kv, hits, st, c.tc);
+      hcr.add(c.tc.cross - cr0);
     }
     if (!(st & PT_ST_FROZEN)) {
       double xi[3];
@@ -514,6 +655,7 @@ __global__ void __launch_bounds__(128) k_track_f64(const __grid_constant__ Stage
     if (s == 4 && !(st & PT_ST_FROZEN)) ++c.steps;
   }
   stage_counters(a, c);
+  hcr.flush(a.stats, PT_C_HCR, 4);
 }
 
 // ---------------------------------------------------------------------------

@@ -59,6 +59,11 @@ STAT_FIELDS = ["particle_steps", "crossings", "wall_hits", "newton_it_fp32", "ne
                "dt_warn", "near_wall"]
 
 
+class Histograms(ctypes.Structure):
+    _fields_ = [("newton_fp32", ctypes.c_int64 * 8), ("newton_final", ctypes.c_int64 * 8),
+                ("crossings", ctypes.c_int64 * 4)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in STAT_FIELDS] + [("reserved", ctypes.c_int64 * 2)]
 
@@ -74,7 +79,7 @@ EXPORTS = ["pt_config_default", "pt_init_mesh", "pt_set_config", "pt_set_fluid",
            "pt_mlp_features", "pt_mlp_nparams", "pt_mlp_set", "pt_mlp_get", "pt_mlp_forward",
            "pt_mlp_grad", "pt_push_batch", "pt_profile", "pt_profile_read", "pt_destroy",
            "pt_last_error", "pt_deposit_noalloc", "pt_find_element", "pt_stage_terms",
-           "pt_launch_count", "pt_measure_peak", "pt_mlp_start"]
+           "pt_launch_count", "pt_measure_peak", "pt_mlp_start", "pt_read_histograms"]
 
 
 def library_path() -> str:
@@ -124,6 +129,7 @@ def lib():
             L.pt_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int64)]
             L.pt_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+            L.pt_read_histograms.argtypes = [_vp, ctypes.POINTER(Histograms)]
             L.pt_mlp_start.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_int32]
             L.pt_measure_peak.argtypes = [ctypes.c_int32, _vp, ctypes.POINTER(ctypes.c_double)]
             L.pt_destroy.argtypes = [_vp]
@@ -392,6 +398,13 @@ class Context:
         ms, k = ctypes.c_double(0.0), ctypes.c_int64(0)
         self._check(lib().pt_profile_read(self.h, ctypes.byref(ms), ctypes.byref(k)))
         return float(ms.value), int(k.value)
+
+    def histograms(self):
+        """Histograms of the last push (staged schedule): dict of lists."""
+        h = Histograms()
+        self._check(lib().pt_read_histograms(self.h, ctypes.byref(h)))
+        return {"newton_fp32": list(h.newton_fp32), "newton_final": list(h.newton_final),
+                "crossings": list(h.crossings)}
 
     def launch_count(self):
         """Kernel launches this context queued since the last call (then cleared)."""

@@ -134,3 +134,21 @@ def test_staged_empty_frozen_and_lost_on_entry():
         empty = pt.ParticleSet.create(np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0),
                                       np.zeros(0, np.int32), ctx.precision, "cuda")
         assert ctx.push(empty, 3, wl.dt)["particle_steps"] == 0
+
+
+def test_histograms_count_every_particle_stage():
+    wl = W.curved_channel((6, 6, 6), 3, 5, P=3000, nsteps=10, dt=2e-3, seed=6)
+    _speed_up(wl, 6)
+    h = 2.0 / 6
+    ctx = H.gpu_context(wl, "fp32", schedule=pt.SCHEDULE_STAGED, band_ref=2e-4, band_x=1e-4 * h)
+    parts = H.gpu_particles(wl, ctx)
+    st = ctx.push(parts, 10, wl.dt)
+    hist = ctx.histograms()
+    stages = 5 * st["particle_steps"]  # no particle froze
+    assert sum(hist["newton_fp32"]) == stages and sum(hist["newton_final"]) == stages
+    # the totals also hold the walk's inverse maps after a crossing
+    assert sum(k * c for k, c in enumerate(hist["newton_fp32"])) <= st["newton_it_fp32"]
+    assert sum(hist["crossings"]) == st["slow_track"]
+    assert sum(k * c for k, c in enumerate(hist["crossings"][:3])) + 3 * hist["crossings"][3] \
+        <= st["crossings"]
+    print("histograms", hist)

@@ -282,7 +282,8 @@ def test_ctypes_layouts_match_the_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     pairs = [("pt_config", pt.Config), ("pt_mesh_desc", pt.MeshDesc),
-             ("pt_particles", pt.CParticles), ("pt_stats", pt.Stats)]
+             ("pt_particles", pt.CParticles), ("pt_stats", pt.Stats),
+             ("pt_histograms", pt.Histograms)]
     lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "pt.h"', "int main(void) {"]
     for cname, cls in pairs:
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
