@@ -409,6 +409,8 @@ def run_config(args):
                          "peak_kind": peak_kind, "flops_per_particle_stage": flops,
                          "newton_iterations_per_stage": {"full": it64 if f64 else it32,
                                                          "residual_only": 0.0 if f64 else it64}}}
+    if cfg == "c4":
+        line["batch_tuning"] = pt.batch_tuning(ctxs[0])
     if dep_ev:
         dep_ms = sum(a.elapsed_time(b) for a, b in dep_ev) / len(dep_ev)
         Sbytes = S.numel() * 4

@@ -392,11 +392,22 @@ pt_status pt_mlp_grad(pt_ctx* ctx, int32_t B, const float* in_dev, const float* 
                       float* grad_dev, float* loss_host);
 
 /* Batched push: nbox independent contexts (PT_FP32, ngeo = 1, N in 3..7),
- * each with its own particles, advanced by one persistent launch per step
- * chunk; the sequence is captured once per (nbox, nsteps) in a CUDA graph on
- * ctxs[0]'s stream.  out: host array of nbox pt_stats or NULL (synchronises). */
+ * each with its own particles.  The boxes are grouped by N; per step chunk
+ * one binning of all particles, then one persistent launch per group with the
+ * kernel instantiated for that N, the groups' launches running concurrently.
+ * The first call tunes each group's block size (64, 96 or 128 threads, timed
+ * on successive chunks); later calls replay the sequence captured once per
+ * (nsteps, dt) in a CUDA graph on ctxs[0]'s stream.  out: host array of nbox
+ * pt_stats or NULL (synchronises). */
 pt_status pt_push_batch(pt_ctx* const* ctxs, const pt_particles* parts, int32_t nbox,
                         int32_t nsteps, double dt, pt_stats* out);
+/* The batched push's tuning, per degree group (in increasing N): N_out[i], the
+ * chosen block size block_out[i] (0 while tuning) and the measured ms per step
+ * of the three candidates ms_out[3 i + k]; *ngroups receives the number of
+ * groups (0 before the first pt_push_batch with ctx0 first).  Arrays may be
+ * NULL; at most max_groups entries are written. */
+pt_status pt_batch_tuning(pt_ctx* ctx0, int32_t* N_out, int32_t* block_out, float* ms_out,
+                          int32_t max_groups, int32_t* ngroups);
 
 /* Kernel timing (diagnostics).  pt_profile(ctx, 1) makes every later push
  * record a CUDA event pair around each launch of the push kernel on the

@@ -1,8 +1,11 @@
-// pt_batch.cu -- many independent contexts (boxes) advanced together: one
-// counting sort over the concatenated element space of all boxes, then one
-// persistent push kernel whose threads look up their particle's box and run
-// the push for that box's polynomial degree.  The launch sequence of a call
-// is captured once in a CUDA graph and replayed.
+// pt_batch.cu -- many independent contexts (boxes) advanced together.  The
+// boxes are grouped by polynomial degree N; their elements are concatenated in
+// that order, so that one counting sort over the concatenated element space
+// leaves the particles of each group contiguous.  Each group is pushed by its
+// own instantiation of the push kernel (registers and unrolling of that N),
+// its block size chosen per group by timing the candidates on the first
+// chunks of the first call; the groups' kernels run as parallel branches of a
+// CUDA graph captured once per (nsteps, dt) and replayed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,6 +35,7 @@ struct BatchArgs {
   int64_t ptot;
   int etot;
   const int* perm;
+  const int* offs;            // [etot + 2] segment offsets of the sorted order
   int nsteps;
   double dt;
   unsigned long long* stats;  // [nbox][PT_C_COUNT]
@@ -76,26 +80,27 @@ constexpr int kMaxBoxCounters = 256;
 #ifndef PT_BATCH_MINB
 #define PT_BATCH_MINB 3
 #endif
-template <int G>
-__global__ void __launch_bounds__(128, PT_BATCH_MINB) k_push_batch(const BatchArgs a) {
+// One degree group: the particles whose global element lies in [e_lo, e_hi)
+// (sorted positions offs[e_lo] .. offs[e_hi]), all in boxes with N + 1 = NP.
+// The last group also takes the trailing bin of owners out of range, which the
+// push marks lost without touching the fluid state.
+template <int G, int NP>
+__global__ void __launch_bounds__(128, PT_BATCH_MINB) k_push_batch(const BatchArgs a, int e_lo,
+                                                                   int e_hi) {
   __shared__ unsigned long long sc[kMaxBoxCounters][6];
   for (int i = threadIdx.x; i < kMaxBoxCounters * 6; i += blockDim.x) (&sc[0][0])[i] = 0ull;
   __syncthreads();
+  const int64_t beg = a.offs[e_lo], end = a.offs[e_hi];
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.ptot; t += stride) {
+  for (int64_t t = beg + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < end; t += stride) {
     const int64_t gp = a.perm[t];
     const int b = find_box(a.poffs, a.nbox, gp);
     const DevBox& bx = a.boxes[b];
     const int64_t ip = gp - bx.poff;
     const float* U = reinterpret_cast<const float*>(bx.U);
     PushCounters c = {0, 0, 0, {0, 0, 0}};
-    switch (bx.np) {
-      case 4: push_particle_f32<G, 4, false>(bx.m, bx.k, nullptr, nullptr, U, bx.p, ip, true, a.nsteps, a.dt, c); break;
-      case 5: push_particle_f32<G, 5, false>(bx.m, bx.k, nullptr, nullptr, U, bx.p, ip, true, a.nsteps, a.dt, c); break;
-      case 6: push_particle_f32<G, 6, false>(bx.m, bx.k, nullptr, nullptr, U, bx.p, ip, true, a.nsteps, a.dt, c); break;
-      case 7: push_particle_f32<G, 7, false>(bx.m, bx.k, nullptr, nullptr, U, bx.p, ip, true, a.nsteps, a.dt, c); break;
-      default: push_particle_f32<G, 8, false>(bx.m, bx.k, nullptr, nullptr, U, bx.p, ip, true, a.nsteps, a.dt, c); break;
-    }
+    push_particle_f32<G, NP, false>(bx.m, bx.k, nullptr, nullptr, U, bx.p, ip, true, a.nsteps,
+                                    a.dt, c);
     const int slot = b < kMaxBoxCounters ? b : kMaxBoxCounters - 1;
     if (c.steps) atomicAdd(&sc[slot][0], c.steps);
     if (c.it32) atomicAdd(&sc[slot][1], c.it32);
@@ -110,6 +115,29 @@ __global__ void __launch_bounds__(128, PT_BATCH_MINB) k_push_batch(const BatchAr
     const unsigned long long v = (&sc[0][0])[i];
     if (v) atomicAdd(a.stats + (size_t)(i / 6) * PT_C_COUNT + slots[i % 6], v);
   }
+}
+
+static void launch_group(int np, const BatchArgs& a, int e_lo, int e_hi, int grid, int block,
+                         cudaStream_t s) {
+  switch (np) {
+    case 4: k_push_batch<2, 4><<<grid, block, 0, s>>>(a, e_lo, e_hi); break;
+    case 5: k_push_batch<2, 5><<<grid, block, 0, s>>>(a, e_lo, e_hi); break;
+    case 6: k_push_batch<2, 6><<<grid, block, 0, s>>>(a, e_lo, e_hi); break;
+    case 7: k_push_batch<2, 7><<<grid, block, 0, s>>>(a, e_lo, e_hi); break;
+    default: k_push_batch<2, 8><<<grid, block, 0, s>>>(a, e_lo, e_hi); break;
+  }
+}
+
+static int group_occupancy(int np, int block) {
+  int nb = 0;
+  switch (np) {
+    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push_batch<2, 4>, block, 0); break;
+    case 5: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push_batch<2, 5>, block, 0); break;
+    case 6: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push_batch<2, 6>, block, 0); break;
+    case 7: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push_batch<2, 7>, block, 0); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push_batch<2, 8>, block, 0); break;
+  }
+  return std::max(nb, 1);
 }
 
 __global__ void k_status_counts_batch(const BatchArgs a) {
@@ -136,6 +164,17 @@ using namespace pt;
 DevMesh pt_dev_mesh(const pt_ctx* c);
 void pt_fill_consts(const pt_ctx* c, DevConsts& k);
 
+struct pt_batch_group {
+  int np = 0;           // N + 1 of the group's boxes
+  int e_lo = 0, e_hi = 0;  // its range of the concatenated element space
+  int block = 0;        // chosen threads per block (0: still tuning)
+  int occ[3] = {0, 0, 0};  // resident blocks per SM for each candidate block size
+  float ms[3] = {0.f, 0.f, 0.f};  // measured time per step of each candidate
+  int tried = 0;
+  cudaStream_t st = nullptr;      // branch stream of the captured graph
+  cudaEvent_t done = nullptr;
+};
+
 struct pt_batch_plan {
   std::vector<const pt_ctx*> ctxs;
   std::vector<pt_particles> parts;
@@ -148,28 +187,33 @@ struct pt_batch_plan {
   int* d_perm = nullptr;
   unsigned long long* d_stats = nullptr;
   int nsm = 1;
-  // online block-size tuning: candidates are tried on successive chunks of
-  // the first call, timed with events; the fastest is kept
-  int block = 0;
-  std::vector<int> tried;
-  std::vector<float> tried_ms;
-  int occ[3] = {0, 0, 0};  // resident blocks per SM of k_push_batch per candidate block size
+  std::vector<pt_batch_group> groups;
   // private stream the graph is captured on (the caller's stream may be the
   // legacy default stream, which cannot be captured); the graph runs on the
   // caller's stream
   cudaStream_t cap = nullptr;
+  cudaEvent_t fork = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_nsteps = -1;
   double graph_dt = 0.0;
-  int graph_block = 0;
   ~pt_batch_plan() {
     if (graph) cudaGraphExecDestroy(graph);
+    for (auto& g : groups) {
+      if (g.st) cudaStreamDestroy(g.st);
+      if (g.done) cudaEventDestroy(g.done);
+    }
+    if (fork) cudaEventDestroy(fork);
     if (cap) cudaStreamDestroy(cap);
     cudaFree(d_boxes);
     cudaFree(d_poffs);
     cudaFree(d_scratch);
     cudaFree(d_perm);
     cudaFree(d_stats);
+  }
+  bool tuned() const {
+    for (const auto& g : groups)
+      if (!g.block) return false;
+    return true;
   }
 };
 
@@ -181,7 +225,13 @@ void pt_batch_release(pt_ctx* c) {
 static const int kBlocks[3] = {64, 96, 128};
 static const int kChunk = 10;
 
-static void enqueue_chunk(pt_batch_plan* P, const BatchArgs& a, int block, cudaStream_t s) {
+static int group_grid(const pt_batch_plan* P, const pt_batch_group& g, int cand) {
+  const int64_t want = (P->ptot + kBlocks[cand] - 1) / kBlocks[cand];
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)P->nsm * g.occ[cand]));
+}
+
+// binning of all particles over the concatenated element space
+static void enqueue_bin(pt_batch_plan* P, const BatchArgs& a, cudaStream_t s) {
   BinLayout L;
   bin_layout(P->etot, P->d_scratch, L);
   cudaMemsetAsync(L.counts, 0, sizeof(int) * L.nbins, s);
@@ -189,14 +239,29 @@ static void enqueue_chunk(pt_batch_plan* P, const BatchArgs& a, int block, cudaS
   k_hist_batch<<<std::max(g, 1), 256, 0, s>>>(a, L.counts);
   bin_scan(L, s);
   k_scatter_batch<<<std::max(g, 1), 256, 0, s>>>(a, L.cursor, P->d_perm);
-  // occupancy was queried when the plan was made: no API call but stream work
-  // may run here while the stream is being captured
-  int occ = 1;
+}
+
+static int cand_of(int block) {
   for (int i = 0; i < 3; ++i)
-    if (kBlocks[i] == block) occ = std::max(P->occ[i], 1);
-  const int64_t want = (P->ptot + block - 1) / block;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)P->nsm * occ));
-  k_push_batch<2><<<grid, block, 0, s>>>(a);
+    if (kBlocks[i] == block) return i;
+  return 2;
+}
+
+// one chunk with every group on its tuned block size; the groups as parallel
+// branches (fork / join events) when par, else one after another on s
+static void enqueue_chunk(pt_batch_plan* P, const BatchArgs& a, cudaStream_t s, bool par) {
+  enqueue_bin(P, a, s);
+  if (par) cudaEventRecord(P->fork, s);
+  for (auto& g : P->groups) {
+    const int cand = cand_of(g.block);
+    cudaStream_t gs = par ? g.st : s;
+    if (par) cudaStreamWaitEvent(gs, P->fork, 0);
+    launch_group(g.np, a, g.e_lo, g.e_hi, group_grid(P, g, cand), kBlocks[cand], gs);
+    if (par) {
+      cudaEventRecord(g.done, gs);
+      cudaStreamWaitEvent(s, g.done, 0);
+    }
+  }
 }
 
 static bool same_plan(const pt_batch_plan* P, pt_ctx* const* ctxs, const pt_particles* parts,
@@ -244,13 +309,34 @@ extern "C" pt_status pt_push_batch(pt_ctx* const* ctxs, const pt_particles* part
     P->nsm = c0->nsm;
     std::vector<DevBox> hb(nbox);
     std::vector<int64_t> poffs(nbox + 1, 0);
-    int64_t pt = 0;
+    // element space ordered by degree (then box index): each degree's
+    // particles form one contiguous range of the sorted order
+    std::vector<int> order(nbox);
+    for (int b = 0; b < nbox; ++b) order[b] = b;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return ctxs[x]->N < ctxs[y]->N; });
     int64_t et = 0;
+    for (int i = 0; i < nbox; ++i) {
+      const int b = order[i];
+      const pt_ctx* c = ctxs[b];
+      if (P->groups.empty() || P->groups.back().np != c->N + 1) {
+        pt_batch_group g;
+        g.np = c->N + 1;
+        g.e_lo = g.e_hi = (int)et;
+        P->groups.push_back(g);
+      }
+      hb[b].eoff = (int)et;
+      et += c->nelem;
+      P->groups.back().e_hi = (int)et;
+    }
+    if (!P->groups.empty()) P->groups.back().e_hi = (int)et + 1;  // + the trailing bin
+    int64_t pt = 0;
     for (int b = 0; b < nbox; ++b) {
       const pt_ctx* c = ctxs[b];
       P->ctxs.push_back(c);
       P->parts.push_back(parts[b]);
       DevBox& d = hb[b];
+      const int eoff = d.eoff;
       std::memset(&d, 0, sizeof d);
       d.m = pt_dev_mesh(c);
       pt_fill_consts(c, d.k);
@@ -258,11 +344,10 @@ extern "C" pt_status pt_push_batch(pt_ctx* const* ctxs, const pt_particles* part
              parts[b].status};
       d.U = c->U;
       d.np = c->N + 1;
-      d.eoff = (int)et;
+      d.eoff = eoff;
       d.poff = pt;
       poffs[b] = pt;
       pt += parts[b].n;
-      et += c->nelem;
     }
     poffs[nbox] = pt;
     if (pt > INT32_MAX || et > (1 << 28)) {
@@ -282,10 +367,15 @@ extern "C" pt_status pt_push_batch(pt_ctx* const* ctxs, const pt_particles* part
     }
     cudaMemcpy(P->d_boxes, hb.data(), sizeof(DevBox) * nbox, cudaMemcpyHostToDevice);
     cudaMemcpy(P->d_poffs, poffs.data(), sizeof(int64_t) * (nbox + 1), cudaMemcpyHostToDevice);
-    for (int i = 0; i < 3; ++i)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P->occ[i], k_push_batch<2>, kBlocks[i], 0);
-    if (cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking) != cudaSuccess) {
-      c0->err = "pt_push_batch: stream creation failed";
+    bool ok = cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (auto& g : P->groups) {
+      for (int i = 0; i < 3; ++i) g.occ[i] = group_occupancy(g.np, kBlocks[i]);
+      ok = ok && cudaStreamCreateWithFlags(&g.st, cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+      c0->err = "pt_push_batch: stream or event creation failed";
       return PT_ERR_CUDA;
     }
   }
@@ -296,42 +386,49 @@ extern "C" pt_status pt_push_batch(pt_ctx* const* ctxs, const pt_particles* part
   a.ptot = P->ptot;
   a.etot = P->etot;
   a.perm = P->d_perm;
+  {
+    BinLayout L;
+    bin_layout(P->etot, P->d_scratch, L);
+    a.offs = L.offs;
+  }
   a.dt = dt;
   a.stats = P->d_stats;
   if (P->ptot > 0 && nsteps > 0) {
-    if (P->block == 0) {
-      // tuning call: chunks go out one by one with candidate block sizes
+    if (!P->tuned()) {
+      // tuning call: chunk by chunk, every group still tuning runs the next
+      // candidate block size, timed on its own; groups run one after another
       cudaMemsetAsync(P->d_stats, 0, sizeof(unsigned long long) * PT_C_COUNT * nbox, s);
       for (int s0 = 0; s0 < nsteps; s0 += kChunk) {
         a.nsteps = std::min(kChunk, nsteps - s0);
-        const int cand = (int)P->tried.size();
-        const int block = cand < 3 ? kBlocks[cand] : 128;
-        cudaEvent_t e0, e1;
-        cudaEventCreate(&e0);
-        cudaEventCreate(&e1);
-        cudaEventRecord(e0, s);
-        enqueue_chunk(P, a, block, s);
-        c0->launches += 6;  // histogram, three scan kernels, scatter, push
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        if (cand < 3) {
-          P->tried.push_back(block);
-          P->tried_ms.push_back(ms / std::max(a.nsteps, 1));
+        enqueue_bin(P, a, s);
+        c0->launches += 5;
+        for (auto& g : P->groups) {
+          const int cand = g.block ? cand_of(g.block) : std::min(g.tried, 2);
+          cudaEvent_t e0, e1;
+          cudaEventCreate(&e0);
+          cudaEventCreate(&e1);
+          cudaEventRecord(e0, s);
+          launch_group(g.np, a, g.e_lo, g.e_hi, group_grid(P, g, cand), kBlocks[cand], s);
+          cudaEventRecord(e1, s);
+          c0->launches += 1;
+          cudaEventSynchronize(e1);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          if (!g.block) {
+            g.ms[cand] = ms / std::max(a.nsteps, 1);
+            if (++g.tried == 3) {
+              int best = 0;
+              for (int i = 1; i < 3; ++i)
+                if (g.ms[i] < g.ms[best]) best = i;
+              g.block = kBlocks[best];
+            }
+          }
         }
       }
-      if (P->tried.size() >= 3) {
-        int best = 0;
-        for (int i = 1; i < 3; ++i)
-          if (P->tried_ms[i] < P->tried_ms[best]) best = i;
-        P->block = P->tried[best];
-      }
     } else {
-      if (!P->graph || P->graph_nsteps != nsteps || P->graph_dt != dt ||
-          P->graph_block != P->block) {
+      if (!P->graph || P->graph_nsteps != nsteps || P->graph_dt != dt) {
         if (P->graph) cudaGraphExecDestroy(P->graph);
         P->graph = nullptr;
         cudaGraph_t g = nullptr;
@@ -341,7 +438,7 @@ extern "C" pt_status pt_push_batch(pt_ctx* const* ctxs, const pt_particles* part
           cudaMemsetAsync(P->d_stats, 0, sizeof(unsigned long long) * PT_C_COUNT * nbox, P->cap);
           for (int s0 = 0; s0 < nsteps; s0 += kChunk) {
             a.nsteps = std::min(kChunk, nsteps - s0);
-            enqueue_chunk(P, a, P->block, P->cap);
+            enqueue_chunk(P, a, P->cap, true);
           }
           e = cudaStreamEndCapture(P->cap, &g);
         }
@@ -354,10 +451,9 @@ extern "C" pt_status pt_push_batch(pt_ctx* const* ctxs, const pt_particles* part
         }
         P->graph_nsteps = nsteps;
         P->graph_dt = dt;
-        P->graph_block = P->block;
       }
       cudaError_t e = cudaGraphLaunch(P->graph, s);
-      c0->launches += 6 * (int64_t)((nsteps + kChunk - 1) / kChunk);
+      c0->launches += (5 + (int64_t)P->groups.size()) * ((nsteps + kChunk - 1) / kChunk);
       if (e != cudaSuccess) {
         c0->err = std::string("pt_push_batch: graph launch: ") + cudaGetErrorString(e);
         return PT_ERR_CUDA;
@@ -409,4 +505,20 @@ extern "C" pt_status pt_push_batch(pt_ctx* const* ctxs, const pt_particles* part
   }
   if (ret != PT_OK) c0->err = "pt_push_batch: some particles were frozen (see stats)";
   return ret;
+}
+
+extern "C" pt_status pt_batch_tuning(pt_ctx* ctx0, int32_t* np_out, int32_t* block_out,
+                                     float* ms_out, int32_t max_groups, int32_t* ngroups) {
+  if (!ctx0 || !ngroups) return PT_ERR_ARG;
+  const pt_batch_plan* P = ctx0->batch;
+  *ngroups = P ? (int32_t)P->groups.size() : 0;
+  if (!P) return PT_OK;
+  for (int i = 0; i < (int)P->groups.size() && i < max_groups; ++i) {
+    const auto& g = P->groups[i];
+    if (np_out) np_out[i] = g.np - 1;
+    if (block_out) block_out[i] = g.block;
+    if (ms_out)
+      for (int k = 0; k < 3; ++k) ms_out[3 * i + k] = g.ms[k];
+  }
+  return PT_OK;
 }

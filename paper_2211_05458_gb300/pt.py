@@ -79,7 +79,8 @@ EXPORTS = ["pt_config_default", "pt_init_mesh", "pt_set_config", "pt_set_fluid",
            "pt_mlp_features", "pt_mlp_nparams", "pt_mlp_set", "pt_mlp_get", "pt_mlp_forward",
            "pt_mlp_grad", "pt_push_batch", "pt_profile", "pt_profile_read", "pt_destroy",
            "pt_last_error", "pt_deposit_noalloc", "pt_find_element", "pt_stage_terms",
-           "pt_launch_count", "pt_measure_peak", "pt_mlp_start", "pt_read_histograms"]
+           "pt_launch_count", "pt_measure_peak", "pt_mlp_start", "pt_read_histograms",
+           "pt_batch_tuning"]
 
 
 def library_path() -> str:
@@ -130,6 +131,8 @@ def lib():
                                           ctypes.POINTER(ctypes.c_int64)]
             L.pt_launch_count.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
             L.pt_read_histograms.argtypes = [_vp, ctypes.POINTER(Histograms)]
+            L.pt_batch_tuning.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_int32)]
             L.pt_mlp_start.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_int32]
             L.pt_measure_peak.argtypes = [ctypes.c_int32, _vp, ctypes.POINTER(ctypes.c_double)]
             L.pt_destroy.argtypes = [_vp]
@@ -444,3 +447,17 @@ def measure_peak(kind: int, stream=None) -> float:
     if rc != 0:
         raise PtError(rc, "pt_measure_peak failed")
     return float(t.value)
+
+
+def batch_tuning(ctx0):
+    """Per degree group of the batched push led by ctx0: list of dicts
+    (N, chosen block size, ms per step of the 64/96/128 candidates)."""
+    ng = ctypes.c_int32(0)
+    n = (ctypes.c_int32 * 8)()
+    b = (ctypes.c_int32 * 8)()
+    ms = (ctypes.c_float * 24)()
+    rc = lib().pt_batch_tuning(ctx0.h, n, b, ms, 8, ctypes.byref(ng))
+    if rc != 0:
+        raise PtError(rc, "pt_batch_tuning failed")
+    return [{"N": int(n[i]), "block": int(b[i]), "ms_per_step": [float(ms[3 * i + k]) for k in range(3)]}
+            for i in range(min(ng.value, 8))]

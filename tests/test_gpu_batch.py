@@ -1,6 +1,7 @@
-"""Batched push of many independent boxes (one persistent kernel per chunk,
-captured in a CUDA graph after the first call): identical to pushing every box
-alone, and within the FP32-mode tolerance of the oracle."""
+"""Batched push of many independent boxes (boxes grouped by polynomial degree,
+one persistent kernel per group and chunk with a tuned block size, captured in
+a CUDA graph after the tuning call): identical to pushing every box alone, and
+within the FP32-mode tolerance of the oracle."""
 import numpy as np
 import pytest
 import torch
@@ -26,6 +27,7 @@ def _setup(nbox=6, seed=1):
 
 def test_batch_equals_individual_pushes_bitwise():
     boxes, ctxs, parts = _setup()
+    parts[0].elem[0] = -1  # an owner out of range: lost in both, untouched otherwise
     ref = [p.clone() for p in parts]
     # 20 steps are two chunks: calls 1 and 2 try the three block sizes, call 3
     # captures the graph and replays it, call 4 replays it again
@@ -38,8 +40,14 @@ def test_batch_equals_individual_pushes_bitwise():
     for a, b in zip(parts, ref):
         for f in ("x", "v", "elem", "hits", "status"):
             assert torch.equal(getattr(a, f), getattr(b, f)), f
-    assert sum(s["particle_steps"] for s in st) == 20 * sum(p.n for p in parts)
+    assert sum(s["particle_steps"] for s in st) == 20 * (sum(p.n for p in parts) - 1)
     assert sum(s["crossings"] for s in st) > 100
+    assert int(parts[0].status[0]) & pt.ST_LOST
+    # one group per polynomial degree, each with a tuned block size
+    tun = pt.batch_tuning(ctxs[0])
+    print("batch tuning", tun)
+    assert [g["N"] for g in tun] == sorted({wl.N for wl in boxes})
+    assert all(g["block"] in (64, 96, 128) and min(g["ms_per_step"]) > 0 for g in tun)
 
 
 def test_batch_matches_oracle_fp32():
