@@ -176,12 +176,12 @@ def make_workload(args, device, seed, precision):
                             seed=seed, device=device, precision=precision)
 
 
-# DRAM bytes per particle-step of k_push, from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum of the push kernel on the 32^3, 10^6-particle case, per
-# particle-step; see profiles/); traffic scales with the particles processed.
-# None while the kernel has changed since the last capture (the capture of
-# 136 B per particle-step predates the FP32-decided face crossings).
-TRAFFIC_BYTES_PER_PARTICLE_STEP = None
+# DRAM bytes per particle-stage of the stage kernel k_stage_f32 (learned start),
+# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of one
+# launch on the 32^3, 10^6-particle channel, divided by its 10^6 particles;
+# profiles/); the traffic is per particle, so it scales with the particles of
+# a launch.  None while the kernel differs from the captured one.
+TRAFFIC_BYTES_PER_PARTICLE_STAGE = None
 
 
 def algorithmic_flops_per_particle_stage(G=4, NP=6, ntri=2, it_full=2.0, it_resid=2.0):
@@ -539,6 +539,10 @@ def main():
         if world > 1:
             dist.barrier()
     ms = ev0.elapsed_time(ev1)
+    # device time per kernel kind from libpt's own events on its stream:
+    # 0 push chunks (the resident kernel, or a staged chunk incl. its copies),
+    # 1 stage kernels, 2 learned-start kernels, 3 exact-tracking kernels
+    kinds = {k: ctx.profile_read_kind(k) for k in (1, 2, 3)}
     kern_ms, launches = ctx.profile_read()
     gpu_launches = ctx.launch_count()
     ctx.profile(False)
@@ -546,22 +550,42 @@ def main():
     ms = reduce_time_ms(ms, world, dev)
     value = throughput(P, args.inner, args.steps, world, ms)
     stats = ctx.push(parts, 1, wl.dt, stats=True)  # one more step with counters
+    hist = ctx.histograms()
+    staged = kinds[1][1] > 0
 
-    # roofline of the dominant kernel (k_push): it is bound by FP32 arithmetic and
-    # issue latency, not by memory (DRAM traffic is a few percent of peak)
+    # roofline of the dominant kernel: the stage kernel of the staged schedule
+    # (one RK stage of every particle per launch), else the resident push (a
+    # whole chunk of steps per launch).  It is bound by FP32 arithmetic and
+    # issue latency, not by memory.
     nps = max(stats["particle_steps"], 1) * 5
     it32, it64 = stats["newton_it_fp32"] / nps, stats["newton_it_fp64"] / nps
+    # iterations per stage as the stage kernel runs them (the totals also
+    # hold the walk's inverse maps after a crossing)
+    h_it32 = sum(k * c for k, c in enumerate(hist["newton_fp32"])) / max(sum(hist["newton_fp32"]), 1)
+    h_it64 = sum(k * c for k, c in enumerate(hist["newton_final"])) / max(sum(hist["newton_final"]), 1)
+    if staged:
+        it32, it64 = h_it32, h_it64
     flops_stage = algorithmic_flops_per_particle_stage(G=4, NP=wl.N + 1, ntri=2, it_full=it32,
                                                        it_resid=it64)
-    avg_launch_s = (kern_ms / 1e3) / max(launches, 1)
-    flops_launch = flops_stage * 5 * args.inner * P
+    if staged:
+        kname = "k_stage_f32<G=4,NP=6,%s>" % ("learned start" if guess else "trilinear start")
+        k_ms, k_n = kinds[1]
+        flops_launch = flops_stage * P
+    else:
+        kname = "k_push<4,6,fp32,%s>" % ("learned" if guess else "trilinear")
+        k_ms, k_n = kern_ms, launches
+        flops_launch = flops_stage * 5 * args.inner * P
+    avg_launch_s = (k_ms / 1e3) / max(k_n, 1)
     achieved = flops_launch / avg_launch_s / 1e12
     fp32_peak = peaks_alu["fp32"]
+    # DRAM bytes per particle-stage of the stage kernel from one ncu capture
+    # of the same kernel on the 32^3, 10^6-particle channel (profiles/)
+    traffic = (TRAFFIC_BYTES_PER_PARTICLE_STAGE * P
+               if (staged and TRAFFIC_BYTES_PER_PARTICLE_STAGE) else None)
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak,
-                "traffic": (TRAFFIC_BYTES_PER_PARTICLE_STEP * P * args.inner
-                            if TRAFFIC_BYTES_PER_PARTICLE_STEP else None),
-                "kernel": "k_push<4,6,fp32,%s>" % ("learned" if guess else "trilinear"),
+                "traffic": traffic,
+                "kernel": kname,
                 "peak_kind": "measured: libpt FP32 FMA probe (pt_measure_peak), "
                              f"{peaks_alu['sms']} SMs; from unit counts: "
                              f"{fp32_peak_tflops(sms=peaks_alu['sms']):.1f}",
@@ -569,18 +593,30 @@ def main():
                 "flops_per_particle_stage": flops_stage,
                 "newton_iterations_per_stage": {"full": it32, "residual_only": it64},
                 "launch_ms": avg_launch_s * 1e3,
-                "kernel_share_of_step": (kern_ms / ms) if ms > 0 else None,
-                "hbm_frac_of_measured": ((TRAFFIC_BYTES_PER_PARTICLE_STEP * P * args.inner
-                                          / avg_launch_s / 1e9) / float(peaks.get("hbm_gbs", 6800.0))
-                                         if TRAFFIC_BYTES_PER_PARTICLE_STEP else None)}
+                "kernel_share_of_step": (k_ms / ms) if ms > 0 else None,
+                "hbm_gbs_from_traffic": (traffic / avg_launch_s / 1e9 if traffic else None),
+                "hbm_frac_of_measured": (traffic / avg_launch_s / 1e9 /
+                                         float(peaks.get("hbm_gbs", 6800.0)) if traffic else None),
+                "other_kernels_ms_per_launch": {
+                    "learned_start": kinds[2][0] / max(kinds[2][1], 1) if kinds[2][1] else None,
+                    "exact_tracking": kinds[3][0] / max(kinds[3][1], 1) if kinds[3][1] else None},
+                "share_of_step": {"stage": kinds[1][0] / ms, "learned_start": kinds[2][0] / ms,
+                                  "exact_tracking": kinds[3][0] / ms} if staged else None}
     if guess:
         # the learned start's own products run on the tensor cores (BF16, FP32
         # accumulate): 3x64 + 2 x 64x64 + 64x3 multiply-adds per particle-stage
         mlp_flops = 2 * (3 * 64 + 2 * 64 * 64 + 64 * 3)
-        t_ach = mlp_flops * 5 * args.inner * P / avg_launch_s / 1e12
-        roofline["mlp_tensor"] = {"flops_per_particle_stage": mlp_flops, "achieved": t_ach,
+        if staged and kinds[2][1]:
+            t_s = kinds[2][0] / 1e3 / kinds[2][1]
+            t_ach = mlp_flops * P / t_s / 1e12
+            t_kern = "k_guess_tc (tcgen05, one RK stage of every particle per launch)"
+        else:
+            t_ach = mlp_flops * 5 * args.inner * P / avg_launch_s / 1e12
+            t_kern = "inside k_push (mma.sync)"
+        roofline["mlp_tensor"] = {"kernel": t_kern, "flops_per_particle_stage": mlp_flops,
+                                  "achieved": t_ach,
                                   "peak": float(peaks.get("bf16_tflops", 1900.0)),
-                                  "unit": "TFLOP/s",
+                                  "unit": "TFLOP/s", "peak_kind": peak_kind + " (cuBLAS bf16)",
                                   "frac": t_ach / float(peaks.get("bf16_tflops", 1900.0))}
 
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
@@ -592,12 +628,15 @@ def main():
                        "drag and RK; double-float final Newton to |dxi| < 1e-12; FP64 "
                        "intersection where FP32 is ambiguous",
                        "inner_steps_per_call": args.inner, "guess": "mlp" if guess else "trilinear",
+                       "schedule": "staged (one kernel per RK stage)" if staged else
+                                   "resident (one kernel per call chunk)",
                        "inputs_vs_l2": inputs_vs_l2(P, wl),
                        "parallelism": f"weak, {world} independent GPU(s)"},
             "gpu_launches": gpu_launches, "clocks": clk.summary(), "roofline": roofline,
             "stats_one_step": {k: stats[k] for k in ("particle_steps", "crossings", "wall_hits",
                                                      "newton_it_fp32", "newton_it_fp64",
-                                                     "slow_track", "near_face")}}
+                                                     "slow_track", "near_face", "near_wall")},
+            "histograms_one_step": hist}
     if mlp_info:
         line["mlp"] = mlp_info
 

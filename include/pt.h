@@ -245,6 +245,12 @@ pt_status pt_set_fluid(pt_ctx* ctx, int32_t N, int32_t node_type, const void* U_
 
 /* Advances every live particle by nsteps steps of the 5-stage, 4th-order
  * low-storage RK scheme of Carpenter & Kennedy (Sec. 3.1) with time step dt.
+ * The fluid state registered by pt_set_fluid is frozen during a call: all
+ * nsteps x 5 stages interpolate the same U.  A solver that updates U every
+ * time step calls pt_push with nsteps = 1 between its own updates (binning
+ * and, in the staged schedule, the sorted copy of the particle state are then
+ * paid per step); the paper's fully coupled loop, in which the fluid and the
+ * particles advance stage by stage together, is not offered.
  * Per stage and particle (Sec. 3.2): inverse map x -> xi by Newton, tensor-
  * product interpolation of rho and rho u at xi (Eq. part_interpolation),
  * drag (Eqs. dragforce, dragfactor) plus gravity, the RK update of x and v,
@@ -416,6 +422,12 @@ pt_status pt_batch_tuning(pt_ctx* ctx0, int32_t* N_out, int32_t* block_out, floa
  * record.  pt_profile(ctx, 0) stops recording. */
 pt_status pt_profile(pt_ctx* ctx, int32_t enable);
 pt_status pt_profile_read(pt_ctx* ctx, double* kernel_ms, int64_t* launches);
+/* As pt_profile_read for one kind of kernel, clearing only that record:
+ * kind 0 the push (the resident kernel, or a whole chunk of the staged
+ * schedule from its sorted copy to the copy back), 1 the staged schedule's
+ * stage kernels, 2 its learned-start kernels, 3 its exact-tracking kernels.
+ * (pt_profile_read reads kind 0 and clears all four.) */
+pt_status pt_profile_read_kind(pt_ctx* ctx, int32_t kind, double* kernel_ms, int64_t* launches);
 
 /* Reads the histograms of the last pt_push into *out (synchronises). */
 pt_status pt_read_histograms(pt_ctx* ctx, pt_histograms* out);

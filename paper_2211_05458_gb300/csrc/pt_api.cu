@@ -915,7 +915,7 @@ static pt_status read_stats(pt_ctx* c, const pt_particles* p, double dt, pt_stat
   return PT_OK;
 }
 
-static cudaEvent_t take_event(pt_ctx* c) {
+static cudaEvent_t take_event(pt_ctx* c, int kind = 0) {
   cudaEvent_t e = nullptr;
   if (!c->ev_free.empty()) {
     e = c->ev_free.back();
@@ -923,7 +923,7 @@ static cudaEvent_t take_event(pt_ctx* c) {
   } else if (cudaEventCreate(&e) != cudaSuccess) {
     return nullptr;
   }
-  c->ev_used.push_back(e);
+  c->ev_used[kind].push_back(e);
   return e;
 }
 
@@ -1034,16 +1034,19 @@ static pt_status push_staged(pt_ctx* c, const pt_particles* p, int32_t nsteps, d
         a.stage = st;
         a.count = ctr + (k & 1);
         a.count_next = ctr + ((k + 1) & 1);
-        if (mlp) {
-          rc = launch_staged(c->g, f64, np, PT_SOP_GUESS, a, dp, c->d_perm, gguess, 128,
-                             c->stream);
+        // each kernel between an event pair of its kind when profiling
+        auto timed = [&](int kind, int op, int g, int b) {
+          cudaEvent_t q0 = c->profile ? take_event(c, kind) : nullptr;
+          cudaEvent_t q1 = c->profile ? take_event(c, kind) : nullptr;
+          if (q0) cudaEventRecord(q0, c->stream);
+          const int r = launch_staged(c->g, f64, np, op, a, dp, c->d_perm, g, b, c->stream);
+          if (q1) cudaEventRecord(q1, c->stream);
           c->launches += 1;
-        }
-        if (!rc) rc = launch_staged(c->g, f64, np, PT_SOP_STAGE, a, dp, c->d_perm, grid, block,
-                                    c->stream);
-        if (!rc) rc = launch_staged(c->g, f64, np, PT_SOP_TRACK, a, dp, c->d_perm, gtrack, 128,
-                                    c->stream);
-        c->launches += 2;
+          return r;
+        };
+        if (mlp) rc = timed(2, PT_SOP_GUESS, gguess, 128);
+        if (!rc) rc = timed(1, PT_SOP_STAGE, grid, block);
+        if (!rc) rc = timed(3, PT_SOP_TRACK, gtrack, 128);
       }
     }
     if (!rc) rc = launch_staged(c->g, f64, np, PT_SOP_SCATTER, a, dp, c->d_perm, gmove, 256,
@@ -1451,22 +1454,32 @@ pt_status pt_profile(pt_ctx* c, int32_t enable) {
   return PT_OK;
 }
 
-pt_status pt_profile_read(pt_ctx* c, double* ms, int64_t* launches) {
+pt_status pt_profile_read_kind(pt_ctx* c, int32_t kind, double* ms, int64_t* launches) {
   if (!c) return fail(nullptr, PT_ERR_ARG, "ctx is NULL");
+  if (kind < 0 || kind > 3) return fail(c, PT_ERR_ARG, "kind must be 0..3");
   CK(cudaStreamSynchronize(c->stream));
   double tot = 0.0;
   int64_t k = 0;
-  for (size_t i = 0; i + 1 < c->ev_used.size(); i += 2) {
+  std::vector<cudaEvent_t>& u = c->ev_used[kind];
+  for (size_t i = 0; i + 1 < u.size(); i += 2) {
     float t = 0.f;
-    if (cudaEventElapsedTime(&t, c->ev_used[i], c->ev_used[i + 1]) == cudaSuccess) {
+    if (cudaEventElapsedTime(&t, u[i], u[i + 1]) == cudaSuccess) {
       tot += t;
       ++k;
     }
   }
-  for (cudaEvent_t e : c->ev_used) c->ev_free.push_back(e);
-  c->ev_used.clear();
+  for (cudaEvent_t e : u) c->ev_free.push_back(e);
+  u.clear();
   if (ms) *ms = tot;
   if (launches) *launches = k;
+  return PT_OK;
+}
+
+pt_status pt_profile_read(pt_ctx* c, double* ms, int64_t* launches) {
+  if (!c) return fail(nullptr, PT_ERR_ARG, "ctx is NULL");
+  pt_status s = pt_profile_read_kind(c, 0, ms, launches);
+  if (s) return s;
+  for (int k = 1; k < 4; ++k) pt_profile_read_kind(c, k, nullptr, nullptr);  // clear the rest
   return PT_OK;
 }
 
@@ -1492,7 +1505,8 @@ pt_status pt_launch_count(pt_ctx* c, int64_t* n) {
 
 pt_status pt_destroy(pt_ctx* c) {
   if (!c) return PT_OK;
-  for (cudaEvent_t e : c->ev_used) cudaEventDestroy(e);
+  for (auto& u : c->ev_used)
+    for (cudaEvent_t e : u) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
   for (void* q : c->allocs) cudaFree(q);
   if (c->d_scratch) cudaFree(c->d_scratch);

@@ -70,7 +70,10 @@ struct pt_ctx {
   int64_t launches = 0;
   // kernel timing (pt_profile)
   bool profile = false;
-  std::vector<cudaEvent_t> ev_free, ev_used;
+  // event pairs per kernel kind: 0 the push (a whole chunk of the staged
+  // schedule, the resident kernel), 1 stage kernels, 2 learned start, 3 exact
+  // tracking (staged schedule)
+  std::vector<cudaEvent_t> ev_free, ev_used[4];
   std::string err = "no error";
 };
 

@@ -646,6 +646,10 @@ template <int NP, typename T>
 __device__ __forceinline__ void interp4(const T* __restrict__ Ue, const T* l1, const T* l2,
                                         const T* l3, T* out) {
   constexpr int N3 = NP * NP * NP;
+  // FP32 rows of 6 nodes: two rows (48 bytes, 16-byte aligned at even rows
+  // since every variable block is a multiple of 16 bytes) in three 16-byte
+  // loads; rows of 4 or 8 nodes in 16-byte loads
+  constexpr bool kPair = std::is_same<T, float>::value && NP == 6;
 #pragma unroll 1
   for (int v = 0; v < 4; ++v) {
     const T* Uv = Ue + v * N3;
@@ -653,20 +657,46 @@ __device__ __forceinline__ void interp4(const T* __restrict__ Ue, const T* l1, c
 #pragma unroll 1
     for (int kk = 0; kk < NP; ++kk) {
       T t2 = T(0);
+      if constexpr (kPair) {
 #pragma unroll
-      for (int j = 0; j < NP; ++j) {
-        const T* row = Uv + NP * (j + NP * kk);
-        T t1 = T(0);
-        if constexpr (std::is_same<T, float>::value && NP % 2 == 0) {
-          float rv[NP];
-          load_row<NP>(reinterpret_cast<const float*>(row), rv);
+        for (int j = 0; j < NP; j += 2) {
+          const float4* q = reinterpret_cast<const float4*>(Uv + NP * (j + NP * kk));
+          const float4 q0 = __ldg(q), q1 = __ldg(q + 1), q2 = __ldg(q + 2);
+          const float r0[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
+          const float r1[6] = {q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+          T t1 = T(0), u1 = T(0);
 #pragma unroll
-          for (int i = 0; i < NP; ++i) t1 = tfma((T)rv[i], l1[i], t1);
-        } else {
+          for (int i = 0; i < NP; ++i) t1 = tfma((T)r0[i], l1[i], t1);
 #pragma unroll
-          for (int i = 0; i < NP; ++i) t1 = tfma(__ldg(row + i), l1[i], t1);
+          for (int i = 0; i < NP; ++i) u1 = tfma((T)r1[i], l1[i], u1);
+          t2 = tfma(t1, l2[j], t2);
+          t2 = tfma(u1, l2[j + 1], t2);
         }
-        t2 = tfma(t1, l2[j], t2);
+      } else {
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+          const T* row = Uv + NP * (j + NP * kk);
+          T t1 = T(0);
+          if constexpr (std::is_same<T, float>::value && NP % 4 == 0) {
+#pragma unroll
+            for (int i = 0; i < NP; i += 4) {
+              const float4 q = __ldg(reinterpret_cast<const float4*>(row + i));
+              t1 = tfma((T)q.x, l1[i], t1);
+              t1 = tfma((T)q.y, l1[i + 1], t1);
+              t1 = tfma((T)q.z, l1[i + 2], t1);
+              t1 = tfma((T)q.w, l1[i + 3], t1);
+            }
+          } else if constexpr (std::is_same<T, float>::value && NP % 2 == 0) {
+            float rv[NP];
+            load_row<NP>(reinterpret_cast<const float*>(row), rv);
+#pragma unroll
+            for (int i = 0; i < NP; ++i) t1 = tfma((T)rv[i], l1[i], t1);
+          } else {
+#pragma unroll
+            for (int i = 0; i < NP; ++i) t1 = tfma(__ldg(row + i), l1[i], t1);
+          }
+          t2 = tfma(t1, l2[j], t2);
+        }
       }
       acc = tfma(t2, l3[kk], acc);
     }

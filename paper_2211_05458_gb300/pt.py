@@ -80,7 +80,7 @@ EXPORTS = ["pt_config_default", "pt_init_mesh", "pt_set_config", "pt_set_fluid",
            "pt_mlp_grad", "pt_push_batch", "pt_profile", "pt_profile_read", "pt_destroy",
            "pt_last_error", "pt_deposit_noalloc", "pt_find_element", "pt_stage_terms",
            "pt_launch_count", "pt_measure_peak", "pt_mlp_start", "pt_read_histograms",
-           "pt_batch_tuning"]
+           "pt_batch_tuning", "pt_profile_read_kind"]
 
 
 def library_path() -> str:
@@ -135,6 +135,8 @@ def lib():
                                           ctypes.POINTER(ctypes.c_int32)]
             L.pt_mlp_start.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_int32]
             L.pt_measure_peak.argtypes = [ctypes.c_int32, _vp, ctypes.POINTER(ctypes.c_double)]
+            L.pt_profile_read_kind.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_int64)]
             L.pt_destroy.argtypes = [_vp]
             L.pt_last_error.argtypes = [_vp]
             L.pt_last_error.restype = ctypes.c_char_p
@@ -408,6 +410,14 @@ class Context:
         self._check(lib().pt_read_histograms(self.h, ctypes.byref(h)))
         return {"newton_fp32": list(h.newton_fp32), "newton_final": list(h.newton_final),
                 "crossings": list(h.crossings)}
+
+    def profile_read_kind(self, kind: int):
+        """(ms, launches) of one kernel kind: 0 push/chunk, 1 stage, 2 learned
+        start, 3 exact tracking; clears that record only."""
+        ms, k = ctypes.c_double(0.0), ctypes.c_int64(0)
+        self._check(lib().pt_profile_read_kind(self.h, int(kind), ctypes.byref(ms),
+                                               ctypes.byref(k)))
+        return float(ms.value), int(k.value)
 
     def launch_count(self):
         """Kernel launches this context queued since the last call (then cleared)."""
