@@ -948,7 +948,7 @@ static pt_status stage_args(pt_ctx* c, int64_t n, StageArgs& a) {
   else bytes += 2 * al(12 * nn);                      // xh, xl
   bytes += 3 * al(3 * rs * nn) + al(rs * nn);         // v, kx, kv, d
   bytes += al((f64 ? 24 : 24) * nn);                  // xe
-  bytes += f64 ? 0 : al(12 * nn);                     // guess
+  bytes += f64 ? 0 : al(12 * nn) + 2 * al(12 * nn);   // guess, converged xi (hi, lo)
   bytes += 4 * al(4 * nn) + 256;                      // e, hits, st, list, counters
   if (c->state_cap < n || !c->d_state) {
     if (c->d_state) cudaFree(c->d_state);
@@ -966,6 +966,7 @@ static pt_status stage_args(pt_ctx* c, int64_t n, StageArgs& a) {
   a.x = nullptr;
   a.xh = a.xl = nullptr;
   a.guess = nullptr;
+  a.xih = a.xil = nullptr;
   if (f64) {
     a.x = (double*)take(24 * nn);
   } else {
@@ -977,7 +978,11 @@ static pt_status stage_args(pt_ctx* c, int64_t n, StageArgs& a) {
   a.kv = take(3 * rs * nn);
   a.d = take(rs * nn);
   a.xe = take(24 * nn);
-  if (!f64) a.guess = (float*)take(12 * nn);
+  if (!f64) {
+    a.guess = (float*)take(12 * nn);
+    a.xih = (float*)take(12 * nn);
+    a.xil = (float*)take(12 * nn);
+  }
   a.e = (int*)take(4 * nn);
   a.hits = (int*)take(4 * nn);
   a.st = (unsigned*)take(4 * nn);

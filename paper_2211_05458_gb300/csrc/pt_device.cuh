@@ -13,12 +13,6 @@
 #include "pt_df.cuh"
 #include "pt_internal.h"
 
-// 1: evaluate the per-dimension Lagrange bases of the Newton residuals in a
-// rolled loop (one copy of the code, values through local memory), which
-// shrinks the hot loop's instruction footprint
-#ifndef PT_ROLL_BASIS
-#define PT_ROLL_BASIS 1
-#endif
 // 1: screen each touched face in FP32 before its exact FP64 solve
 #ifndef PT_FACE_SCREEN
 #define PT_FACE_SCREEN 1
@@ -39,6 +33,25 @@ __device__ __forceinline__ T tabs(T a) {
 template <typename T>
 __device__ __forceinline__ T tmax3(T a, T b, T c) {
   return fmax(fmax(tabs(a), tabs(b)), tabs(c));
+}
+
+// a[i] for a run-time i without indexing the array dynamically (which would
+// put it in local memory): a chain of selects over the unrolled indices
+template <int N, typename T>
+__device__ __forceinline__ T pick(const T* a, int i) {
+  T v = a[0];
+#pragma unroll
+  for (int j = 1; j < N; ++j)
+    if (j == i) v = a[j];
+  return v;
+}
+
+// a[i] = v for a run-time i, likewise
+template <int N, typename T>
+__device__ __forceinline__ void put(T* a, int i, T v) {
+#pragma unroll
+  for (int j = 0; j < N; ++j)
+    if (j == i) a[j] = v;
 }
 
 template <typename T>
@@ -184,11 +197,7 @@ __device__ __forceinline__ void map_j32(const float* __restrict__ X, const float
   constexpr int G3 = G * G * G;
   float lb[3][G], db[3][G];
   if (tm != 7) {
-#if PT_ROLL_BASIS
-#pragma unroll 1
-#else
 #pragma unroll
-#endif
     for (int d = 0; d < 3; ++d) lagr_d<G, float>(xi[d], k.gn32, k.gw32, lb[d], db[d]);
   }
   const float *l0 = lb[0], *d0 = db[0], *l1 = lb[1], *d1 = db[1], *l2 = lb[2], *d2 = db[2];
@@ -230,17 +239,21 @@ __device__ __forceinline__ void map_j32(const float* __restrict__ X, const float
           T1 = fmaf(s1, l1[b], T1);
           T2 = fmaf(sv, d1[b], T2);
         }
-        const float lc = l2[c], dc = d2[c];
+        const float lc = pick<G>(l2, c), dc = pick<G>(d2, c);
         cr = fmaf(T0, lc, cr);
         j0 = fmaf(T1, lc, j0);
         j1 = fmaf(T2, lc, j1);
         j2 = fmaf(T0, dc, j2);
       }
     }
-    chi[r] = cr;
-    J[3 * r] = j0;
-    J[3 * r + 1] = j1;
-    J[3 * r + 2] = j2;
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      if (q == r) {
+        chi[q] = cr;
+        J[3 * q] = j0;
+        J[3 * q + 1] = j1;
+        J[3 * q + 2] = j2;
+      }
   }
 }
 
@@ -363,11 +376,7 @@ __device__ __forceinline__ void resid_df(const float* __restrict__ Xh,
   constexpr int G3 = G * G * G;
   df lb[3][G];
   if (tm != 7) {
-#if PT_ROLL_BASIS
-#pragma unroll 1
-#else
 #pragma unroll
-#endif
     for (int d = 0; d < 3; ++d) lagr_df<G>(xi[d], k, lb[d]);
   }
   const df* l0 = lb[0];
@@ -418,11 +427,11 @@ __device__ __forceinline__ void resid_df(const float* __restrict__ Xh,
           for (int a = 0; a < G; ++a) dacc_fma(a1, df{rh[a], rl[a]}, l0[a]);
           dacc_fma(a2, dacc_result(a1), l1[b]);
         }
-        dacc_fma(a3, dacc_result(a2), l2[c]);
+        dacc_fma(a3, dacc_result(a2), pick<G>(l2, c));
       }
     }
-    const df rr = df_sub(dacc_result(a3), xloc[q]);
-    r[q] = __fadd_rn(rr.hi, rr.lo);
+    const df rr = df_sub(dacc_result(a3), pick<3>(xloc, q));
+    put<3>(r, q, __fadd_rn(rr.hi, rr.lo));
   }
 }
 
@@ -530,7 +539,7 @@ __device__ __forceinline__ void map_inc32(const float* __restrict__ X, const flo
       }
       acc = t1 + t2 + t3;
     }
-    dchi[q] = acc;
+    put<3>(dchi, q, acc);
   }
 }
 
@@ -698,9 +707,9 @@ __device__ __forceinline__ void interp4(const T* __restrict__ Ue, const T* l1, c
           t2 = tfma(t1, l2[j], t2);
         }
       }
-      acc = tfma(t2, l3[kk], acc);
+      acc = tfma(t2, pick<NP>(l3, kk), acc);
     }
-    out[v] = acc;
+    put<4>(out, v, acc);
   }
 }
 

@@ -168,6 +168,8 @@ struct StageArgs {
   int* hits;              // [n]
   unsigned* st;           // [n] status bits
   float* guess;           // [3][n] learned start (MLP) or null
+  float* xih;             // FP32 mode, split stage: [3][n] converged xi, double-float
+  float* xil;
   unsigned* list;         // [n] listed positions (| 1 << 31: walk only)
   unsigned* count;        // entries in list
   unsigned* count_next;   // the next stage's counter (cleared by this stage)

@@ -1366,6 +1366,12 @@ struct Family {
       case PT_SOP_STAGE:
         if constexpr (F64) {
           k_stage_f64<G, NP><<<grid, block, 0, s>>>(a);
+        } else if (PT_STAGE_SPLIT && !UStage<NP>::ok) {
+          if (kMlp && a.k.guess == PT_GUESS_MLP)
+            k_locate_f32<G, kMlp><<<grid, block, 0, s>>>(a);
+          else
+            k_locate_f32<G, false><<<grid, block, 0, s>>>(a);
+          k_advance_f32<G, NP><<<grid, block, 0, s>>>(a);
         } else {
           if (kMlp && a.k.guess == PT_GUESS_MLP)
             k_stage_f32<G, NP, kMlp><<<grid, block, 0, s>>>(a);
@@ -1420,10 +1426,16 @@ struct Family {
   template <int NP>
   static int occ_stage(int block) {
     int nb = 0;
-    if constexpr (F64)
+    if constexpr (F64) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage_f64<G, NP>, block, 0);
-    else
+    } else if (PT_STAGE_SPLIT && !UStage<NP>::ok) {
+      int nl = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_advance_f32<G, NP>, block, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nl, k_locate_f32<G, false>, block, 0);
+      nb = nb < nl ? nb : nl;
+    } else {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage_f32<G, NP, false>, block, 0);
+    }
     return nb;
   }
   static int staged_np(int np, int op, const StageArgs& a, const DevParticles& p, const int* perm,

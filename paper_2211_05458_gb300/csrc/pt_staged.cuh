@@ -34,6 +34,18 @@
 #ifndef PT_STAGE_U
 #define PT_STAGE_U 0
 #endif
+// 1: the FP32 stage runs as two kernels, k_locate_f32 (inverse map) and
+// k_advance_f32 (interpolation, drag, RK update, slab test); 0: one kernel,
+// k_stage_f32
+#ifndef PT_STAGE_SPLIT
+#define PT_STAGE_SPLIT 1
+#endif
+#ifndef PT_LOCATE_MINB
+#define PT_LOCATE_MINB 2
+#endif
+#ifndef PT_ADVANCE_MINB
+#define PT_ADVANCE_MINB 3
+#endif
 
 namespace pt {
 
@@ -222,6 +234,159 @@ __device__ __forceinline__ unsigned stage_one_f32(const StageArgs& a, int64_t t,
   a.st[t] = st;
   if (s == 4 && !list) ++c.steps;
   return list;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 mode, split stage: the inverse map and the rest of the stage in two
+// kernels, each with fewer live registers than the whole stage (the
+// converged xi goes through HBM as a double-float, 24 bytes)
+// ---------------------------------------------------------------------------
+
+template <int G, bool MLP>
+__global__ void __launch_bounds__(128, PT_LOCATE_MINB) k_locate_f32(const __grid_constant__ StageArgs a) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.count_next = 0u;
+  PushCounters c = {0, 0, 0, {0, 0, 0}};
+  Hist8 h32, h64;
+  const int64_t n = a.n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+    unsigned st = a.st[t];
+    if (st & PT_ST_FROZEN) continue;
+    const int e = a.e[t];
+    df xd[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) xd[r] = df{a.xh[r * n + t], a.xl[r * n + t]};
+    float guess[3];
+    if constexpr (MLP) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) guess[r] = a.guess[r * n + t];
+    } else {
+      const float xf[3] = {xd[0].hi, xd[1].hi, xd[2].hi};
+      trilinear_guess(a.m, e, xf, guess);
+    }
+    df zd[3];
+    int i32 = 0, i64 = 0;
+    const bool ok = newton_df<G>(a.m, a.k, e, xd, guess, zd, i32, i64);
+    c.it32 += i32;
+    c.it64 += i64;
+    h32.add(i32);
+    h64.add(i64);
+    if (!ok) {
+      a.st[t] = st | PT_ST_NEWTON_FAIL;
+      continue;
+    }
+    const float mx = tmax3(zd[0].hi + zd[0].lo, zd[1].hi + zd[1].lo, zd[2].hi + zd[2].lo);
+    if (mx > 1.f - fmaxf(1e-5f, (float)a.k.band_ref)) {  // decide the bands exactly (rare)
+      const double z[3] = {df_to_double(zd[0]), df_to_double(zd[1]), df_to_double(zd[2])};
+      const double md = tmax3(z[0], z[1], z[2]);
+      if (md > 1.0 + a.k.lost_tol) {  // outside: the walk after the last crossing ran already
+        a.st[t] = st | PT_ST_LOST;
+        continue;
+      }
+      if (md > 1.0 - a.k.band_ref) a.st[t] = st | near_bits(a.m, e, z, a.k.band_ref);
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      a.xih[r * n + t] = zd[r].hi;
+      a.xil[r * n + t] = zd[r].lo;
+    }
+  }
+  stage_counters(a, c);
+  h32.flush(a.stats, PT_C_H32, 8);
+  h64.flush(a.stats, PT_C_H64, 8);
+}
+
+// Interpolation, drag, RK update and slab test of every live particle from
+// the xi of k_locate_f32; returns 0, 1 (listed for exact tracking) or 2
+// (listed for the walk), as stage_one_f32.
+template <int G, int NP>
+__device__ __forceinline__ unsigned advance_one_f32(const StageArgs& a, int64_t t,
+                                                    PushCounters& c) {
+  constexpr int N3 = NP * NP * NP;
+  const int64_t n = a.n;
+  const int s = a.stage;
+  unsigned st = a.st[t];
+  if (st & PT_ST_FROZEN) return 0u;
+  const int e = a.e[t];
+  float* vg = reinterpret_cast<float*>(a.v);
+  float* kxg = reinterpret_cast<float*>(a.kx);
+  float* kvg = reinterpret_cast<float*>(a.kv);
+  const float d = reinterpret_cast<const float*>(a.d)[t];
+  df xd[3], zd[3];
+  float v[3], kx[3] = {0.f, 0.f, 0.f}, kv[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    xd[r] = df{a.xh[r * n + t], a.xl[r * n + t]};
+    zd[r] = df{a.xih[r * n + t], a.xil[r * n + t]};
+    v[r] = vg[r * n + t];
+    if (s > 0) {
+      kx[r] = kxg[r * n + t];
+      kv[r] = kvg[r * n + t];
+    }
+  }
+  const float mu = (float)a.k.mu;
+  const float tau = (float)a.k.rho_p * d * d / (18.f * mu);
+  const float xi[3] = {zd[0].hi + zd[0].lo, zd[1].hi + zd[1].lo, zd[2].hi + zd[2].lo};
+  const float* Ue = reinterpret_cast<const float*>(a.U) + (size_t)e * 5 * N3;
+  float l1[NP], l2[NP], l3[NP], Uv[4], acc[3];
+  lagr<NP, float>(xi[0], a.k.sn32, a.k.sw32, l1);
+  lagr<NP, float>(xi[1], a.k.sn32, a.k.sw32, l2);
+  lagr<NP, float>(xi[2], a.k.sn32, a.k.sw32, l3);
+  interp4<NP, float>(Ue, l1, l2, l3, Uv);
+  particle_accel_f32<G, NP>(a.m, a.k, Ue, e, zd, Uv, v, d, tau, st, acc);
+  const float As = a.k.A32[s], Bs = a.k.B32[s], dt = (float)a.dt;
+  const float xf[3] = {xd[0].hi, xd[1].hi, xd[2].hi};
+  df xe[3];
+  float bf[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    kx[r] = As * kx[r] + dt * v[r];
+    kv[r] = As * kv[r] + dt * acc[r];
+    xe[r] = df_add(xd[r], df_from(Bs * kx[r]));
+    bf[r] = xe[r].hi;
+    v[r] = v[r] + Bs * kv[r];
+  }
+  const int touch = slab_touch(a.m, e, xf, bf);
+  unsigned list = 0u;
+  if (!(touch & (a.k.track == PT_TRACK_REFERENCE ? 2 : 1))) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) xd[r] = xe[r];
+    if (touch) list = 2u;
+  } else {
+    float* xeg = reinterpret_cast<float*>(a.xe);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      xeg[r * n + t] = xe[r].hi;
+      xeg[(3 + r) * n + t] = xe[r].lo;
+    }
+    list = 1u;
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    a.xh[r * n + t] = xd[r].hi;
+    a.xl[r * n + t] = xd[r].lo;
+    vg[r * n + t] = v[r];
+    if (s < 4) {
+      kxg[r * n + t] = kx[r];
+      kvg[r * n + t] = kv[r];
+    }
+  }
+  a.st[t] = st;
+  if (s == 4 && !list) ++c.steps;
+  return list;
+}
+
+template <int G, int NP>
+__global__ void __launch_bounds__(128, PT_ADVANCE_MINB) k_advance_f32(const __grid_constant__ StageArgs a) {
+  PushCounters c = {0, 0, 0, {0, 0, 0}};
+  const int64_t n = a.n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nround = (n + stride - 1) / stride * stride;  // uniform trip count per warp
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nround; t += stride) {
+    const unsigned want = t < n ? advance_one_f32<G, NP>(a, t, c) : 0u;
+    list_append(a, t, want);
+  }
+  stage_counters(a, c);
 }
 
 // shared-memory slots of the element staging (at most 40 KB per block)
