@@ -310,9 +310,11 @@ def run_config(args):
     prec = pt.FP64 if f64 else pt.FP32
     dt_ = torch.float64 if f64 else torch.float32
     ctxs, parts = [], []
+    sched = {"auto": pt.SCHEDULE_AUTO, "resident": pt.SCHEDULE_RESIDENT,
+             "staged": pt.SCHEDULE_STAGED}[args.schedule]
     for wl in wls:
         c = pt.Context(wl.mesh, stream=stream, precision=prec, mu=wl.mu, rho_p=wl.rho_p,
-                       drag_law=wl.drag_law, rebin_every=args.inner)
+                       drag_law=wl.drag_law, rebin_every=args.inner, schedule=sched)
         c.set_fluid(wl.N, wl.node_type, wl.U.to(dt_).contiguous())
         ctxs.append(c)
         parts.append(pt.ParticleSet.create(wl.x, wl.v, wl.d, wl.elem, prec, dev))
@@ -401,6 +403,7 @@ def run_config(args):
             "vs_baseline": None,
             "dtype": "f64" if f64 else "f32", "data": "synthetic",
             "config": {"workload": names[cfg], "inner_steps_per_call": inner,
+                       "schedule": args.schedule,
                        "parallelism": (f"{world} GPU(s), boxes split by cost P (N+1)^3"
                                        if sharded else f"weak, {world} independent GPU(s)")},
             "gpu_launches": launches, "clocks": clk.summary(),

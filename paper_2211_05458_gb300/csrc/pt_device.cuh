@@ -13,6 +13,22 @@
 #include "pt_df.cuh"
 #include "pt_internal.h"
 
+// 1: evaluate the per-dimension Lagrange bases of the Newton residuals in a
+// rolled loop (one copy of the code, values through local memory), which
+// shrinks the hot loop's instruction footprint
+#ifndef PT_ROLL_BASIS
+#define PT_ROLL_BASIS 1
+#endif
+// 1: run-time indices into small register arrays of the interpolation
+// (PT_PICK_INTERP) and of the element map (PT_PICK_MAP) go through chains of
+// selects instead of dynamic indexing, which keeps the arrays out of local
+// memory at the cost of more live registers
+#ifndef PT_PICK_INTERP
+#define PT_PICK_INTERP 0
+#endif
+#ifndef PT_PICK_MAP
+#define PT_PICK_MAP 0
+#endif
 // 1: screen each touched face in FP32 before its exact FP64 solve
 #ifndef PT_FACE_SCREEN
 #define PT_FACE_SCREEN 1
@@ -197,7 +213,11 @@ __device__ __forceinline__ void map_j32(const float* __restrict__ X, const float
   constexpr int G3 = G * G * G;
   float lb[3][G], db[3][G];
   if (tm != 7) {
+#if PT_ROLL_BASIS
+#pragma unroll 1
+#else
 #pragma unroll
+#endif
     for (int d = 0; d < 3; ++d) lagr_d<G, float>(xi[d], k.gn32, k.gw32, lb[d], db[d]);
   }
   const float *l0 = lb[0], *d0 = db[0], *l1 = lb[1], *d1 = db[1], *l2 = lb[2], *d2 = db[2];
@@ -239,13 +259,18 @@ __device__ __forceinline__ void map_j32(const float* __restrict__ X, const float
           T1 = fmaf(s1, l1[b], T1);
           T2 = fmaf(sv, d1[b], T2);
         }
+#if PT_PICK_MAP
         const float lc = pick<G>(l2, c), dc = pick<G>(d2, c);
+#else
+        const float lc = l2[c], dc = d2[c];
+#endif
         cr = fmaf(T0, lc, cr);
         j0 = fmaf(T1, lc, j0);
         j1 = fmaf(T2, lc, j1);
         j2 = fmaf(T0, dc, j2);
       }
     }
+#if PT_PICK_MAP
 #pragma unroll
     for (int q = 0; q < 3; ++q)
       if (q == r) {
@@ -254,6 +279,12 @@ __device__ __forceinline__ void map_j32(const float* __restrict__ X, const float
         J[3 * q + 1] = j1;
         J[3 * q + 2] = j2;
       }
+#else
+    chi[r] = cr;
+    J[3 * r] = j0;
+    J[3 * r + 1] = j1;
+    J[3 * r + 2] = j2;
+#endif
   }
 }
 
@@ -376,7 +407,11 @@ __device__ __forceinline__ void resid_df(const float* __restrict__ Xh,
   constexpr int G3 = G * G * G;
   df lb[3][G];
   if (tm != 7) {
+#if PT_ROLL_BASIS
+#pragma unroll 1
+#else
 #pragma unroll
+#endif
     for (int d = 0; d < 3; ++d) lagr_df<G>(xi[d], k, lb[d]);
   }
   const df* l0 = lb[0];
@@ -427,11 +462,19 @@ __device__ __forceinline__ void resid_df(const float* __restrict__ Xh,
           for (int a = 0; a < G; ++a) dacc_fma(a1, df{rh[a], rl[a]}, l0[a]);
           dacc_fma(a2, dacc_result(a1), l1[b]);
         }
+#if PT_PICK_MAP
         dacc_fma(a3, dacc_result(a2), pick<G>(l2, c));
       }
     }
     const df rr = df_sub(dacc_result(a3), pick<3>(xloc, q));
     put<3>(r, q, __fadd_rn(rr.hi, rr.lo));
+#else
+        dacc_fma(a3, dacc_result(a2), l2[c]);
+      }
+    }
+    const df rr = df_sub(dacc_result(a3), xloc[q]);
+    r[q] = __fadd_rn(rr.hi, rr.lo);
+#endif
   }
 }
 
@@ -539,7 +582,11 @@ __device__ __forceinline__ void map_inc32(const float* __restrict__ X, const flo
       }
       acc = t1 + t2 + t3;
     }
+#if PT_PICK_MAP
     put<3>(dchi, q, acc);
+#else
+    dchi[q] = acc;
+#endif
   }
 }
 
@@ -707,9 +754,15 @@ __device__ __forceinline__ void interp4(const T* __restrict__ Ue, const T* l1, c
           t2 = tfma(t1, l2[j], t2);
         }
       }
+#if PT_PICK_INTERP
       acc = tfma(t2, pick<NP>(l3, kk), acc);
     }
     put<4>(out, v, acc);
+#else
+      acc = tfma(t2, l3[kk], acc);
+    }
+    out[v] = acc;
+#endif
   }
 }
 

@@ -38,10 +38,10 @@
 // k_advance_f32 (interpolation, drag, RK update, slab test); 0: one kernel,
 // k_stage_f32
 #ifndef PT_STAGE_SPLIT
-#define PT_STAGE_SPLIT 1
+#define PT_STAGE_SPLIT 0
 #endif
 #ifndef PT_LOCATE_MINB
-#define PT_LOCATE_MINB 2
+#define PT_LOCATE_MINB 3
 #endif
 #ifndef PT_ADVANCE_MINB
 #define PT_ADVANCE_MINB 3
