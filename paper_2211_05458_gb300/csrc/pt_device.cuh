@@ -698,10 +698,57 @@ __device__ __forceinline__ bool newton_mixed(const DevMesh& m, const DevConsts& 
 // interpolation of rho and rho u (Eq. part_interpolation), sum-factorised
 // ---------------------------------------------------------------------------
 
+#ifndef PT_INTERP_V2
+#define PT_INTERP_V2 0
+#endif
 template <int NP, typename T>
 __device__ __forceinline__ void interp4(const T* __restrict__ Ue, const T* l1, const T* l2,
                                         const T* l3, T* out) {
   constexpr int N3 = NP * NP * NP;
+#if PT_INTERP_V2
+  // two variables per pass: their row loads are independent, which doubles
+  // the loads in flight per iteration
+  if constexpr (std::is_same<T, float>::value && NP == 6) {
+#pragma unroll 1
+    for (int v = 0; v < 4; v += 2) {
+      const float* Ua = Ue + v * N3;
+      const float* Ub = Ua + N3;
+      float acca = 0.f, accb = 0.f;
+#pragma unroll 1
+      for (int kk = 0; kk < NP; ++kk) {
+        float ta = 0.f, tb = 0.f;
+#pragma unroll
+        for (int j = 0; j < NP; j += 2) {
+          const float4* qa = reinterpret_cast<const float4*>(Ua + NP * (j + NP * kk));
+          const float4* qb = reinterpret_cast<const float4*>(Ub + NP * (j + NP * kk));
+          const float4 a0 = __ldg(qa), a1 = __ldg(qa + 1), a2 = __ldg(qa + 2);
+          const float4 b0 = __ldg(qb), b1 = __ldg(qb + 1), b2 = __ldg(qb + 2);
+          const float ra0[6] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y};
+          const float ra1[6] = {a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
+          const float rb0[6] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y};
+          const float rb1[6] = {b1.z, b1.w, b2.x, b2.y, b2.z, b2.w};
+          float sa0 = 0.f, sa1 = 0.f, sb0 = 0.f, sb1 = 0.f;
+#pragma unroll
+          for (int i = 0; i < NP; ++i) {
+            sa0 = fmaf(ra0[i], l1[i], sa0);
+            sa1 = fmaf(ra1[i], l1[i], sa1);
+            sb0 = fmaf(rb0[i], l1[i], sb0);
+            sb1 = fmaf(rb1[i], l1[i], sb1);
+          }
+          ta = fmaf(sa0, l2[j], ta);
+          ta = fmaf(sa1, l2[j + 1], ta);
+          tb = fmaf(sb0, l2[j], tb);
+          tb = fmaf(sb1, l2[j + 1], tb);
+        }
+        acca = fmaf(ta, l3[kk], acca);
+        accb = fmaf(tb, l3[kk], accb);
+      }
+      out[v] = acca;
+      out[v + 1] = accb;
+    }
+    return;
+  }
+#endif
   // FP32 rows of 6 nodes: two rows (48 bytes, 16-byte aligned at even rows
   // since every variable block is a multiple of 16 bytes) in three 16-byte
   // loads; rows of 4 or 8 nodes in 16-byte loads
