@@ -266,6 +266,24 @@ pt_status pt_set_fluid(pt_ctx* ctx, int32_t N, int32_t node_type, const void* U_
 pt_status pt_push(pt_ctx* ctx, const pt_particles* p, int32_t nsteps, double dt,
                   pt_stats* out);
 
+/* One RK stage for a solver that advances the fluid and the particles stage
+ * by stage together (Sec. 3.2.2: the particles use the fluid's RK scheme,
+ * each stage interpolating the fluid state of that stage).  Call with
+ * stage = 0, 1, 2, 3, 4 in turn, the same particle arrays and dt, updating
+ * the fluid state registered by pt_set_fluid (in place or by another
+ * pt_set_fluid with the same N) between the calls.  Stage 0 bins the
+ * particles and copies them into library-owned device buffers (the staged
+ * schedule's state); stages 0..4 each run the inverse map, interpolation,
+ * drag, RK stage and tracking on that state; stage 4 copies the state back
+ * into the caller's arrays, which hold the step's start state until then.
+ * With a fluid state that does not change, the five calls give bitwise the
+ * result of pt_push with nsteps = 1 in the staged schedule.  out: as pt_push,
+ * read at stage 4 (NULL otherwise).  PT_ERR_STATE for a stage out of order;
+ * PT_ERR_ARG for other particle arrays or another dt than at stage 0;
+ * pt_push and pt_deposit return PT_ERR_STATE while a sequence is open. */
+pt_status pt_push_stage(pt_ctx* ctx, const pt_particles* p, int32_t stage, double dt,
+                        pt_stats* out);
+
 /* As pt_push, but the particle arrays are HOST memory (same layout); the
  * library stages them through its own device buffers, copies the results
  * back and synchronises.  Intended for callers without device buffers. */
@@ -424,7 +442,7 @@ pt_status pt_profile(pt_ctx* ctx, int32_t enable);
 pt_status pt_profile_read(pt_ctx* ctx, double* kernel_ms, int64_t* launches);
 /* As pt_profile_read for one kind of kernel, clearing only that record:
  * kind 0 the push (the resident kernel, or a whole chunk of the staged
- * schedule from its sorted copy to the copy back), 1 the staged schedule's
+ * schedule from its binning to the copy back), 1 the staged schedule's
  * stage kernels, 2 its learned-start kernels, 3 its exact-tracking kernels.
  * (pt_profile_read reads kind 0 and clears all four.) */
 pt_status pt_profile_read_kind(pt_ctx* ctx, int32_t kind, double* kernel_ms, int64_t* launches);

@@ -995,12 +995,20 @@ static pt_status stage_args(pt_ctx* c, int64_t n, StageArgs& a) {
 // The staged schedule: per chunk of rebin_every steps, binning, the sorted
 // copy of the particle state, per RK stage (the learned start,) the stage
 // kernel and the exact-tracking kernel over its list, and the copy back.
-static pt_status push_staged(pt_ctx* c, const pt_particles* p, int32_t nsteps, double dt) {
+// Launch shapes of the staged schedule for n particles.
+struct StagedLaunch {
+  bool f64 = false, mlp = false;
+  int np = 0, grid = 1, block = 128, gmove = 1, gtrack = 1, gguess = 1;
+  DevParticles dp{};
+  unsigned* ctr = nullptr;  // two list counters, used by alternate stages
+};
+
+static pt_status staged_prepare(pt_ctx* c, const pt_particles* p, double dt, StageArgs& a,
+                                StagedLaunch& L) {
   const int64_t n = p->n;
-  const bool f64 = c->cfg.precision == PT_FP64;
-  const bool mlp = !f64 && c->cfg.guess == PT_GUESS_MLP;
-  const int np = c->N + 1;
-  StageArgs a;
+  L.f64 = c->cfg.precision == PT_FP64;
+  L.mlp = !L.f64 && c->cfg.guess == PT_GUESS_MLP;
+  L.np = c->N + 1;
   pt_status s = stage_args(c, n, a);
   if (s) return s;
   a.m = dev_mesh(c);
@@ -1010,53 +1018,78 @@ static pt_status push_staged(pt_ctx* c, const pt_particles* p, int32_t nsteps, d
   a.n = n;
   a.dt = dt;
   a.stats = c->d_stats;
-  const DevParticles dp = {n, p->x, p->v, p->d, p->elem, p->hits, p->status};
-  const int block = 128;
-  const int occ = max_active_stage(c->g, f64, np, block);
-  const int grid = grid_for(c, n, block, occ);
-  const int gmove = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)c->nsm * 8));
-  const int gtrack = c->nsm * 4;
-  const int gguess = (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, (int64_t)c->nsm * 4));
-  unsigned* const ctr = a.count;  // two list counters, used by alternate stages
-  CK(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), c->stream));
+  L.dp = {n, p->x, p->v, p->d, p->elem, p->hits, p->status};
+  const int occ = max_active_stage(c->g, L.f64, L.np, L.block);
+  L.grid = grid_for(c, n, L.block, occ);
+  L.gmove = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)c->nsm * 8));
+  L.gtrack = c->nsm * 4;
+  L.gguess = (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, (int64_t)c->nsm * 4));
+  L.ctr = a.count;
+  return PT_OK;
+}
+
+// binning and the sorted copy of the caller's particles
+static int staged_begin(pt_ctx* c, const pt_particles* p, StageArgs& a, const StagedLaunch& L) {
+  int rc = bin_by_element(p->elem, p->n, c->nelem, c->d_scratch, c->d_perm, nullptr, c->nsm,
+                          c->stream);
+  c->launches += 5;
+  if (!rc) rc = launch_staged(c->g, L.f64, L.np, PT_SOP_GATHER, a, L.dp, c->d_perm, L.gmove, 256,
+                              c->stream);
+  c->launches += 1;
+  return rc;
+}
+
+// RK stage st (k: running stage count, which selects the list counter)
+static int staged_stage(pt_ctx* c, StageArgs& a, const StagedLaunch& L, int st, int k) {
+  a.stage = st;
+  a.count = L.ctr + (k & 1);
+  a.count_next = L.ctr + ((k + 1) & 1);
+  // each kernel between an event pair of its kind when profiling
+  auto timed = [&](int kind, int op, int g, int b) {
+    cudaEvent_t q0 = c->profile ? take_event(c, kind) : nullptr;
+    cudaEvent_t q1 = c->profile ? take_event(c, kind) : nullptr;
+    if (q0) cudaEventRecord(q0, c->stream);
+    const int r = launch_staged(c->g, L.f64, L.np, op, a, L.dp, c->d_perm, g, b, c->stream);
+    if (q1) cudaEventRecord(q1, c->stream);
+    c->launches += 1;
+    return r;
+  };
+  int rc = 0;
+  if (L.mlp) rc = timed(2, PT_SOP_GUESS, L.gguess, 128);
+  if (!rc) rc = timed(1, PT_SOP_STAGE, L.grid, L.block);
+  if (!rc) rc = timed(3, PT_SOP_TRACK, L.gtrack, 128);
+  return rc;
+}
+
+static int staged_end(pt_ctx* c, StageArgs& a, const StagedLaunch& L) {
+  c->launches += 1;
+  return launch_staged(c->g, L.f64, L.np, PT_SOP_SCATTER, a, L.dp, c->d_perm, L.gmove, 256,
+                       c->stream);
+}
+
+// The staged schedule: per chunk of rebin_every steps, binning, the sorted
+// copy of the particle state, per RK stage (the learned start,) the stage
+// kernel and the exact-tracking kernel over its list, and the copy back.
+static pt_status push_staged(pt_ctx* c, const pt_particles* p, int32_t nsteps, double dt) {
+  StageArgs a;
+  StagedLaunch L;
+  pt_status s = staged_prepare(c, p, dt, a, L);
+  if (s) return s;
+  CK(cudaMemsetAsync(L.ctr, 0, 2 * sizeof(unsigned), c->stream));
   const int chunk = c->cfg.rebin_every > 0 ? c->cfg.rebin_every : 10;
   int k = 0;
   for (int s0 = 0; s0 < nsteps; s0 += chunk) {
-    int rc = bin_by_element(p->elem, n, c->nelem, c->d_scratch, c->d_perm, nullptr, c->nsm,
-                            c->stream);
-    if (rc) return fail(c, PT_ERR_CUDA, "binning: %s", cudaGetErrorString((cudaError_t)rc));
-    c->launches += 5;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (c->profile) {
       e0 = take_event(c);
       e1 = take_event(c);
-      if (e0) cudaEventRecord(e0, c->stream);
     }
-    rc = launch_staged(c->g, f64, np, PT_SOP_GATHER, a, dp, c->d_perm, gmove, 256, c->stream);
+    if (e0) cudaEventRecord(e0, c->stream);
+    int rc = staged_begin(c, p, a, L);
     const int ns = std::min(chunk, nsteps - s0);
-    for (int step = 0; step < ns && !rc; ++step) {
-      for (int st = 0; st < 5 && !rc; ++st, ++k) {
-        a.stage = st;
-        a.count = ctr + (k & 1);
-        a.count_next = ctr + ((k + 1) & 1);
-        // each kernel between an event pair of its kind when profiling
-        auto timed = [&](int kind, int op, int g, int b) {
-          cudaEvent_t q0 = c->profile ? take_event(c, kind) : nullptr;
-          cudaEvent_t q1 = c->profile ? take_event(c, kind) : nullptr;
-          if (q0) cudaEventRecord(q0, c->stream);
-          const int r = launch_staged(c->g, f64, np, op, a, dp, c->d_perm, g, b, c->stream);
-          if (q1) cudaEventRecord(q1, c->stream);
-          c->launches += 1;
-          return r;
-        };
-        if (mlp) rc = timed(2, PT_SOP_GUESS, gguess, 128);
-        if (!rc) rc = timed(1, PT_SOP_STAGE, grid, block);
-        if (!rc) rc = timed(3, PT_SOP_TRACK, gtrack, 128);
-      }
-    }
-    if (!rc) rc = launch_staged(c->g, f64, np, PT_SOP_SCATTER, a, dp, c->d_perm, gmove, 256,
-                                c->stream);
-    c->launches += 2;
+    for (int step = 0; step < ns && !rc; ++step)
+      for (int st = 0; st < 5 && !rc; ++st, ++k) rc = staged_stage(c, a, L, st, k);
+    if (!rc) rc = staged_end(c, a, L);
     if (e1) cudaEventRecord(e1, c->stream);
     if (rc) return fail(c, PT_ERR_CUDA, "staged push launch: %s",
                         cudaGetErrorString((cudaError_t)rc));
@@ -1126,7 +1159,54 @@ pt_status pt_push(pt_ctx* c, const pt_particles* p, int32_t nsteps, double dt, p
     return fail(c, PT_ERR_STATE, "learned guess needs ngeo = 3 and a trained network");
   if (c->cfg.guess == PT_GUESS_MLP && push_block(c) > 128)
     return fail(c, PT_ERR_ARG, "the learned guess needs a push block of at most 128 threads");
+  if (c->stage_next != 0)
+    return fail(c, PT_ERR_STATE, "a pt_push_stage sequence is open (stage %d expected)",
+                c->stage_next);
   return pt_push_impl(c, p, nsteps, dt, out);
+}
+
+pt_status pt_push_stage(pt_ctx* c, const pt_particles* p, int32_t stage, double dt,
+                        pt_stats* out) {
+  if (!c) return fail(nullptr, PT_ERR_ARG, "ctx is NULL");
+  if (c->N < 0 || !c->U) return fail(c, PT_ERR_STATE, "pt_set_fluid was not called");
+  pt_status s = validate_particles(c, p);
+  if (s) return s;
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(c, PT_ERR_ARG, "dt must be finite and > 0");
+  if (stage < 0 || stage > 4) return fail(c, PT_ERR_ARG, "stage must be 0..4");
+  if (stage != c->stage_next)
+    return fail(c, PT_ERR_STATE, "pt_push_stage: stage %d expected, %d given", c->stage_next, stage);
+  if (stage > 0 && (std::memcmp(&c->stage_p, p, sizeof *p) != 0 || dt != c->stage_dt))
+    return fail(c, PT_ERR_ARG, "pt_push_stage: the particles and dt of stage 0 are required");
+  if (c->cfg.guess == PT_GUESS_MLP && (c->g != 4 || !c->mlp_ready))
+    return fail(c, PT_ERR_STATE, "learned guess needs ngeo = 3 and a trained network");
+  const int64_t n = p->n;
+  StageArgs a;
+  StagedLaunch L;
+  if (stage == 0) {
+    CK(cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * PT_C_COUNT, c->stream));
+    s = ensure_scratch(c, std::max<int64_t>(n, 1));
+    if (s) return s;
+  }
+  s = staged_prepare(c, p, dt, a, L);
+  if (s) return s;
+  int rc = 0;
+  if (n > 0) {
+    if (stage == 0) {
+      CK(cudaMemsetAsync(L.ctr, 0, 2 * sizeof(unsigned), c->stream));
+      rc = staged_begin(c, p, a, L);
+    }
+    if (!rc) rc = staged_stage(c, a, L, stage, stage);
+    if (!rc && stage == 4) rc = staged_end(c, a, L);
+    if (rc) {
+      c->stage_next = 0;
+      return fail(c, PT_ERR_CUDA, "pt_push_stage launch: %s", cudaGetErrorString((cudaError_t)rc));
+    }
+  }
+  c->stage_p = *p;
+  c->stage_dt = dt;
+  c->stage_next = (stage + 1) % 5;
+  if (stage == 4 && out) return read_stats(c, p, dt, out);
+  return PT_OK;
 }
 
 pt_status pt_push_host(pt_ctx* c, const pt_particles* h, int32_t nsteps, double dt,
@@ -1271,6 +1351,9 @@ pt_status pt_deposit(pt_ctx* c, const pt_particles* p, int32_t mode, float* S) {
                 "mode must be PT_DEPOSIT_ATOMIC or PT_DEPOSIT_SEGMENTED, optionally | "
                 "PT_DEPOSIT_NEAREST");
   if (!S) return fail(c, PT_ERR_ARG, "S is NULL");
+  if (c->stage_next != 0)
+    return fail(c, PT_ERR_STATE, "a pt_push_stage sequence is open (stage %d expected)",
+                c->stage_next);
   const int np = c->N + 1;
   const size_t n3 = (size_t)np * np * np;
   const int64_t n = p->n;

@@ -66,6 +66,11 @@ struct pt_ctx {
   // particle state of the staged schedule (sorted order), grown on demand
   void* d_state = nullptr;
   int64_t state_cap = 0;
+  // pt_push_stage: the next stage expected (0: none open), the particles and
+  // time step of the open sequence
+  int stage_next = 0;
+  pt_particles stage_p{};
+  double stage_dt = 0.0;
   // kernels queued since the last pt_launch_count
   int64_t launches = 0;
   // kernel timing (pt_profile)

@@ -29,6 +29,13 @@
 #ifndef PT_PICK_MAP
 #define PT_PICK_MAP 0
 #endif
+// FP32 Newton iterations of the FP32 mode stop once the step is below this;
+// the final iterations (double-float residuals, last FP32 inverse Jacobian)
+// take over and converge linearly with a factor of about the step at which
+// that Jacobian was evaluated
+#ifndef PT_NEWTON_SWITCH
+#define PT_NEWTON_SWITCH 1e-5f
+#endif
 // 1: screen each touched face in FP32 before its exact FP64 solve
 #ifndef PT_FACE_SCREEN
 #define PT_FACE_SCREEN 1
@@ -628,7 +635,7 @@ __device__ __forceinline__ bool newton_df(const DevMesh& m, const DevConsts& k, 
       have = false;
       break;
     }
-    if (tmax3(d[0], d[1], d[2]) < 1e-5f) break;
+    if (tmax3(d[0], d[1], d[2]) < PT_NEWTON_SWITCH) break;
   }
   if (have) {
 #pragma unroll
@@ -698,8 +705,10 @@ __device__ __forceinline__ bool newton_mixed(const DevMesh& m, const DevConsts& 
 // interpolation of rho and rho u (Eq. part_interpolation), sum-factorised
 // ---------------------------------------------------------------------------
 
+// 1: the FP32 interpolation at N = 5 takes two variables per pass (their row
+// loads independent: twice the loads in flight; +5 % at the 64^3 workload)
 #ifndef PT_INTERP_V2
-#define PT_INTERP_V2 0
+#define PT_INTERP_V2 1
 #endif
 template <int NP, typename T>
 __device__ __forceinline__ void interp4(const T* __restrict__ Ue, const T* l1, const T* l2,

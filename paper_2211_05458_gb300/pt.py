@@ -80,7 +80,7 @@ EXPORTS = ["pt_config_default", "pt_init_mesh", "pt_set_config", "pt_set_fluid",
            "pt_mlp_grad", "pt_push_batch", "pt_profile", "pt_profile_read", "pt_destroy",
            "pt_last_error", "pt_deposit_noalloc", "pt_find_element", "pt_stage_terms",
            "pt_launch_count", "pt_measure_peak", "pt_mlp_start", "pt_read_histograms",
-           "pt_batch_tuning", "pt_profile_read_kind"]
+           "pt_batch_tuning", "pt_profile_read_kind", "pt_push_stage"]
 
 
 def library_path() -> str:
@@ -106,6 +106,7 @@ def lib():
             L.pt_push.argtypes = [_vp, ctypes.POINTER(CParticles), ctypes.c_int32, ctypes.c_double,
                                   ctypes.POINTER(Stats)]
             L.pt_push_host.argtypes = L.pt_push.argtypes
+            L.pt_push_stage.argtypes = L.pt_push.argtypes
             L.pt_deposit.argtypes = [_vp, ctypes.POINTER(CParticles), ctypes.c_int32, _vp]
             L.pt_deposit_noalloc.argtypes = [_vp, ctypes.POINTER(CParticles), ctypes.c_int32,
                                              _vp]
@@ -292,6 +293,16 @@ class Context:
         out = st.as_dict()
         out["status_code"] = rc
         return out
+
+    def push_stage(self, parts: ParticleSet, stage: int, dt: float, stats: bool = False):
+        """One RK stage (0..4 in turn) for a solver that updates the fluid state
+        between stages; the particle arrays are updated at stage 4."""
+        st = Stats() if stats else None
+        p = parts.struct()
+        rc = lib().pt_push_stage(self.h, ctypes.byref(p), int(stage), float(dt),
+                                 ctypes.byref(st) if st is not None else None)
+        self._check(rc, (PT_OK, PT_WARN_DT, PT_ERR_NEWTON, PT_ERR_LOST, PT_ERR_CROSS))
+        return st.as_dict() if st is not None else None
 
     def push_host(self, parts: ParticleSet, nsteps: int, dt: float, stats: bool = True):
         st = Stats() if stats else None

@@ -152,3 +152,51 @@ def test_histograms_count_every_particle_stage():
     assert sum(k * c for k, c in enumerate(hist["crossings"][:3])) + 3 * hist["crossings"][3] \
         <= st["crossings"]
     print("histograms", hist)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_push_stage_sequence_equals_one_step_push(precision):
+    """pt_push_stage(0..4) with an unchanged fluid state gives bitwise the
+    result of pt_push(nsteps = 1) in the staged schedule; a fluid state that
+    changes between stages changes the result; calls out of order and other
+    pushes while a sequence is open are refused."""
+    wl = W.curved_channel((6, 6, 6), 3, 5, P=2000, nsteps=1, dt=2e-3, seed=8)
+    _speed_up(wl, 8)
+    h = 2.0 / 6
+    band = dict(band_ref=2e-4, band_x=1e-4 * h) if precision == "fp32" else {}
+    ctx = H.gpu_context(wl, precision, schedule=pt.SCHEDULE_STAGED, **band)
+    one = H.gpu_particles(wl, ctx)
+    st1 = ctx.push(one, 1, wl.dt)
+    stg = H.gpu_particles(wl, ctx)
+    x0 = stg.x.clone()
+    for s in range(5):
+        st = ctx.push_stage(stg, s, wl.dt, stats=(s == 4))
+        if s < 4:
+            assert torch.equal(stg.x, x0)  # the caller's arrays change at stage 4
+    torch.cuda.synchronize()
+    a, b = H.gpu_result(one), H.gpu_result(stg)
+    for k in FIELDS:
+        assert np.array_equal(a[k], b[k]), k
+    assert st["particle_steps"] == st1["particle_steps"] and st["crossings"] == st1["crossings"]
+    # the fluid state read at every stage: scaling it after stage 2 changes the result
+    ctx2 = H.gpu_context(wl, precision, schedule=pt.SCHEDULE_STAGED, **band)
+    U = wl.U.to("cuda", torch.float64 if precision == "fp64" else torch.float32).contiguous()
+    ctx2.set_fluid(wl.N, wl.node_type, U)
+    chg = H.gpu_particles(wl, ctx2)
+    for s in range(5):
+        if s == 3:
+            U[:, 1:4] *= 1.5  # in place: the registered array
+        ctx2.push_stage(chg, s, wl.dt)
+    torch.cuda.synchronize()
+    assert not torch.equal(chg.v, stg.v)
+    # order and exclusivity
+    with pytest.raises(pt.PtError):
+        ctx2.push_stage(chg, 2, wl.dt)
+    ctx2.push_stage(chg, 0, wl.dt)
+    with pytest.raises(pt.PtError):
+        ctx2.push(chg, 1, wl.dt)
+    with pytest.raises(pt.PtError):
+        ctx2.deposit(chg, pt.DEPOSIT_ATOMIC)
+    for s in range(1, 5):
+        ctx2.push_stage(chg, s, wl.dt)
+    ctx2.push(chg, 1, wl.dt)
