@@ -704,6 +704,17 @@ def main():
             "value": P * 10 / (e0.elapsed_time(e1) / 1e3), "unit": METRIC,
             "note": "same push, pt_push(nsteps = 1) per time step (fluid state updated by the "
                     "caller between calls); the default run uses 10 steps per call"}
+        # a solver that advances fluid and particles stage by stage together
+        e0.record(stream)
+        for _ in range(10):
+            for s_ in range(5):
+                ctx.push_stage(pc, s_, wl.dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        line["coupled_per_stage_calls"] = {
+            "value": P * 10 / (e0.elapsed_time(e1) / 1e3), "unit": METRIC,
+            "note": "same push, pt_push_stage(0..4) per time step (fluid state updated by the "
+                    "caller between RK stages)"}
         del pc
     if not args.no_extras and rank == 0 and "e2e" in legs:
         # e2e: same metric through pt_push_host with pinned host buffers
