@@ -214,20 +214,44 @@ __device__ __forceinline__ int corner_node(int q) {
 
 // FP32, nodes coordinate-major [3][G^3]; chi and Jacobian J[r][q] = d chi_r / d xi_q.
 // Coordinates flagged in tm are trilinear in xi: their 8-corner form is used.
-template <int G>
+// Per-thread scratch for the per-dimension bases: SS = 0 keeps them in a
+// local array (computed in a rolled loop, read through local memory); SS > 0
+// puts them in shared memory at sb[row * SS] (sb: this thread's column of a
+// [rows][SS] block array), which keeps local memory out of the L1 cache.
+template <int SS>
+struct BasisStore {
+  float* sb;
+  float loc[SS > 0 ? 1 : 6 * PT_MAXG];
+  __device__ __forceinline__ float* row(int r) { return SS > 0 ? sb + r * SS : loc + r; }
+  __device__ __forceinline__ float get(int r) const { return SS > 0 ? sb[r * SS] : loc[r]; }
+};
+
+template <int G, int SS = 0>
 __device__ __forceinline__ void map_j32(const float* __restrict__ X, const float* xi, int tm,
-                                        const DevConsts& k, float* chi, float* J) {
+                                        const DevConsts& k, float* chi, float* J,
+                                        float* sb = nullptr) {
   constexpr int G3 = G * G * G;
-  float lb[3][G], db[3][G];
+  // rows d G + i: l_i(xi_d); rows (3 + d) G + i: l_i'(xi_d)
+  BasisStore<SS> bs;
+  bs.sb = sb;
   if (tm != 7) {
 #if PT_ROLL_BASIS
 #pragma unroll 1
 #else
 #pragma unroll
 #endif
-    for (int d = 0; d < 3; ++d) lagr_d<G, float>(xi[d], k.gn32, k.gw32, lb[d], db[d]);
+    for (int d = 0; d < 3; ++d) {
+      float l[G], dl[G];
+      lagr_d<G, float>(xi[d], k.gn32, k.gw32, l, dl);
+#pragma unroll
+      for (int i = 0; i < G; ++i) {
+        *bs.row(d * G + i) = l[i];
+        *bs.row((3 + d) * G + i) = dl[i];
+      }
+    }
   }
-  const float *l0 = lb[0], *d0 = db[0], *l1 = lb[1], *d1 = db[1], *l2 = lb[2], *d2 = db[2];
+#define PT_L(d, i) bs.get((d) * G + (i))
+#define PT_D(d, i) bs.get((3 + (d)) * G + (i))
   const float hp[3] = {0.5f * (1.f + xi[0]), 0.5f * (1.f + xi[1]), 0.5f * (1.f + xi[2])};
   const float hm[3] = {0.5f * (1.f - xi[0]), 0.5f * (1.f - xi[1]), 0.5f * (1.f - xi[2])};
   // one coordinate at a time; the loops over c and r stay rolled so that the
@@ -259,18 +283,14 @@ __device__ __forceinline__ void map_j32(const float* __restrict__ X, const float
           load_row<G>(Xr + G * (b + G * c), row);
 #pragma unroll
           for (int a = 0; a < G; ++a) {
-            sv = fmaf(row[a], l0[a], sv);
-            s1 = fmaf(row[a], d0[a], s1);
+            sv = fmaf(row[a], PT_L(0, a), sv);
+            s1 = fmaf(row[a], PT_D(0, a), s1);
           }
-          T0 = fmaf(sv, l1[b], T0);
-          T1 = fmaf(s1, l1[b], T1);
-          T2 = fmaf(sv, d1[b], T2);
+          T0 = fmaf(sv, PT_L(1, b), T0);
+          T1 = fmaf(s1, PT_L(1, b), T1);
+          T2 = fmaf(sv, PT_D(1, b), T2);
         }
-#if PT_PICK_MAP
-        const float lc = pick<G>(l2, c), dc = pick<G>(d2, c);
-#else
-        const float lc = l2[c], dc = d2[c];
-#endif
+        const float lc = PT_L(2, c), dc = PT_D(2, c);
         cr = fmaf(T0, lc, cr);
         j0 = fmaf(T1, lc, j0);
         j1 = fmaf(T2, lc, j1);
@@ -294,6 +314,8 @@ __device__ __forceinline__ void map_j32(const float* __restrict__ X, const float
 #endif
   }
 }
+#undef PT_L
+#undef PT_D
 
 // FP64, nodes point-major [G^3][3]; with WJ also the Jacobian
 template <int G, bool WJ>
@@ -407,23 +429,32 @@ __device__ __forceinline__ void lagr_df(df x, const DevConsts& k, df* l) {
 // Residual chi(xi) - x of the element map in double-float, sum-factorised;
 // nodes as hi [3][G^3] + lo [3][G^3] (relative to the element centre);
 // coordinates flagged in tm use the 8-corner trilinear form.
-template <int G>
+template <int G, int SS = 0>
 __device__ __forceinline__ void resid_df(const float* __restrict__ Xh,
                                          const float* __restrict__ Xl, const df* xi, int tm,
-                                         const df* xloc, const DevConsts& k, float* r) {
+                                         const df* xloc, const DevConsts& k, float* r,
+                                         float* sb = nullptr) {
   constexpr int G3 = G * G * G;
-  df lb[3][G];
+  // rows d G + i: high part of l_i(xi_d); rows (3 + d) G + i: low part
+  BasisStore<SS> bs;
+  bs.sb = sb;
   if (tm != 7) {
 #if PT_ROLL_BASIS
 #pragma unroll 1
 #else
 #pragma unroll
 #endif
-    for (int d = 0; d < 3; ++d) lagr_df<G>(xi[d], k, lb[d]);
+    for (int d = 0; d < 3; ++d) {
+      df l[G];
+      lagr_df<G>(xi[d], k, l);
+#pragma unroll
+      for (int i = 0; i < G; ++i) {
+        *bs.row(d * G + i) = l[i].hi;
+        *bs.row((3 + d) * G + i) = l[i].lo;
+      }
+    }
   }
-  const df* l0 = lb[0];
-  const df* l1 = lb[1];
-  const df* l2 = lb[2];
+#define PT_LDF(d, i) df{bs.get((d) * G + (i)), bs.get((3 + (d)) * G + (i))}
   df w8[8];
   if (tm != 0) {
     df hp[3], hm[3];
@@ -466,23 +497,21 @@ __device__ __forceinline__ void resid_df(const float* __restrict__ Xh,
           load_row<G>(Ph + G * (b + G * c), rh);
           load_row<G>(Pl + G * (b + G * c), rl);
 #pragma unroll
-          for (int a = 0; a < G; ++a) dacc_fma(a1, df{rh[a], rl[a]}, l0[a]);
-          dacc_fma(a2, dacc_result(a1), l1[b]);
+          for (int a = 0; a < G; ++a) dacc_fma(a1, df{rh[a], rl[a]}, PT_LDF(0, a));
+          dacc_fma(a2, dacc_result(a1), PT_LDF(1, b));
         }
-#if PT_PICK_MAP
-        dacc_fma(a3, dacc_result(a2), pick<G>(l2, c));
+        dacc_fma(a3, dacc_result(a2), PT_LDF(2, c));
       }
     }
+#if PT_PICK_MAP
     const df rr = df_sub(dacc_result(a3), pick<3>(xloc, q));
     put<3>(r, q, __fadd_rn(rr.hi, rr.lo));
 #else
-        dacc_fma(a3, dacc_result(a2), l2[c]);
-      }
-    }
     const df rr = df_sub(dacc_result(a3), xloc[q]);
     r[q] = __fadd_rn(rr.hi, rr.lo);
 #endif
   }
+#undef PT_LDF
 }
 
 // Lagrange basis at z (l) and its increment dl = l(z + dz) - l(z), the latter
@@ -608,10 +637,10 @@ __device__ __noinline__ bool newton64_cold(const double* X64, const double* xl, 
 // 1e-5, then double-float residuals with the last FP32 inverse Jacobian until
 // the step is below newton_tol.  Returns the double-float xi in zd; a full
 // FP64 Newton is the (out-of-line) fallback.
-template <int G>
+template <int G, int SS = 0>
 __device__ __forceinline__ bool newton_df(const DevMesh& m, const DevConsts& k, int e,
                                           const df* xd, const float* guess, df* zd, int& it32,
-                                          int& it64) {
+                                          int& it64, float* sb = nullptr) {
   constexpr int G3 = G * G * G;
   const float* X32 = m.xg32 + (size_t)e * 3 * G3;
   const float* X32l = m.xg32lo + (size_t)e * 3 * G3;
@@ -622,7 +651,7 @@ __device__ __forceinline__ bool newton_df(const DevMesh& m, const DevConsts& k, 
   #pragma unroll 1
   for (int it = 0; it < 8; ++it) {
     float chi[3], J[9], r[3], d[3];
-    map_j32<G>(X32, z, tm, k, chi, J);
+    map_j32<G, SS>(X32, z, tm, k, chi, J, sb);
     if (!inv3(J, Ji)) break;
     have = true;
 #pragma unroll
@@ -657,7 +686,7 @@ __device__ __forceinline__ bool newton_df(const DevMesh& m, const DevConsts& k, 
 #pragma unroll
         for (int q = 0; q < 3; ++q) r[q] = rp[q] + dchi[q];
       } else {
-        resid_df<G>(X32, X32l, zd, tm, xd, k, r);
+        resid_df<G, SS>(X32, X32l, zd, tm, xd, k, r, sb);
       }
       matvec3(Ji, r, d);
 #pragma unroll

@@ -125,10 +125,17 @@ __device__ __forceinline__ void interp4_sh(const float* Ue, const float* l1, con
   }
 }
 
+// rows of the per-thread basis scratch of the inverse map (6 G floats)
+#ifndef PT_SMEM_BASIS
+#define PT_SMEM_BASIS 1
+#endif
+constexpr int kBasisRows = 6 * PT_MAXG;
+
 template <int G, int NP, bool MLP>
 __device__ __forceinline__ unsigned stage_one_f32(const StageArgs& a, int64_t t,
                                                   PushCounters& c, Hist8& h32, Hist8& h64,
-                                                  const float* Us = nullptr) {
+                                                  const float* Us = nullptr,
+                                                  float* sb = nullptr) {
   constexpr int N3 = NP * NP * NP;
   const int64_t n = a.n;
   const int s = a.stage;
@@ -162,7 +169,9 @@ __device__ __forceinline__ unsigned stage_one_f32(const StageArgs& a, int64_t t,
   }
   df zd[3];
   int i32 = 0, i64 = 0;
-  const bool ok = newton_df<G>(a.m, a.k, e, xd, guess, zd, i32, i64);
+  const bool ok = (PT_SMEM_BASIS && sb)
+                      ? newton_df<G, 128>(a.m, a.k, e, xd, guess, zd, i32, i64, sb)
+                      : newton_df<G>(a.m, a.k, e, xd, guess, zd, i32, i64);
   c.it32 += i32;
   c.it64 += i64;
   h32.add(i32);
@@ -407,8 +416,11 @@ __global__ void __launch_bounds__(128, PT_STAGE_MINB) k_stage_f32(const __grid_c
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t nround = (n + stride - 1) / stride * stride;  // uniform trip count per warp
   if constexpr (!UStage<NP>::ok) {
+    // this thread's column of the basis scratch (blocks of 128 threads)
+    __shared__ float s_basis[PT_SMEM_BASIS ? kBasisRows * 128 : 1];
+    float* sb = PT_SMEM_BASIS ? s_basis + threadIdx.x : nullptr;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nround; t += stride) {
-      const unsigned want = t < n ? stage_one_f32<G, NP, MLP>(a, t, c, h32, h64) : 0u;
+      const unsigned want = t < n ? stage_one_f32<G, NP, MLP>(a, t, c, h32, h64, nullptr, sb) : 0u;
       list_append(a, t, want);
     }
   } else {
