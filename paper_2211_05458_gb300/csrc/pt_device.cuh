@@ -1592,27 +1592,22 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
   tc.slow++;
   double xs[3] = {x[0], x[1], x[2]};
   double td[3] = {xe[0] - xs[0], xe[1] - xs[1], xe[2] - xs[2]};
-  if (td[0] == 0.0 && td[1] == 0.0 && td[2] == 0.0) {
+  double L = sqrt(dot3d(td, td));
+  if (!(L > 0.0)) {
 #pragma unroll
     for (int r = 0; r < 3; ++r) x[r] = xe[r];
     return;
   }
-  // The ray frame (unit direction, two normals, length).  FP64 mode builds it
-  // in FP64 at once.  FP32 mode builds the FP32 copy that the slab test and
-  // the screen use first, and the FP64 frame only when an exact solve, a
-  // wall, an open or a mortar face needs it: a crossing that the FP32 screen
-  // decides (R27) then issues no FP64 instruction for the frame.
-  constexpr bool kLazy = std::is_same<R, float>::value;
-  double L = 0.0;
-  double n1[3], n2[3];
-  float tdf[3], Lf, n1f[3], n2f[3];
-  bool have64 = false;
-  auto frame64 = [&]() {
-    if (have64) return;
-    L = sqrt(dot3d(td, td));
+  {
     const double iL = 1.0 / L;
 #pragma unroll
     for (int r = 0; r < 3; ++r) td[r] *= iL;
+  }
+  float tdf[3] = {(float)td[0], (float)td[1], (float)td[2]};
+  float Lf = (float)L;
+  float n1f[3], n2f[3];
+  double n1[3], n2[3];
+  {
     double ax[3] = {0, 0, 0};
     int im = 0;
     if (fabs(td[1]) < fabs(td[im])) im = 1;
@@ -1623,45 +1618,11 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
 #pragma unroll
     for (int r = 0; r < 3; ++r) n1[r] *= inn;
     cross3d(td, n1, n2);
-    have64 = true;
-  };
-  auto copy32 = [&]() {
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      tdf[r] = (float)td[r];
       n1f[r] = (float)n1[r];
       n2f[r] = (float)n2[r];
     }
-    Lf = (float)L;
-  };
-  bool lazy = kLazy;
-  if (lazy) {
-    const float u[3] = {(float)td[0], (float)td[1], (float)td[2]};
-    Lf = sqrtf(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    lazy = Lf > 1e-30f && Lf < 1e30f;
-    if (lazy) {
-      const float iLf = 1.f / Lf;
-#pragma unroll
-      for (int r = 0; r < 3; ++r) tdf[r] = u[r] * iLf;
-      float ax[3] = {0.f, 0.f, 0.f};
-      int im = 0;
-      if (fabsf(tdf[1]) < fabsf(tdf[im])) im = 1;
-      if (fabsf(tdf[2]) < fabsf(tdf[im])) im = 2;
-      ax[im] = 1.f;
-      n1f[0] = tdf[1] * ax[2] - tdf[2] * ax[1];
-      n1f[1] = tdf[2] * ax[0] - tdf[0] * ax[2];
-      n1f[2] = tdf[0] * ax[1] - tdf[1] * ax[0];
-      const float inn = rsqrtf(n1f[0] * n1f[0] + n1f[1] * n1f[1] + n1f[2] * n1f[2]);
-#pragma unroll
-      for (int r = 0; r < 3; ++r) n1f[r] *= inn;
-      n2f[0] = tdf[1] * n1f[2] - tdf[2] * n1f[1];
-      n2f[1] = tdf[2] * n1f[0] - tdf[0] * n1f[2];
-      n2f[2] = tdf[0] * n1f[1] - tdf[1] * n1f[0];
-    }
-  }
-  if (!lazy) {
-    frame64();
-    copy32();
   }
   double a0 = 0.0;
   int fin = -1;
@@ -1754,7 +1715,6 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
           }
         }
         exact_seen = true;
-        frame64();
         const double* Bf = m.bil + 72 * (size_t)e + 12 * f;
         double Bl[12];
 #pragma unroll
@@ -1829,7 +1789,6 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
     const int info = __ldg(m.finfo + 6 * (size_t)e + bf);
     const int bc = finfo_bc(info);
     if (bc == PT_BC_MORTAR) {
-      frame64();
       mortar_enter<G, CLIP>(m, k, __ldg(m.fnbr + 6 * (size_t)e + bf), bs, bt, xs, td, n1, n2, L,
                             a0, best, e, fin, a0, st);
       tc.cross++;
@@ -1847,7 +1806,6 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
       a0 = best;
       tc.cross++;
     } else if (bc == PT_BC_WALL) {
-      frame64();
       double ps[3], pt[3], nrm[3];
       const int kind = finfo_kind(info);
       if (kind == PT_FACE_CURVED) {
@@ -1906,7 +1864,6 @@ __device__ __noinline__ void track_slow(const DevMesh& m, const DevConsts& k, in
       Lf = (float)L;
       if (!(L > 0.0)) break;
     } else {
-      frame64();
 #pragma unroll
       for (int r = 0; r < 3; ++r) x[r] = xs[r] + best * td[r];
       st |= PT_ST_OPEN;
