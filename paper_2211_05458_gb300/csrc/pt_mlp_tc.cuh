@@ -6,9 +6,11 @@
 //   layer 1: D[128 x 64] = pre_e (per-particle element part, written into
 //            TMEM with tcgen05.st) + A1[128 x 16] B1[16 x 64], A1 holding
 //            xi_tri as a high and a low BF16 part per component;
-//   layers 2, 3: D = b (tcgen05.st) + A[128 x 64] (W/2)^T, A = 2 GELU(z) of
-//            the previous layer (GELU on packed BF16 pairs, the factor 1/2 in
-//            the weights, as in the warp-level form);
+//   layers 2, 3: D = 1 b^T + A[128 x 64] (W/2)^T, A = 2 GELU(z) of the
+//            previous layer (GELU on packed BF16 pairs, the factor 1/2 in the
+//            weights, as in the warp-level form); the bias enters as one more
+//            K = 16 MMA of a constant operand (columns 0, 1 = 1) with the
+//            bias's high and low BF16 parts, so no thread handles it;
 //   output: D[128 x 16] = A (W4/2)^T (rows 3..15 of W4 zero), + b4 in FP32.
 // One elected thread issues the MMAs and commits them to an mbarrier; every
 // thread reads its own row (TMEM lane = particle) with tcgen05.ld, applies
@@ -31,13 +33,15 @@ struct __align__(1024) MlpTcSmem {
   uint16_t a1[128 * 16];  // layer-1 operand, K = 16
   uint16_t b1[64 * 16];   // layer-1 weights, K = 16 (columns 2q, 2q+1 = W1x[.][q])
   uint16_t b4[16 * 64];   // W4 / 2, rows 3..15 zero
-  float bias[2][64];      // b2, b3
+  uint16_t ones[128 * 16];  // bias operand: k = 0, 1 equal to 1, K = 16
+  uint16_t bb[2][64 * 16];  // b2, b3 as high (k = 0) and low (k = 1) BF16 parts
   unsigned long long mbar;
   uint32_t tmem;
 };
-// dynamic shared memory of k_guess_tc: at most 4 CTAs per SM (4 x 128 TMEM
-// columns = the SM's 512)
-constexpr int kMlpTcSmem = 48 * 1024 + 1024;
+// dynamic shared memory of k_guess_tc (the struct plus room to align it to
+// 1024 bytes): at most 4 CTAs per SM (4 x 128 TMEM columns = the SM's 512)
+constexpr int kMlpTcSmem = (int)sizeof(MlpTcSmem) + 1024;
+static_assert(4 * (kMlpTcSmem + 1024) <= 228 * 1024, "4 CTAs per SM");
 constexpr uint32_t kMlpTcCols = 128;
 
 __device__ __forceinline__ uint32_t cm_off(int row, int kg, int sbo) {
@@ -173,9 +177,17 @@ __device__ __forceinline__ void mlp_tc_load(MlpTcSmem& s, const DevMLP& p) {
     s.b4[cm_off(row, c >> 3, 1024) / 2 + (c & 7)] =
         __bfloat16_as_ushort(__float2bfloat16_rn(row < 3 ? 0.5f * p.w4[row * 64 + c] : 0.f));
   }
-  for (int i = threadIdx.x; i < 64; i += blockDim.x) {
-    s.bias[0][i] = p.b2[i];
-    s.bias[1][i] = p.b3[i];
+  for (int i = threadIdx.x; i < 128 * 16; i += blockDim.x) {
+    const int row = i >> 4, k = i & 15;
+    s.ones[cm_off(row, k >> 3, 256) / 2 + (k & 7)] =
+        __bfloat16_as_ushort(__float2bfloat16_rn(k < 2 ? 1.f : 0.f));
+  }
+  for (int i = threadIdx.x; i < 2 * 64 * 16; i += blockDim.x) {
+    const int l = i >> 10, row = (i >> 4) & 63, k = i & 15;
+    const float b = l ? p.b3[row] : p.b2[row];
+    const float hi = __bfloat162float(__float2bfloat16_rn(b));
+    s.bb[l][cm_off(row, k >> 3, 256) / 2 + (k & 7)] =
+        __bfloat16_as_ushort(__float2bfloat16_rn(k == 0 ? hi : (k == 1 ? b - hi : 0.f)));
   }
 }
 
@@ -240,6 +252,9 @@ __device__ __forceinline__ bool mlp_tc_tile(MlpTcSmem& s, const DevMLP& p, const
         const uint16_t* B = layer == 1 ? s.b2 : layer == 2 ? s.b3 : s.b4;
         const uint32_t dcol = layer == 3 ? 64u : 0u;
         const int N = layer == 3 ? 16 : 64;
+        if (layer < 3)  // the accumulator starts at the bias
+          umma_bf16(tmem, umma_desc(smem_u32(s.ones), 128, 256),
+                    umma_desc(smem_u32(s.bb[layer - 1]), 128, 256), umma_idesc(128, 64), 0u);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
           umma_bf16(tmem + dcol, umma_desc(smem_u32(s.ah) + 256 * kk, 128, 1024),
@@ -280,12 +295,6 @@ __device__ __forceinline__ bool mlp_tc_tile(MlpTcSmem& s, const DevMLP& p, const
       asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};\n" ::"r"(arow + 128 * kg), "r"(w0),
                    "r"(w1), "r"(w2), "r"(w3)
                    : "memory");
-    }
-    // the next hidden layer's accumulator starts at its bias
-    if (layer < 2) {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) tmem_st16(lane_base + 16 * c, s.bias[layer] + 16 * c);
-      tmem_wait_st();
     }
   }
   return ok;
