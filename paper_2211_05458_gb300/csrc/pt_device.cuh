@@ -152,13 +152,23 @@ __device__ __forceinline__ void lagr_d(T x, const T* nodes, const T* w, T* l, T*
   }
 }
 
+// Read-only load: through the non-coherent path from global memory, or (SH)
+// a generic load, for data that may sit in shared memory.
+template <bool SH, typename V>
+__device__ __forceinline__ V ldx(const V* p) {
+  if constexpr (SH)
+    return *p;
+  else
+    return __ldg(p);
+}
+
 // G consecutive floats starting at p (p is 16-byte aligned when G == 4 and
 // 8-byte aligned when G is even: row starts are multiples of G in arrays whose
 // per-element blocks are multiples of 16 bytes)
-template <int G>
+template <int G, bool SH = false>
 __device__ __forceinline__ void load_row(const float* __restrict__ p, float* v) {
   if constexpr (G == 4) {
-    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    const float4 q = ldx<SH>(reinterpret_cast<const float4*>(p));
     v[0] = q.x;
     v[1] = q.y;
     v[2] = q.z;
@@ -166,13 +176,13 @@ __device__ __forceinline__ void load_row(const float* __restrict__ p, float* v) 
   } else if constexpr (G % 2 == 0) {
 #pragma unroll
     for (int i = 0; i < G; i += 2) {
-      const float2 q = __ldg(reinterpret_cast<const float2*>(p + i));
+      const float2 q = ldx<SH>(reinterpret_cast<const float2*>(p + i));
       v[i] = q.x;
       v[i + 1] = q.y;
     }
   } else {
 #pragma unroll
-    for (int i = 0; i < G; ++i) v[i] = __ldg(p + i);
+    for (int i = 0; i < G; ++i) v[i] = ldx<SH>(p + i);
   }
 }
 
@@ -218,6 +228,16 @@ __device__ __forceinline__ int corner_node(int q) {
 // local array (computed in a rolled loop, read through local memory); SS > 0
 // puts them in shared memory at sb[row * SS] (sb: this thread's column of a
 // [rows][SS] block array), which keeps local memory out of the L1 cache.
+// With a shared-memory scratch (SS > 0), the small per-thread results that
+// the rolled loops index at run time (chi, J, a residual, the interpolation's
+// third-direction basis and its outputs) also go through rows of the scratch
+// from kScratchOut on instead of through local memory (PT_SMEM_OUT = 1).
+#ifndef PT_SMEM_OUT
+#define PT_SMEM_OUT 1
+#endif
+constexpr int kScratchOut = 6 * PT_MAXG;
+constexpr int kScratchRows = kScratchOut + 12;
+
 template <int SS>
 struct BasisStore {
   float* sb;
@@ -226,7 +246,7 @@ struct BasisStore {
   __device__ __forceinline__ float get(int r) const { return SS > 0 ? sb[r * SS] : loc[r]; }
 };
 
-template <int G, int SS = 0>
+template <int G, int SS = 0, bool SH = false>
 __device__ __forceinline__ void map_j32(const float* __restrict__ X, const float* xi, int tm,
                                         const DevConsts& k, float* chi, float* J,
                                         float* sb = nullptr) {
@@ -263,7 +283,7 @@ __device__ __forceinline__ void map_j32(const float* __restrict__ X, const float
     if ((tm >> r) & 1) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const float xv = __ldg(Xr + corner_node<G>(q));
+        const float xv = ldx<SH>(Xr + corner_node<G>(q));
         const float a0 = (q & 1) ? hp[0] : hm[0], a1 = (q & 2) ? hp[1] : hm[1],
                     a2 = (q & 4) ? hp[2] : hm[2];
         const float s0 = (q & 1) ? 0.5f : -0.5f, s1 = (q & 2) ? 0.5f : -0.5f,
@@ -280,7 +300,7 @@ __device__ __forceinline__ void map_j32(const float* __restrict__ X, const float
 #pragma unroll
         for (int b = 0; b < G; ++b) {
           float sv = 0.f, s1 = 0.f, row[G];
-          load_row<G>(Xr + G * (b + G * c), row);
+          load_row<G, SH>(Xr + G * (b + G * c), row);
 #pragma unroll
           for (int a = 0; a < G; ++a) {
             sv = fmaf(row[a], PT_L(0, a), sv);
@@ -307,11 +327,24 @@ __device__ __forceinline__ void map_j32(const float* __restrict__ X, const float
         J[3 * q + 2] = j2;
       }
 #else
-    chi[r] = cr;
-    J[3 * r] = j0;
-    J[3 * r + 1] = j1;
-    J[3 * r + 2] = j2;
+    if constexpr (SS > 0 && PT_SMEM_OUT) {
+      sb[(kScratchOut + r) * SS] = cr;
+      sb[(kScratchOut + 3 + 3 * r) * SS] = j0;
+      sb[(kScratchOut + 4 + 3 * r) * SS] = j1;
+      sb[(kScratchOut + 5 + 3 * r) * SS] = j2;
+    } else {
+      chi[r] = cr;
+      J[3 * r] = j0;
+      J[3 * r + 1] = j1;
+      J[3 * r + 2] = j2;
+    }
 #endif
+  }
+  if constexpr (SS > 0 && PT_SMEM_OUT && !PT_PICK_MAP) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) chi[q] = sb[(kScratchOut + q) * SS];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) J[q] = sb[(kScratchOut + 3 + q) * SS];
   }
 }
 #undef PT_L
@@ -429,7 +462,7 @@ __device__ __forceinline__ void lagr_df(df x, const DevConsts& k, df* l) {
 // Residual chi(xi) - x of the element map in double-float, sum-factorised;
 // nodes as hi [3][G^3] + lo [3][G^3] (relative to the element centre);
 // coordinates flagged in tm use the 8-corner trilinear form.
-template <int G, int SS = 0>
+template <int G, int SS = 0, bool SH = false>
 __device__ __forceinline__ void resid_df(const float* __restrict__ Xh,
                                          const float* __restrict__ Xl, const df* xi, int tm,
                                          const df* xloc, const DevConsts& k, float* r,
@@ -482,7 +515,7 @@ __device__ __forceinline__ void resid_df(const float* __restrict__ Xh,
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         const int i = corner_node<G>(c);
-        dacc_fma(a3, df{__ldg(Ph + i), __ldg(Pl + i)}, w8[c]);
+        dacc_fma(a3, df{ldx<SH>(Ph + i), ldx<SH>(Pl + i)}, w8[c]);
       }
     } else {
 #pragma unroll 1
@@ -494,8 +527,8 @@ __device__ __forceinline__ void resid_df(const float* __restrict__ Xh,
           df_acc a1;
           dacc_init(a1);
           float rh[G], rl[G];
-          load_row<G>(Ph + G * (b + G * c), rh);
-          load_row<G>(Pl + G * (b + G * c), rl);
+          load_row<G, SH>(Ph + G * (b + G * c), rh);
+          load_row<G, SH>(Pl + G * (b + G * c), rl);
 #pragma unroll
           for (int a = 0; a < G; ++a) dacc_fma(a1, df{rh[a], rl[a]}, PT_LDF(0, a));
           dacc_fma(a2, dacc_result(a1), PT_LDF(1, b));
@@ -508,8 +541,15 @@ __device__ __forceinline__ void resid_df(const float* __restrict__ Xh,
     put<3>(r, q, __fadd_rn(rr.hi, rr.lo));
 #else
     const df rr = df_sub(dacc_result(a3), xloc[q]);
-    r[q] = __fadd_rn(rr.hi, rr.lo);
+    if constexpr (SS > 0 && PT_SMEM_OUT)
+      sb[(kScratchOut + q) * SS] = __fadd_rn(rr.hi, rr.lo);
+    else
+      r[q] = __fadd_rn(rr.hi, rr.lo);
 #endif
+  }
+  if constexpr (SS > 0 && PT_SMEM_OUT && !PT_PICK_MAP) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) r[q] = sb[(kScratchOut + q) * SS];
   }
 #undef PT_LDF
 }
@@ -555,10 +595,10 @@ __device__ __forceinline__ void lagr_inc(float z, float dz, const float* xn, con
 // second residual of the final Newton iterations: r(z + dz) = r(z) + dchi, with
 // r(z) from the double-float residual.  Nodes: FP32 high parts, relative to the
 // element centre (the low parts change dchi by ~1e-8 of itself).
-template <int G>
+template <int G, bool SH = false, int SS = 0>
 __device__ __forceinline__ void map_inc32(const float* __restrict__ X, const float* z,
                                           const float* dz, int tm, const DevConsts& k,
-                                          float* dchi) {
+                                          float* dchi, float* sb = nullptr) {
   constexpr int G3 = G * G * G;
   float l0[G], dl0[G], l1[G], dl1[G], l2[G], dl2[G];
   lagr_inc<G>(z[0], dz[0], k.gn32, k.gw32, l0, dl0);
@@ -584,7 +624,7 @@ __device__ __forceinline__ void map_inc32(const float* __restrict__ X, const flo
                     d2 = (c & 4) ? dh[2] : -dh[2];
         const float A1 = a1 + d1, A2 = a2 + d2;
         const float dw = d0 * A1 * A2 + a0 * d1 * A2 + a0 * a1 * d2;
-        acc = fmaf(__ldg(Xq + corner_node<G>(c)), dw, acc);
+        acc = fmaf(ldx<SH>(Xq + corner_node<G>(c)), dw, acc);
       }
     } else {
       float t1 = 0.f, t2 = 0.f, t3 = 0.f;
@@ -594,7 +634,7 @@ __device__ __forceinline__ void map_inc32(const float* __restrict__ X, const flo
 #pragma unroll
         for (int b = 0; b < G; ++b) {
           float row[G];
-          load_row<G>(Xq + G * (b + G * c), row);
+          load_row<G, SH>(Xq + G * (b + G * c), row);
           float A = 0.f, B = 0.f;
 #pragma unroll
           for (int a = 0; a < G; ++a) {
@@ -621,8 +661,15 @@ __device__ __forceinline__ void map_inc32(const float* __restrict__ X, const flo
 #if PT_PICK_MAP
     put<3>(dchi, q, acc);
 #else
-    dchi[q] = acc;
+    if constexpr (SS > 0 && PT_SMEM_OUT)
+      sb[(kScratchOut + q) * SS] = acc;
+    else
+      dchi[q] = acc;
 #endif
+  }
+  if constexpr (SS > 0 && PT_SMEM_OUT && !PT_PICK_MAP) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) dchi[q] = sb[(kScratchOut + q) * SS];
   }
 }
 
@@ -637,13 +684,16 @@ __device__ __noinline__ bool newton64_cold(const double* X64, const double* xl, 
 // 1e-5, then double-float residuals with the last FP32 inverse Jacobian until
 // the step is below newton_tol.  Returns the double-float xi in zd; a full
 // FP64 Newton is the (out-of-line) fallback.
-template <int G, int SS = 0>
+// Xs: optional copy of the element's FP32 nodes, high parts [3][G^3], then the
+// low parts from the next 16-byte boundary (read with generic loads when SH).
+template <int G, int SS = 0, bool SH = false>
 __device__ __forceinline__ bool newton_df(const DevMesh& m, const DevConsts& k, int e,
                                           const df* xd, const float* guess, df* zd, int& it32,
-                                          int& it64, float* sb = nullptr) {
+                                          int& it64, float* sb = nullptr,
+                                          const float* Xs = nullptr) {
   constexpr int G3 = G * G * G;
-  const float* X32 = m.xg32 + (size_t)e * 3 * G3;
-  const float* X32l = m.xg32lo + (size_t)e * 3 * G3;
+  const float* X32 = Xs ? Xs : m.xg32 + (size_t)e * 3 * G3;
+  const float* X32l = Xs ? Xs + ((3 * G3 + 3) & ~3) : m.xg32lo + (size_t)e * 3 * G3;
   const int tm = __ldg(m.tmask + e);
   float z[3] = {guess[0], guess[1], guess[2]};
   float Ji[9];
@@ -651,7 +701,7 @@ __device__ __forceinline__ bool newton_df(const DevMesh& m, const DevConsts& k, 
   #pragma unroll 1
   for (int it = 0; it < 8; ++it) {
     float chi[3], J[9], r[3], d[3];
-    map_j32<G, SS>(X32, z, tm, k, chi, J, sb);
+    map_j32<G, SS, SH>(X32, z, tm, k, chi, J, sb);
     if (!inv3(J, Ji)) break;
     have = true;
 #pragma unroll
@@ -682,11 +732,11 @@ __device__ __forceinline__ bool newton_df(const DevMesh& m, const DevConsts& k, 
       float r[3], d[3];
       if (inc) {
         float dchi[3];
-        map_inc32<G>(X32, z, dz, tm, k, dchi);
+        map_inc32<G, SH, SS>(X32, z, dz, tm, k, dchi, sb);
 #pragma unroll
         for (int q = 0; q < 3; ++q) r[q] = rp[q] + dchi[q];
       } else {
-        resid_df<G, SS>(X32, X32l, zd, tm, xd, k, r, sb);
+        resid_df<G, SS, SH>(X32, X32l, zd, tm, xd, k, r, sb);
       }
       matvec3(Ji, r, d);
 #pragma unroll
@@ -739,14 +789,20 @@ __device__ __forceinline__ bool newton_mixed(const DevMesh& m, const DevConsts& 
 #ifndef PT_INTERP_V2
 #define PT_INTERP_V2 1
 #endif
-template <int NP, typename T>
+template <int NP, typename T, bool SH = false, int SS = 0>
 __device__ __forceinline__ void interp4(const T* __restrict__ Ue, const T* l1, const T* l2,
-                                        const T* l3, T* out) {
+                                        const T* l3, T* out, float* sb = nullptr) {
   constexpr int N3 = NP * NP * NP;
 #if PT_INTERP_V2
   // two variables per pass: their row loads are independent, which doubles
   // the loads in flight per iteration
   if constexpr (std::is_same<T, float>::value && NP == 6) {
+    // rows kScratchOut + kk: l3; kScratchOut + NP + v: the results
+    constexpr bool kS = SS > 0 && PT_SMEM_OUT;
+    if constexpr (kS) {
+#pragma unroll
+      for (int kk = 0; kk < NP; ++kk) sb[(kScratchOut + kk) * SS] = l3[kk];
+    }
 #pragma unroll 1
     for (int v = 0; v < 4; v += 2) {
       const float* Ua = Ue + v * N3;
@@ -759,8 +815,8 @@ __device__ __forceinline__ void interp4(const T* __restrict__ Ue, const T* l1, c
         for (int j = 0; j < NP; j += 2) {
           const float4* qa = reinterpret_cast<const float4*>(Ua + NP * (j + NP * kk));
           const float4* qb = reinterpret_cast<const float4*>(Ub + NP * (j + NP * kk));
-          const float4 a0 = __ldg(qa), a1 = __ldg(qa + 1), a2 = __ldg(qa + 2);
-          const float4 b0 = __ldg(qb), b1 = __ldg(qb + 1), b2 = __ldg(qb + 2);
+          const float4 a0 = ldx<SH>(qa), a1 = ldx<SH>(qa + 1), a2 = ldx<SH>(qa + 2);
+          const float4 b0 = ldx<SH>(qb), b1 = ldx<SH>(qb + 1), b2 = ldx<SH>(qb + 2);
           const float ra0[6] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y};
           const float ra1[6] = {a1.z, a1.w, a2.x, a2.y, a2.z, a2.w};
           const float rb0[6] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y};
@@ -778,11 +834,21 @@ __device__ __forceinline__ void interp4(const T* __restrict__ Ue, const T* l1, c
           tb = fmaf(sb0, l2[j], tb);
           tb = fmaf(sb1, l2[j + 1], tb);
         }
-        acca = fmaf(ta, l3[kk], acca);
-        accb = fmaf(tb, l3[kk], accb);
+        const float lk = kS ? sb[(kScratchOut + kk) * SS] : l3[kk];
+        acca = fmaf(ta, lk, acca);
+        accb = fmaf(tb, lk, accb);
       }
-      out[v] = acca;
-      out[v + 1] = accb;
+      if constexpr (kS) {
+        sb[(kScratchOut + NP + v) * SS] = acca;
+        sb[(kScratchOut + NP + 1 + v) * SS] = accb;
+      } else {
+        out[v] = acca;
+        out[v + 1] = accb;
+      }
+    }
+    if constexpr (kS) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) out[v] = sb[(kScratchOut + NP + v) * SS];
     }
     return;
   }
@@ -802,7 +868,7 @@ __device__ __forceinline__ void interp4(const T* __restrict__ Ue, const T* l1, c
 #pragma unroll
         for (int j = 0; j < NP; j += 2) {
           const float4* q = reinterpret_cast<const float4*>(Uv + NP * (j + NP * kk));
-          const float4 q0 = __ldg(q), q1 = __ldg(q + 1), q2 = __ldg(q + 2);
+          const float4 q0 = ldx<SH>(q), q1 = ldx<SH>(q + 1), q2 = ldx<SH>(q + 2);
           const float r0[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
           const float r1[6] = {q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
           T t1 = T(0), u1 = T(0);
@@ -821,7 +887,7 @@ __device__ __forceinline__ void interp4(const T* __restrict__ Ue, const T* l1, c
           if constexpr (std::is_same<T, float>::value && NP % 4 == 0) {
 #pragma unroll
             for (int i = 0; i < NP; i += 4) {
-              const float4 q = __ldg(reinterpret_cast<const float4*>(row + i));
+              const float4 q = ldx<SH>(reinterpret_cast<const float4*>(row + i));
               t1 = tfma((T)q.x, l1[i], t1);
               t1 = tfma((T)q.y, l1[i + 1], t1);
               t1 = tfma((T)q.z, l1[i + 2], t1);
@@ -829,12 +895,12 @@ __device__ __forceinline__ void interp4(const T* __restrict__ Ue, const T* l1, c
             }
           } else if constexpr (std::is_same<T, float>::value && NP % 2 == 0) {
             float rv[NP];
-            load_row<NP>(reinterpret_cast<const float*>(row), rv);
+            load_row<NP, SH>(reinterpret_cast<const float*>(row), rv);
 #pragma unroll
             for (int i = 0; i < NP; ++i) t1 = tfma((T)rv[i], l1[i], t1);
           } else {
 #pragma unroll
-            for (int i = 0; i < NP; ++i) t1 = tfma(__ldg(row + i), l1[i], t1);
+            for (int i = 0; i < NP; ++i) t1 = tfma(ldx<SH>(row + i), l1[i], t1);
           }
           t2 = tfma(t1, l2[j], t2);
         }

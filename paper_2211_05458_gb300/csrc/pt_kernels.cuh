@@ -1356,6 +1356,30 @@ struct Family {
     }
     return (int)cudaGetLastError();
   }
+  // dynamic shared memory of k_stage_f32: the warp slots (blocks of 128 threads)
+  template <int NP>
+  static constexpr int stage_dyn_smem() {
+    if constexpr (F64)
+      return 0;
+    else
+      return UStage<NP>::ok ? 0 : WSlot<G, NP>::bytes;
+  }
+  // allows the dynamic shared memory above 48 KB per block; set once per
+  // instantiation, before the first occupancy query or launch
+  template <int NP>
+  static void stage_smem_attr() {
+    constexpr int dyn = stage_dyn_smem<NP>();
+    if constexpr (dyn > 0) {
+      static bool attr = false;
+      if (!attr) {
+        cudaFuncSetAttribute(k_stage_f32<G, NP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             dyn);
+        cudaFuncSetAttribute(k_stage_f32<G, NP, kMlp>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             dyn);
+        attr = true;
+      }
+    }
+  }
   template <int NP>
   static int staged(int op, const StageArgs& a, const DevParticles& p, const int* perm, int grid,
                     int block, cudaStream_t s) {
@@ -1373,10 +1397,12 @@ struct Family {
             k_locate_f32<G, false><<<grid, block, 0, s>>>(a);
           k_advance_f32<G, NP><<<grid, block, 0, s>>>(a);
         } else {
+          constexpr int dyn = stage_dyn_smem<NP>();
+          stage_smem_attr<NP>();
           if (kMlp && a.k.guess == PT_GUESS_MLP)
-            k_stage_f32<G, NP, kMlp><<<grid, block, 0, s>>>(a);
+            k_stage_f32<G, NP, kMlp><<<grid, block, dyn, s>>>(a);
           else
-            k_stage_f32<G, NP, false><<<grid, block, 0, s>>>(a);
+            k_stage_f32<G, NP, false><<<grid, block, dyn, s>>>(a);
         }
         break;
       case PT_SOP_TRACK:
@@ -1434,7 +1460,9 @@ struct Family {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nl, k_locate_f32<G, false>, block, 0);
       nb = nb < nl ? nb : nl;
     } else {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage_f32<G, NP, false>, block, 0);
+      stage_smem_attr<NP>();
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stage_f32<G, NP, false>, block,
+                                                    stage_dyn_smem<NP>());
     }
     return nb;
   }

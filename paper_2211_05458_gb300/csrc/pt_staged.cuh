@@ -125,37 +125,196 @@ __device__ __forceinline__ void interp4_sh(const float* Ue, const float* l1, con
   }
 }
 
-// rows of the per-thread basis scratch of the inverse map (6 G floats)
+// Element data requested up front: the element's FP32 geometry (high and low
+// parts, 12 G^3 bytes each) and rho, rho u (16 NP^3 bytes) are read through
+// rolled loops, one 64-byte piece per iteration, so without a prefetch their
+// cache misses follow one another.  Issued when the owner is known, the
+// misses overlap.  0: no prefetch; 1: one prefetch.global.L2 per 128-byte
+// line, every thread for its own element (equal addresses of a warp merge);
+// 2: the same with prefetch.global.L1; 3: one cp.async.bulk.prefetch.L2 per
+// array, issued by the first lane of each run of equal owners in the warp.
+// Measured on the 64^3 channel (10^7 particles): mode 3 gains 2-3 % with the
+// trilinear start (its third FP32 Newton iteration leaves the copies time to
+// land) and loses 2-3 % with the learned start; modes 1 and 2 lose 10 % with
+// the learned start.  Default: mode 3, trilinear start only (PT_PREFETCH_CUR).
+#ifndef PT_PREFETCH_ELEM
+#define PT_PREFETCH_ELEM 3
+#endif
+// 1: the current particle's element data is prefetched (mode PT_PREFETCH_ELEM);
+// 2: only with the trilinear start
+#ifndef PT_PREFETCH_CUR
+#define PT_PREFETCH_CUR 2
+#endif
+// 1: the particle state of the thread's next grid-stride position is
+// prefetched into L2 at the start of the current one; 2: in addition, that
+// position's owner is read at the start and its element data prefetched
+// after the current particle's inverse map
+#ifndef PT_PREFETCH_NEXT
+#define PT_PREFETCH_NEXT 0
+#endif
+
+__device__ __forceinline__ void prefetch_line(const void* p) {
+#if PT_PREFETCH_ELEM == 2
+  asm volatile("prefetch.global.L1 [%0];\n" ::"l"(p));
+#else
+  asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
+#endif
+}
+
+template <int BYTES>
+__device__ __forceinline__ void prefetch_range(const void* p) {
+  const uintptr_t b0 = (uintptr_t)p & ~(uintptr_t)127, b1 = (uintptr_t)p + BYTES;
+#pragma unroll
+  for (int i = 0; i < BYTES / 128 + 2; ++i)
+    if (b0 + 128u * i < b1) prefetch_line(reinterpret_cast<const void*>(b0 + 128u * i));
+}
+
+template <int G, int NP>
+__device__ __forceinline__ void prefetch_element(const StageArgs& a, int e, bool tri) {
+  constexpr int G3 = G * G * G, N3 = NP * NP * NP;
+  const float* xh = a.m.xg32 + (size_t)e * 3 * G3;
+  const float* xl = a.m.xg32lo + (size_t)e * 3 * G3;
+  const float* U = reinterpret_cast<const float*>(a.U) + (size_t)e * 5 * N3;
+#if PT_PREFETCH_ELEM == 3
+  // a bulk prefetch needs a 16-byte aligned start and size: element blocks are
+  // 12 G^3 and 20 NP^3 bytes apart from aligned bases
+  // (called by the warp's live lanes only)
+  const int lane = threadIdx.x & 31;
+  const unsigned live = __activemask();
+  const int prev = __shfl_up_sync(live, e, 1);
+  if (lane == 0 || !((live >> (lane - 1)) & 1u) || prev != e) {
+    if constexpr ((12 * G3) % 16 == 0) {
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(xh), "r"(12 * G3));
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(xl), "r"(12 * G3));
+    }
+    if constexpr ((20 * N3) % 16 == 0)
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(U), "r"(16 * N3));
+  }
+#elif PT_PREFETCH_ELEM
+  prefetch_range<12 * G3>(xh);
+  prefetch_range<12 * G3>(xl);
+  prefetch_range<16 * N3>(U);
+  if (tri) prefetch_line(a.m.tri + 12 * (size_t)e);
+#endif
+}
+
+// L2 prefetch of the state that stage_one_f32 reads at position t
+__device__ __forceinline__ void prefetch_state(const StageArgs& a, int64_t t, bool guess) {
+  const int64_t n = a.n;
+  const float* v = reinterpret_cast<const float*>(a.v);
+  const float* kx = reinterpret_cast<const float*>(a.kx);
+  const float* kv = reinterpret_cast<const float*>(a.kv);
+  asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a.st + t));
+  asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a.e + t));
+  asm volatile("prefetch.global.L2 [%0];\n" ::"l"(reinterpret_cast<const float*>(a.d) + t));
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a.xh + r * n + t));
+    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a.xl + r * n + t));
+    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(v + r * n + t));
+    if (a.stage > 0) {
+      asm volatile("prefetch.global.L2 [%0];\n" ::"l"(kx + r * n + t));
+      asm volatile("prefetch.global.L2 [%0];\n" ::"l"(kv + r * n + t));
+    }
+    if (guess) asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a.guess + r * n + t));
+  }
+}
+
+// Warp slots: per warp, K copies of an element's data in shared memory (the
+// FP32 nodes, high then low parts, 6 G^3 floats; rho, rho u, 4 NP^3 floats),
+// one per run of equal owners among the warp's 32 sorted particles (one or
+// two runs at ~30 particles per element).  The warp's lanes copy each slot
+// together, all loads in flight at once, so that the element's cache misses
+// overlap instead of following one another through the rolled loops of the
+// inverse map and the interpolation; particles of further runs read global
+// memory.  PT_STAGE_WSLOT: slots per warp (0: none; at most 40 KB per block).
+#ifndef PT_STAGE_WSLOT
+#define PT_STAGE_WSLOT 0
+#endif
+template <int G, int NP>
+struct WSlot {
+  static constexpr int G3 = G * G * G, N3 = NP * NP * NP;
+  // parts start on 16-byte boundaries: nodes high at 0, low at XS, state at UO
+  static constexpr int XS = (3 * G3 + 3) & ~3;
+  static constexpr int UO = 2 * XS;
+  static constexpr int F = UO + 4 * N3;  // floats per slot (a multiple of 4)
+  // float4 copies: element blocks of the nodes (3 G^3 floats) and of the
+  // state (5 NP^3 floats) and the slot parts are multiples of 16 bytes
+  static constexpr bool vec = (3 * G3) % 4 == 0 && N3 % 4 == 0;
+  static constexpr int K = (PT_STAGE_WSLOT >= 2 && 8 * F * 4 <= 40960)
+                               ? 2
+                               : ((PT_STAGE_WSLOT >= 1 && 4 * F * 4 <= 40960) ? 1 : 0);
+  static constexpr int bytes = 4 * K * F * 4;  // dynamic shared memory, 4 warps per block
+};
+
+// rows of the per-thread shared-memory scratch: the inverse map's bases (6 G
+// floats) and the rolled loops' results (kScratchOut on)
 #ifndef PT_SMEM_BASIS
 #define PT_SMEM_BASIS 1
 #endif
-constexpr int kBasisRows = 6 * PT_MAXG;
+constexpr int kBasisRows = kScratchRows;
 
-template <int G, int NP, bool MLP>
+// The particle state one FP32 stage reads, loaded at once and before anything
+// that depends on it (the status test included), so that its HBM latency is
+// paid once per particle rather than once for the status and again for the
+// rest.
+struct StageIn {
+  unsigned st;
+  int e;
+  float d;
+  df xd[3];
+  float v[3], kx[3], kv[3], g[3];
+};
+
+template <bool MLP>
+__device__ __forceinline__ void stage_load(const StageArgs& a, int64_t t, StageIn& in) {
+  const int64_t n = a.n;
+  const float* vg = reinterpret_cast<const float*>(a.v);
+  const float* kxg = reinterpret_cast<const float*>(a.kx);
+  const float* kvg = reinterpret_cast<const float*>(a.kv);
+  in.st = a.st[t];
+  in.e = a.e[t];
+  in.d = reinterpret_cast<const float*>(a.d)[t];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    in.xd[r] = df{a.xh[r * n + t], a.xl[r * n + t]};
+    in.v[r] = vg[r * n + t];
+    in.kx[r] = a.stage > 0 ? kxg[r * n + t] : 0.f;
+    in.kv[r] = a.stage > 0 ? kvg[r * n + t] : 0.f;
+    if constexpr (MLP) in.g[r] = a.guess[r * n + t];
+  }
+}
+
+// ES: the element's data may come from a warp slot Es (WSlot layout: FP32
+// nodes, high then low parts, then rho, rho u), read with generic loads;
+// Es == nullptr reads global memory the same way.
+template <int G, int NP, bool MLP, bool ES = false>
 __device__ __forceinline__ unsigned stage_one_f32(const StageArgs& a, int64_t t,
+                                                  const StageIn& in,
                                                   PushCounters& c, Hist8& h32, Hist8& h64,
                                                   const float* Us = nullptr,
-                                                  float* sb = nullptr) {
+                                                  float* sb = nullptr, int e_next = -1,
+                                                  const float* Es = nullptr) {
   constexpr int N3 = NP * NP * NP;
+  constexpr int G3 = G * G * G;
   const int64_t n = a.n;
   const int s = a.stage;
-  unsigned st = a.st[t];
+  unsigned st = in.st;
   if (st & PT_ST_FROZEN) return 0u;
-  const int e = a.e[t];
+  const int e = in.e;
+  if (PT_PREFETCH_CUR == 1 || (PT_PREFETCH_CUR == 2 && !MLP)) prefetch_element<G, NP>(a, e, !MLP);
   float* vg = reinterpret_cast<float*>(a.v);
   float* kxg = reinterpret_cast<float*>(a.kx);
   float* kvg = reinterpret_cast<float*>(a.kv);
-  const float d = reinterpret_cast<const float*>(a.d)[t];
+  const float d = in.d;
   df xd[3];
-  float v[3], kx[3] = {0.f, 0.f, 0.f}, kv[3] = {0.f, 0.f, 0.f};
+  float v[3], kx[3], kv[3];
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    xd[r] = df{a.xh[r * n + t], a.xl[r * n + t]};
-    v[r] = vg[r * n + t];
-    if (s > 0) {
-      kx[r] = kxg[r * n + t];
-      kv[r] = kvg[r * n + t];
-    }
+    xd[r] = in.xd[r];
+    v[r] = in.v[r];
+    kx[r] = in.kx[r];
+    kv[r] = in.kv[r];
   }
   const float mu = (float)a.k.mu;
   const float tau = (float)a.k.rho_p * d * d / (18.f * mu);
@@ -163,15 +322,19 @@ __device__ __forceinline__ unsigned stage_one_f32(const StageArgs& a, int64_t t,
   float guess[3];
   if constexpr (MLP) {
 #pragma unroll
-    for (int r = 0; r < 3; ++r) guess[r] = a.guess[r * n + t];
+    for (int r = 0; r < 3; ++r) guess[r] = in.g[r];
   } else {
     trilinear_guess(a.m, e, xf, guess);
   }
   df zd[3];
   int i32 = 0, i64 = 0;
-  const bool ok = (PT_SMEM_BASIS && sb)
-                      ? newton_df<G, 128>(a.m, a.k, e, xd, guess, zd, i32, i64, sb)
-                      : newton_df<G>(a.m, a.k, e, xd, guess, zd, i32, i64);
+  bool ok;
+  if constexpr (ES)
+    ok = newton_df<G, 128, true>(a.m, a.k, e, xd, guess, zd, i32, i64, sb, Es);
+  else
+    ok = (PT_SMEM_BASIS && sb) ? newton_df<G, 128>(a.m, a.k, e, xd, guess, zd, i32, i64, sb)
+                               : newton_df<G>(a.m, a.k, e, xd, guess, zd, i32, i64);
+  if (e_next >= 0) prefetch_element<G, NP>(a, e_next, !MLP);
   c.it32 += i32;
   c.it64 += i64;
   h32.add(i32);
@@ -197,8 +360,12 @@ __device__ __forceinline__ unsigned stage_one_f32(const StageArgs& a, int64_t t,
   lagr<NP, float>(xi[0], a.k.sn32, a.k.sw32, l1);
   lagr<NP, float>(xi[1], a.k.sn32, a.k.sw32, l2);
   lagr<NP, float>(xi[2], a.k.sn32, a.k.sw32, l3);
-  if (Us)
+  if constexpr (ES)
+    interp4<NP, float, true, 128>(Es ? Es + WSlot<G, NP>::UO : Ue, l1, l2, l3, Uv, sb);
+  else if (Us)
     interp4_sh<NP>(Us, l1, l2, l3, Uv);
+  else if (PT_SMEM_BASIS && sb)
+    interp4<NP, float, false, 128>(Ue, l1, l2, l3, Uv, sb);
   else
     interp4<NP, float>(Ue, l1, l2, l3, Uv);
   particle_accel_f32<G, NP>(a.m, a.k, Ue, e, zd, Uv, v, d, tau, st, acc);
@@ -407,6 +574,77 @@ struct UStage {
   static constexpr bool ok = PT_STAGE_U && (NP % 2 == 0);
 };
 
+// Fills the warp's slots for the lanes' owners e0 (-1: no particle, or a
+// frozen one; every lane of the warp calls it) and returns this lane's slot,
+// or nullptr.
+template <int G, int NP>
+__device__ __forceinline__ const float* wslot_fill(const StageArgs& a, int e0, float* slots) {
+  using W = WSlot<G, NP>;
+  constexpr int G3 = W::G3, N3 = W::N3, F = W::F;
+  const int lane = threadIdx.x & 31;
+  const int prev = __shfl_up_sync(0xffffffffu, e0, 1);
+  const bool start = e0 >= 0 && (lane == 0 || prev != e0);
+  const unsigned bm = __ballot_sync(0xffffffffu, start);
+  const int run = __popc(bm & ((2u << lane) - 1u)) - 1;  // this lane's run
+  __syncwarp();  // the warp's reads of the previous contents are complete
+  unsigned rest = bm;
+#pragma unroll
+  for (int q = 0; q < W::K; ++q) {
+    if (!rest) break;
+    const int es = __shfl_sync(0xffffffffu, e0, __ffs(rest) - 1);
+    rest &= rest - 1u;
+    float* dst = slots + q * F;
+    const float* xh = a.m.xg32 + (size_t)es * 3 * G3;
+    const float* xl = a.m.xg32lo + (size_t)es * 3 * G3;
+    const float* U = reinterpret_cast<const float*>(a.U) + (size_t)es * 5 * N3;
+    if constexpr (W::vec) {
+      // float4 pieces: nodes high, nodes low, state; CH loads in flight per lane
+      constexpr int nx = 3 * G3 / 4, nt = F / 4, per = (nt + 31) / 32, CH = 12;
+#pragma unroll
+      for (int j0 = 0; j0 < per; j0 += CH) {
+        float4 r[CH];
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+          const int i = lane + 32 * (j0 + j);
+          if (j0 + j < per && i < nt) {
+            const float* src =
+                i < nx ? xh + 4 * i : (i < 2 * nx ? xl + 4 * (i - nx) : U + 4 * (i - 2 * nx));
+            r[j] = __ldg(reinterpret_cast<const float4*>(src));
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+          const int i = lane + 32 * (j0 + j);
+          if (j0 + j < per && i < nt) reinterpret_cast<float4*>(dst)[i] = r[j];
+        }
+      }
+    } else {
+      // slot index i: nodes high below XS, low below UO (the padding after
+      // 3 G^3 floats of each is left unwritten), state above
+      constexpr int nx = 3 * G3, XS = W::XS, UO = W::UO, per = (F + 31) / 32, CH = 32;
+#pragma unroll
+      for (int j0 = 0; j0 < per; j0 += CH) {
+        float r[CH];
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+          const int i = lane + 32 * (j0 + j);
+          const int o = i < XS ? i : (i < UO ? i - XS : i - UO);
+          if (j0 + j < per && i < F && (i >= UO || o < nx))
+            r[j] = __ldg(i < XS ? xh + o : (i < UO ? xl + o : U + o));
+        }
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+          const int i = lane + 32 * (j0 + j);
+          const int o = i < XS ? i : (i < UO ? i - XS : i - UO);
+          if (j0 + j < per && i < F && (i >= UO || o < nx)) dst[i] = r[j];
+        }
+      }
+    }
+  }
+  __syncwarp();
+  return (e0 >= 0 && run < W::K) ? slots + run * F : nullptr;
+}
+
 template <int G, int NP, bool MLP>
 __global__ void __launch_bounds__(128, PT_STAGE_MINB) k_stage_f32(const __grid_constant__ StageArgs a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.count_next = 0u;
@@ -419,8 +657,33 @@ __global__ void __launch_bounds__(128, PT_STAGE_MINB) k_stage_f32(const __grid_c
     // this thread's column of the basis scratch (blocks of 128 threads)
     __shared__ float s_basis[PT_SMEM_BASIS ? kBasisRows * 128 : 1];
     float* sb = PT_SMEM_BASIS ? s_basis + threadIdx.x : nullptr;
+    if constexpr (WSlot<G, NP>::K > 0) {
+      extern __shared__ __align__(16) float s_wslot[];
+      float* slots = s_wslot + (threadIdx.x >> 5) * WSlot<G, NP>::K * WSlot<G, NP>::F;
+      for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nround; t += stride) {
+        StageIn in;
+        if (t < n) stage_load<MLP>(a, t, in);
+        const int e0 = (t < n && !(in.st & PT_ST_FROZEN)) ? in.e : -1;
+        const float* Es = wslot_fill<G, NP>(a, e0, slots);
+        const unsigned want =
+            t < n ? stage_one_f32<G, NP, MLP, true>(a, t, in, c, h32, h64, nullptr, sb, -1, Es)
+                  : 0u;
+        list_append(a, t, want);
+      }
+    } else
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nround; t += stride) {
-      const unsigned want = t < n ? stage_one_f32<G, NP, MLP>(a, t, c, h32, h64, nullptr, sb) : 0u;
+      int e_next = -1;
+      if (PT_PREFETCH_NEXT && t + stride < n) {
+        prefetch_state(a, t + stride, MLP);
+        if (PT_PREFETCH_NEXT == 2) {
+          e_next = a.e[t + stride];
+          if ((unsigned)e_next >= (unsigned)a.m.nelem) e_next = -1;
+        }
+      }
+      StageIn in;
+      if (t < n) stage_load<MLP>(a, t, in);
+      const unsigned want =
+          t < n ? stage_one_f32<G, NP, MLP>(a, t, in, c, h32, h64, nullptr, sb, e_next) : 0u;
       list_append(a, t, want);
     }
   } else {
@@ -480,7 +743,9 @@ __global__ void __launch_bounds__(128, PT_STAGE_MINB) k_stage_f32(const __grid_c
       }
       phase ^= 1u;
       const float* Us = (e0 >= 0 && run < SL) ? sU[run] : nullptr;
-      const unsigned want = inr ? stage_one_f32<G, NP, MLP>(a, t, c, h32, h64, Us) : 0u;
+      StageIn in;
+      if (inr) stage_load<MLP>(a, t, in);
+      const unsigned want = inr ? stage_one_f32<G, NP, MLP>(a, t, in, c, h32, h64, Us) : 0u;
       list_append(a, t, want);
     }
   }
