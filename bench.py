@@ -181,7 +181,7 @@ def make_workload(args, device, seed, precision):
 # launch on the 32^3, 10^6-particle channel, divided by its 10^6 particles;
 # profiles/); the traffic is per particle, so it scales with the particles of
 # a launch.  None while the kernel differs from the captured one.
-TRAFFIC_BYTES_PER_PARTICLE_STAGE = (235.153920e6 + 62.632704e6) / 1e6
+TRAFFIC_BYTES_PER_PARTICLE_STAGE = (235.257088e6 + 48.194816e6) / 1e6
 
 
 def algorithmic_flops_per_particle_stage(G=4, NP=6, ntri=2, it_full=2.0, it_resid=2.0):

@@ -201,24 +201,6 @@ __device__ __forceinline__ bool mlp_tc_tile(MlpTcSmem& s, const DevMLP& p, const
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
   const uint32_t mbar = smem_u32(&s.mbar);
-  // layer-1 operand row: (hi, lo) BF16 parts of xi_tri at k = 2q, 2q+1
-  {
-    uint32_t w[8];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const float hi = __bfloat162float(__float2bfloat16_rn(xi_tri[q]));
-      w[q] = pack_bf16(hi, xi_tri[q] - hi);
-    }
-#pragma unroll
-    for (int q = 3; q < 8; ++q) w[q] = 0u;
-    const uint32_t a = smem_u32(s.a1) + cm_off(tid, 0, 256);
-    asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};\n" ::"r"(a), "r"(w[0]), "r"(w[1]),
-                 "r"(w[2]), "r"(w[3])
-                 : "memory");
-    asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};\n" ::"r"(a + 128), "r"(w[4]), "r"(w[5]),
-                 "r"(w[6]), "r"(w[7])
-                 : "memory");
-  }
   // accumulator of layer 1 starts at the element part pre_e
   {
     const float4* pre = reinterpret_cast<const float4*>(m.mlp_pre + 64 * (size_t)e);
@@ -236,6 +218,24 @@ __device__ __forceinline__ bool mlp_tc_tile(MlpTcSmem& s, const DevMLP& p, const
       tmem_st16(lane_base + 16 * c, v);
     }
     tmem_wait_st();
+  }
+  // layer-1 operand row: (hi, lo) BF16 parts of xi_tri at k = 2q, 2q+1
+  {
+    uint32_t w[8];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float hi = __bfloat162float(__float2bfloat16_rn(xi_tri[q]));
+      w[q] = pack_bf16(hi, xi_tri[q] - hi);
+    }
+#pragma unroll
+    for (int q = 3; q < 8; ++q) w[q] = 0u;
+    const uint32_t a = smem_u32(s.a1) + cm_off(tid, 0, 256);
+    asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};\n" ::"r"(a), "r"(w[0]), "r"(w[1]),
+                 "r"(w[2]), "r"(w[3])
+                 : "memory");
+    asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};\n" ::"r"(a + 128), "r"(w[4]), "r"(w[5]),
+                 "r"(w[6]), "r"(w[7])
+                 : "memory");
   }
   bool ok = true;
 #pragma unroll 1

@@ -134,11 +134,16 @@ __device__ __forceinline__ void interp4_sh(const float* Ue, const float* l1, con
 // 2: the same with prefetch.global.L1; 3: one cp.async.bulk.prefetch.L2 per
 // array, issued by the first lane of each run of equal owners in the warp.
 // Measured on the 64^3 channel (10^7 particles): mode 3 gains 2-3 % with the
-// trilinear start (its third FP32 Newton iteration leaves the copies time to
-// land) and loses 2-3 % with the learned start; modes 1 and 2 lose 10 % with
-// the learned start.  Default: mode 3, trilinear start only (PT_PREFETCH_CUR).
+// trilinear start (whose table read, a load that depends on the owner, comes
+// before the first node loads and leaves the copies time to land) and loses
+// 2-3 % with the learned start; modes 1 and 2 lose 10 % with the learned
+// start.  Default: mode 3, trilinear start only (PT_PREFETCH_CUR).
 #ifndef PT_PREFETCH_ELEM
 #define PT_PREFETCH_ELEM 3
+#endif
+// parts of the element data prefetched: 1 nodes (high), 2 nodes (low), 4 rho, rho u
+#ifndef PT_PREFETCH_PARTS
+#define PT_PREFETCH_PARTS 6
 #endif
 // 1: the current particle's element data is prefetched (mode PT_PREFETCH_ELEM);
 // 2: only with the trilinear start
@@ -184,16 +189,18 @@ __device__ __forceinline__ void prefetch_element(const StageArgs& a, int e, bool
   const int prev = __shfl_up_sync(live, e, 1);
   if (lane == 0 || !((live >> (lane - 1)) & 1u) || prev != e) {
     if constexpr ((12 * G3) % 16 == 0) {
-      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(xh), "r"(12 * G3));
-      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(xl), "r"(12 * G3));
+      if (PT_PREFETCH_PARTS & 1)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(xh), "r"(12 * G3));
+      if (PT_PREFETCH_PARTS & 2)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(xl), "r"(12 * G3));
     }
     if constexpr ((20 * N3) % 16 == 0)
-      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(U), "r"(16 * N3));
+      if (PT_PREFETCH_PARTS & 4) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(U), "r"(16 * N3));
   }
 #elif PT_PREFETCH_ELEM
-  prefetch_range<12 * G3>(xh);
-  prefetch_range<12 * G3>(xl);
-  prefetch_range<16 * N3>(U);
+  if (PT_PREFETCH_PARTS & 1) prefetch_range<12 * G3>(xh);
+  if (PT_PREFETCH_PARTS & 2) prefetch_range<12 * G3>(xl);
+  if (PT_PREFETCH_PARTS & 4) prefetch_range<16 * N3>(U);
   if (tri) prefetch_line(a.m.tri + 12 * (size_t)e);
 #endif
 }
@@ -756,8 +763,11 @@ __global__ void __launch_bounds__(128, PT_STAGE_MINB) k_stage_f32(const __grid_c
 
 // Exact tracking of the listed stage segments, then the walk that checks the
 // new owner; FP64 on global positions, back to the double-float offset.
+#ifndef PT_TRACK_MINB
+#define PT_TRACK_MINB 1
+#endif
 template <int G, bool CLIP>
-__global__ void __launch_bounds__(128) k_track_f32(const __grid_constant__ StageArgs a) {
+__global__ void __launch_bounds__(128, PT_TRACK_MINB) k_track_f32(const __grid_constant__ StageArgs a) {
   PushCounters c = {0, 0, 0, {0, 0, 0}};
   Hist8 hcr;
   const int64_t n = a.n;
@@ -910,7 +920,15 @@ __global__ void __launch_bounds__(128, 1) k_guess_tc(const __grid_constant__ Sta
     const bool live = !(st & PT_ST_FROZEN) && e0 >= 0 && e0 < a.m.nelem;
     const int e = live ? e0 : 0;
     float xf[3] = {0.f, 0.f, 0.f}, xi_tri[3], guess[3];
-    if (live) start_pos<FROM_X>(a, t, e, xf);
+    if constexpr (FROM_X) {
+      if (live) start_pos<FROM_X>(a, t, e, xf);
+    } else {
+      // the staged offsets are read with the status and the owner (one HBM
+      // latency), and zeroed for dead rows afterwards
+      if (inr) start_pos<FROM_X>(a, t, e, xf);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) xf[r] = live ? xf[r] : 0.f;
+    }
     trilinear_guess(a.m, e, xf, xi_tri);
     if (!mlp_tc_tile(s, a.mlp, a.m, tmem, e, xi_tri, guess, phase)) {
       if (tid == 0) atomicAdd(a.stats + PT_C_TIMEOUT, 1ull);
