@@ -239,3 +239,30 @@ def test_split_call_resume(precision):
         ev = np.abs(a["v"] - b["v"]) / np.maximum(np.abs(a["v"]), 1.0)
         print("FP32 call boundary: max rel dx %.2e dv %.2e" % (ex[~near].max(), ev[~near].max()))
         assert ex[~near].max() <= 1e-9 and ev[~near].max() <= 1e-6
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("schedule", [pt.SCHEDULE_RESIDENT, pt.SCHEDULE_STAGED])
+def test_push_host_equals_device_push(precision, schedule):
+    """pt_push_host (host arrays staged through device buffers and copied
+    back) gives bitwise the device push, from pinned and from pageable host
+    memory."""
+    wl = W.curved_channel((6, 6, 6), 2, 5, P=3000, nsteps=4, dt=2e-3, seed=11)
+    _speed_up(wl, seed=11)
+    h = 2.0 / 6
+    band = dict(band_ref=2e-4, band_x=1e-4 * h) if precision == "fp32" else {}
+    ctx = H.gpu_context(wl, precision, schedule=schedule, **band)
+    dev = H.gpu_particles(wl, ctx)
+    st_dev = ctx.push(dev, 4, wl.dt)
+    torch.cuda.synchronize()
+    ref = H.gpu_result(dev)
+    assert st_dev["crossings"] > 50
+    for pin in (True, False):
+        hp = H.gpu_particles(wl, ctx).to("cpu", pin=pin)
+        st = ctx.push_host(hp, 4, wl.dt)
+        got = H.gpu_result(hp)
+        for k in ("x", "v", "elem", "hits", "status"):
+            assert np.array_equal(ref[k], got[k]), (pin, k)
+        for k, val in st.items():
+            assert st_dev[k] == val, (pin, k)
