@@ -911,23 +911,37 @@ __global__ void __launch_bounds__(128, 1) k_guess_tc(const __grid_constant__ Sta
   const uint32_t tmem = s.tmem;
   uint32_t phase = 0u;
   const int64_t n = a.n;
-  for (int64_t base = (int64_t)blockIdx.x * 128; base < n; base += (int64_t)gridDim.x * 128) {
-    const int64_t t = base + tid;
+  // the status, owner and (staged state) offset of a row, read one tile ahead
+  // so that their HBM latency overlaps the previous tile's network
+  auto row_in = [&](int64_t t, unsigned& st, int& e0, float* xo) {
     const bool inr = t < n;
     // (a.st is null for pt_mlp_start: every particle with an owner in range)
-    const unsigned st = inr ? (a.st ? a.st[t] : 0u) : (unsigned)PT_ST_FROZEN;
-    const int e0 = inr ? a.e[t] : 0;
+    st = inr ? (a.st ? a.st[t] : 0u) : (unsigned)PT_ST_FROZEN;
+    e0 = inr ? a.e[t] : 0;
+    if constexpr (!FROM_X) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) xo[r] = inr ? a.xh[r * n + t] : 0.f;
+    }
+  };
+  const int64_t tstride = (int64_t)gridDim.x * 128;
+  unsigned st_nx;
+  int e_nx;
+  float x_nx[3] = {0.f, 0.f, 0.f};
+  row_in((int64_t)blockIdx.x * 128 + tid, st_nx, e_nx, x_nx);
+  for (int64_t base = (int64_t)blockIdx.x * 128; base < n; base += tstride) {
+    const int64_t t = base + tid;
+    const unsigned st = st_nx;
+    const int e0 = e_nx;
+    float xc[3] = {x_nx[0], x_nx[1], x_nx[2]};
+    if (base + tstride < n) row_in(t + tstride, st_nx, e_nx, x_nx);
     const bool live = !(st & PT_ST_FROZEN) && e0 >= 0 && e0 < a.m.nelem;
     const int e = live ? e0 : 0;
     float xf[3] = {0.f, 0.f, 0.f}, xi_tri[3], guess[3];
     if constexpr (FROM_X) {
       if (live) start_pos<FROM_X>(a, t, e, xf);
     } else {
-      // the staged offsets are read with the status and the owner (one HBM
-      // latency), and zeroed for dead rows afterwards
-      if (inr) start_pos<FROM_X>(a, t, e, xf);
 #pragma unroll
-      for (int r = 0; r < 3; ++r) xf[r] = live ? xf[r] : 0.f;
+      for (int r = 0; r < 3; ++r) xf[r] = live ? xc[r] : 0.f;
     }
     trilinear_guess(a.m, e, xf, xi_tri);
     if (!mlp_tc_tile(s, a.mlp, a.m, tmem, e, xi_tri, guess, phase)) {
