@@ -194,8 +194,10 @@ __device__ __forceinline__ void prefetch_element(const StageArgs& a, int e, bool
       if (PT_PREFETCH_PARTS & 2)
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(xl), "r"(12 * G3));
     }
-    if constexpr ((20 * N3) % 16 == 0)
-      if (PT_PREFETCH_PARTS & 4) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(U), "r"(16 * N3));
+    if constexpr ((20 * N3) % 16 == 0) {
+      if (PT_PREFETCH_PARTS & 4)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(U), "r"(16 * N3));
+    }
   }
 #elif PT_PREFETCH_ELEM
   if (PT_PREFETCH_PARTS & 1) prefetch_range<12 * G3>(xh);
@@ -235,6 +237,8 @@ __device__ __forceinline__ void prefetch_state(const StageArgs& a, int64_t t, bo
 // overlap instead of following one another through the rolled loops of the
 // inverse map and the interpolation; particles of further runs read global
 // memory.  PT_STAGE_WSLOT: slots per warp (0: none; at most 40 KB per block).
+// Measured slower than reading through L1 at every size (the slots leave L1 a
+// third of its room, and the kernel's local memory then misses): off.
 #ifndef PT_STAGE_WSLOT
 #define PT_STAGE_WSLOT 0
 #endif
