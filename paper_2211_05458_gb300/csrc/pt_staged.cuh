@@ -307,7 +307,6 @@ __device__ __forceinline__ unsigned stage_one_f32(const StageArgs& a, int64_t t,
                                                   float* sb = nullptr, int e_next = -1,
                                                   const float* Es = nullptr) {
   constexpr int N3 = NP * NP * NP;
-  constexpr int G3 = G * G * G;
   const int64_t n = a.n;
   const int s = a.stage;
   unsigned st = in.st;
